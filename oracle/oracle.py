@@ -1,0 +1,207 @@
+"""ctypes wrapper of the FP64 CPU oracle (collage_oracle.c) -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg import this
+module.  The CUDA library never does.  The shared object is built here with gcc (OpenMP, no
+floating-point contraction) into ``oracle/_build/``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "collage_oracle.c")
+_HDR = os.path.join(_HERE, "collage_oracle.h")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc if the shared object is missing or older than its sources."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    stale = not os.path.exists(_LIB) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Opts(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("delta", C.c_double), ("tau", C.c_double), ("w_in", C.c_double),
+                ("w_out", C.c_double), ("n_dil", C.c_int), ("dil_weight", C.c_double * 8),
+                ("pad_px", C.c_double), ("rho_px", C.c_double), ("cull", C.c_int)]
+
+
+def options(alpha=3e3, beta=8e4, gamma=5e-4, delta=0.0, tau=0.5, w_in=1.0, w_out=100.0,
+            n_dil=4, dil_weight=(1.0, 2.0, 3.0, 4.0), pad_px=0.0, rho_px=1.0, cull=1) -> Opts:
+    """Oracle options; the defaults are the weights of Eq. 8 and the readings of Eqs. 5-7."""
+    o = Opts()
+    o.alpha, o.beta, o.gamma, o.delta = alpha, beta, gamma, delta
+    o.tau, o.w_in, o.w_out = tau, w_in, w_out
+    o.n_dil = n_dil
+    for k in range(8):
+        o.dil_weight[k] = dil_weight[k] if k < len(dil_weight) else 0.0
+    o.pad_px, o.rho_px, o.cull = pad_px, rho_px, cull
+    return o
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = C.CDLL(build())
+    vp = C.c_void_p
+    lib.ora_scene_create.restype = vp
+    lib.ora_scene_create.argtypes = [C.c_int, _ip, _ip, _fp, _fp, C.c_int, C.c_int, _ip, _fp]
+    lib.ora_scene_free.argtypes = [vp]
+    lib.ora_n_vertices.argtypes = [vp, C.c_int]
+    lib.ora_total_vertices.argtypes = [vp]
+    lib.ora_local_vertices.argtypes = [vp, C.c_int, _dp]
+    lib.ora_world_vertices.argtypes = [vp, _dp, C.c_int, _dp]
+    lib.ora_signed_distance.argtypes = [vp, _dp, C.c_int, C.c_int, _dp, _dp, _ip, _dp]
+    lib.ora_container_sd.argtypes = [vp, C.c_int, _dp, _dp]
+    opt = C.POINTER(Opts)
+    dpn = C.c_void_p  # nullable double*
+    lib.ora_render.argtypes = [vp, _dp, C.c_int, opt, dpn, dpn, dpn]
+    lib.ora_eval.argtypes = [vp, _dp, C.c_int, opt, dpn, dpn, dpn, dpn]
+    lib.ora_adam.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double,
+                             C.c_double, C.c_double, C.c_void_p, C.c_double, C.c_double]
+    for name in ("ora_bins", "ora_bins_bruteforce"):
+        f = getattr(lib, name)
+        f.restype = C.c_long
+        f.argtypes = [vp, _fp, C.c_int, C.c_int, C.c_float, C.c_float, _ip, _ip, C.c_long]
+    lib.ora_bin_radius.restype = C.c_float
+    lib.ora_bin_radius.argtypes = [vp, C.c_int]
+    lib.ora_pair_work.restype = C.c_double
+    lib.ora_pair_work.argtypes = [vp, _dp, C.c_int, opt]
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class Scene:
+    """Flattened elements and container of one collage problem (see workloads.make_problem)."""
+
+    def __init__(self, prob: dict, segs_per_cubic: int = 16):
+        lib = _load()
+        self.n = int(len(prob["kind"]))
+        kind = np.ascontiguousarray(prob["kind"], np.int32)
+        off = np.ascontiguousarray(prob["pt_off"], np.int32)
+        for e in range(self.n):
+            npt = off[e + 1] - off[e]
+            if kind[e] == 0 and (npt < 3 or npt % 3):
+                raise ValueError("cubic path needs 3N control points")
+            if kind[e] == 1 and npt < 3 or kind[e] == 2 and npt < 2:
+                raise ValueError("too few points")
+        self._keep = [kind, off, np.ascontiguousarray(prob["pts"], np.float32),
+                      np.ascontiguousarray(prob["hw"], np.float32),
+                      np.ascontiguousarray(prob["ring_off"], np.int32),
+                      np.ascontiguousarray(prob["ring_pts"], np.float32)]
+        k = self._keep
+        self.h = lib.ora_scene_create(self.n, k[0], k[1], k[2], k[3], segs_per_cubic,
+                                      len(k[4]) - 1, k[4], k[5])
+        self.lib = lib
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.ora_scene_free(self.h)
+            self.h = None
+
+    # geometry -------------------------------------------------------------------------------
+    def n_vertices(self, e):
+        return self.lib.ora_n_vertices(self.h, e)
+
+    def total_vertices(self):
+        return self.lib.ora_total_vertices(self.h)
+
+    def local_vertices(self, e):
+        out = np.zeros(2 * self.n_vertices(e))
+        self.lib.ora_local_vertices(self.h, e, out)
+        return out.reshape(-1, 2)
+
+    def world_vertices(self, params, e):
+        out = np.zeros(2 * self.n_vertices(e))
+        self.lib.ora_world_vertices(self.h, _d(params), e, out)
+        return out.reshape(-1, 2)
+
+    def sd(self, params, e, xy):
+        xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+        n = len(xy)
+        sd, u = np.zeros(n), np.zeros(n)
+        seg = np.zeros(n, np.int32)
+        self.lib.ora_signed_distance(self.h, _d(params), e, n, xy.reshape(-1), sd, seg, u)
+        return sd, seg, u
+
+    def container_sd(self, xy):
+        xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+        out = np.zeros(len(xy))
+        self.lib.ora_container_sd(self.h, len(xy), xy.reshape(-1), out)
+        return out
+
+    # rendering / loss / gradient ------------------------------------------------------------
+    def render(self, params, res, opts):
+        ihat, atau, covc = (np.zeros(res * res) for _ in range(3))
+        self.lib.ora_render(self.h, _d(params), res, C.byref(opts), _ptr(ihat), _ptr(atau),
+                            _ptr(covc))
+        return ihat.reshape(res, res), atau.reshape(res, res), covc.reshape(res, res)
+
+    def eval(self, params, res, opts, grad=True, grad_v=False):
+        terms = np.zeros(5)
+        ga = np.zeros(4 * self.n) if grad else None
+        gb = np.zeros(4 * self.n) if grad else None
+        gv = np.zeros(2 * self.total_vertices()) if grad_v else None
+        self.lib.ora_eval(self.h, _d(params), res, C.byref(opts), _ptr(terms), _ptr(ga),
+                          _ptr(gb), _ptr(gv))
+        out = {"terms": terms}
+        if grad:
+            out["grad_a"], out["grad_b"] = ga, gb
+        if grad_v:
+            out["grad_v"] = gv
+        return out
+
+    def bins(self, params, res, tile, rho_px=1.0, pad_px=0.0, brute=False):
+        p = np.ascontiguousarray(params, np.float32)
+        f = self.lib.ora_bins_bruteforce if brute else self.lib.ora_bins
+        cap = 1
+        dummy_t, dummy_e = np.zeros(1, np.int32), np.zeros(1, np.int32)
+        cnt = f(self.h, p, res, tile, rho_px, pad_px, dummy_t, dummy_e, 0)
+        t, e = np.zeros(max(cnt, 1), np.int32), np.zeros(max(cnt, 1), np.int32)
+        f(self.h, p, res, tile, rho_px, pad_px, t, e, cnt)
+        del cap
+        return t[:cnt], e[:cnt]
+
+    def bin_radius(self, e):
+        return self.lib.ora_bin_radius(self.h, e)
+
+    def pair_work(self, params, res, opts):
+        return self.lib.ora_pair_work(self.h, _d(params), res, C.byref(opts))
+
+
+def _d(params):
+    return np.ascontiguousarray(params, np.float64).reshape(-1)
+
+
+def adam(params, m, v, g, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, trainable=None,
+         s_min=0.05, s_max=20.0):
+    """One FP64 Adam step in place on copies; returns (params, m, v)."""
+    lib = _load()
+    p, m, v = (np.array(x, np.float64).reshape(-1) for x in (params, m, v))
+    g = _d(g)
+    tr = None if trainable is None else np.ascontiguousarray(trainable, np.uint8)
+    lib.ora_adam(len(p) // 4, p, m, v, g, step, lr, b1, b2, eps, _ptr(tr), s_min, s_max)
+    return p, m, v
