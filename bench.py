@@ -1,0 +1,368 @@
+"""Benchmark of the collage hot path: fwd + bwd + Adam iterations per second.
+
+Workload (one step = one iteration of transform -> bin -> raster + losses -> distribution term ->
+adjoint -> Adam): 1000 mixed elements (60% cubic blobs, 30% convex polygons, 10% open polylines)
+in an annulus container at the 1024^2 level of the 128 -> 256 -> 512 -> 1024 pyramid, padding
+2 px, full loss of Eq. 8.  The timed path is the graph-captured, persistent, autotuned one; the
+same workload is also timed on the plain path (eager launches, one block per tile, 16 px tiles).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): collages are independent problems, so each rank optimises its own collage
+(seeded by its rank) with no collective on the data path; the whole-job value is the iterations of
+all ranks over the slowest rank's time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd+step iters/s at 1024², 1000 elems (batched vs plain); % roofline"
+WORKLOAD = "mixed1000_annulus_1024: 1000 elements (600 cubic blobs, 300 convex polygons, " \
+           "100 open polylines), annulus 0.2/0.48, level 1024^2 of 128/256/512/1024, pad 2 px"
+L2_FLUSH_BYTES = 512 << 20
+# Raster forward work per pixel-segment pair, FP32 operations (FMA = 2): w = p - a (2),
+# w.e (3), *1/|e|^2 (1), clamp (2), q = w - t e (4), |q|^2 (3), min (1), crossing test:
+# b.y <= p.y (1), cross(e, w) (3), its sign (1).
+FLOP_PER_PAIR = 21
+# ncu capture of the raster forward kernel (dram__bytes_read.sum + dram__bytes_write.sum per
+# launch) and the hash of raster.cu it was taken with; the figure is reported only while the
+# source is unchanged.
+NCU_TRAFFIC = {"raster_src_sha1": None, "bytes_per_launch": None}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _raster_src_sha1():
+    with open(os.path.join(ROOT, "paper_2406_04008_gb300", "csrc", "raster.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload(rank=0):
+    from paper_2406_04008_gb300 import workloads as W
+    return W.config_problem(3, collage_index=rank)
+
+
+def _opts(**kw):
+    o = dict(pad_px=2.0, n_levels=4, level_res=[128, 256, 512, 1024],
+             level_iters=[300, 200, 100, 50])
+    o.update(kw)
+    return o
+
+
+def _time_steps(col, steps, flush, torch):
+    """Per-step device time with CUDA events on the launching stream, L2 flushed between steps."""
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        col.step(1)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    return times
+
+
+def run_reference(args):
+    """The oracle (FP64 CPU) on the same workload: the reference arm."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import oracle as O
+    O.build()
+    prob = _workload()
+    sc = O.Scene(prob)
+    o = O.options(pad_px=2.0)
+    q = prob["params0"].astype(np.float64)
+    m, v = np.zeros_like(q), np.zeros_like(q)
+    # one oracle iteration takes seconds: the sample is capped so that the run ends in minutes
+    warm, steps = min(args.warmup, 1), min(args.steps, 20)
+    for i in range(warm):
+        g = sc.eval(q, 1024, o)["grad_a"]
+        q, m, v = O.adam(q, m, v, g, i + 1)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        g = sc.eval(q, 1024, o)["grad_a"]
+        q, m, v = O.adam(q, m, v, g, warm + i + 1)
+    dt = time.perf_counter() - t0
+    val = steps / dt
+    cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "iters/s",
+           "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+           "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": 1024, "elements": 1000},
+           "cpu_baseline": {"value": val, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{steps} full FP64 oracle iterations (forward, "
+                                      "gradient, Adam) of the 1024^2 workload (at most 20 of "
+                                      "the requested steps)"},
+           "e2e": {"value": val, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_profile(args):
+    """A fixed launch sequence for ncu: level 1024^2, W eager warm-up iterations, N eager ones."""
+    import torch
+
+    from paper_2406_04008_gb300 import build
+    build.build()
+    from paper_2406_04008_gb300.collage import Collage
+    col = Collage(_workload(), **_opts(use_graphs=0, persistent=1, tile=args.tile))
+    col.set_level(3)
+    col.step(args.warmup)
+    col.step(args.profile_iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_iters": args.profile_iters, "info": col.info()}))
+    col.close()
+
+
+def cpu_baseline(max_seconds=20.0):
+    """The FP64 oracle as it stands, timed on this host's cores on full 1024^2 iterations."""
+    import numpy as np
+
+    from oracle import oracle as O
+    O.build()
+    prob = _workload()
+    sc = O.Scene(prob)
+    o = O.options(pad_px=2.0)
+    q = prob["params0"].astype(np.float64)
+    m, v = np.zeros_like(q), np.zeros_like(q)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        g = sc.eval(q, 1024, o)["grad_a"]
+        q, m, v = O.adam(q, m, v, g, n + 1)
+        n += 1
+        if time.perf_counter() - t0 > max_seconds or n >= 8:
+            break
+    dt = time.perf_counter() - t0
+    pairs = sc.pair_work(prob["params0"].astype(np.float64), 1024, o)
+    return {"value": n / dt, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full FP64 oracle iterations (forward, gradient, Adam) of the 1024^2 "
+                      f"workload, OpenMP over pixel rows"}, pairs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="for ncu: W warm-up then N eager iterations of the 1024^2 step, no timing")
+    ap.add_argument("--tile", type=int, default=16, help="raster tile of --profile-iters")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile_iters:
+        return run_profile(args)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2406_04008_gb300 import build
+    build.build()
+    from paper_2406_04008_gb300.collage import Collage
+
+    prob = _workload(rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda", dtype=torch.float32)
+
+    # ---- the timed path: graph-captured, persistent, autotuned ----
+    col = Collage(prob, **_opts(use_graphs=1, persistent=1, tile=0))
+    col.set_level(3)
+    tile, _ = col.autotune()
+    col.step(args.warmup)
+    torch.cuda.synchronize()
+    info = col.info()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        times = _time_steps(col, args.steps, flush, torch)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = world * args.steps / total
+
+    # ---- end to end through the host-buffer entry point ----
+    p0 = np.ascontiguousarray(prob["params0"], np.float32)
+    pin_out = torch.from_numpy(p0.copy()).pin_memory()  # params in and out, updated in place
+    pin_loss = torch.empty(5, dtype=torch.float32).pin_memory()
+    import ctypes as C
+    lib, h = col.lib, col.h
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    vp = lambda t: C.c_void_p(t.data_ptr())
+    for _ in range(2):
+        lib.collage_step_host(h, stream, 1, vp(pin_out), vp(pin_out), vp(pin_loss))
+    barrier()
+    e2e_t = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = lib.collage_step_host(h, stream, 1, vp(pin_out), vp(pin_out), vp(pin_loss))
+        e2e_t += time.perf_counter() - t0
+        assert st == 0
+    if world > 1:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = {"value": world * args.steps / e2e_t, "unit": "iters/s",
+           "h2d_bytes_per_step": int(p0.nbytes), "d2h_bytes_per_step": int(p0.nbytes + 20)}
+
+    # ---- per-kernel times at the initial params (for the roofline) ----
+    col.set_params(torch.from_numpy(p0).cuda())
+    stages = col.stage_times(20)
+    col.close()
+
+    # ---- the plain path on the same workload ----
+    plain = Collage(prob, **_opts(use_graphs=0, persistent=0, tile=16))
+    plain.set_level(3)
+    plain.step(args.warmup)
+    torch.cuda.synchronize()
+    ptimes = _time_steps(plain, min(args.steps, 50), flush, torch)
+    plain.close()
+    plain_value = len(ptimes) / sum(ptimes)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    cpu = None
+    pairs = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, pairs = cpu_baseline()
+    roof = None
+    if pairs is not None:
+        t_fwd = stages["raster_fwd"] / 1e3
+        achieved = pairs * FLOP_PER_PAIR / t_fwd / 1e12
+        traffic = NCU_TRAFFIC["bytes_per_launch"] \
+            if NCU_TRAFFIC["raster_src_sha1"] == _raster_src_sha1() else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_raster_fwd",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "work": f"{pairs:.4g} pixel-segment pairs x {FLOP_PER_PAIR} flop",
+                "launch_ms": stages["raster_fwd"]}
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": 1024, "elements": 1000, "tile": tile,
+                      "path": "graph-captured persistent autotuned", "l2": "flushed between steps "
+                      f"({L2_FLUSH_BYTES >> 20} MiB write)", "parallelism": f"replicas x{world}"},
+           "plain": {"value": plain_value, "unit": "iters/s",
+                     "path": "eager launches, one block per tile, 16 px tiles",
+                     "speedup": value / world / plain_value},
+           "stage_ms": {k: round(v, 5) for k, v in stages.items()},
+           "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+           "gpu_launches": info["kernels_per_iter"] * args.steps,
+           "wall_s": t_wall}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/* libcollage -- GB300 (sm_103a) hot path of image-space collage and packing.
+ *
+ * Method: Wang & Lu, "Image-Space Collage and Packing with Differentiable Rendering"
+ * (SIGGRAPH Conference Papers 2025, arXiv 2406.04008).  The collage problem (Sec. 3, Eq. 1) places
+ * n vector items inside a container by optimising one similarity transform per item; items are
+ * transformed (Eq. 2), rasterised with anti-aliased coverage, scored by image-space losses against
+ * the rasterised container (Sec. 4.2, Eqs. 5-8, plus the downward force of Sec. 5) and updated by
+ * gradient steps (Eq. 4, here Adam), coarse to fine over a resolution pyramid (Sec. 4.3).
+ *
+ * Conventions.  Unit-square world coordinates, y down.  Pixel (i, j) of an R x R grid has its
+ * centre at ((j + 1/2)/R, (i + 1/2)/R).  Params are float32 (tx, ty, theta, s) per element, with
+ * world point = R(theta) (s * local point) + (tx, ty).
+ *
+ * Pointers: names starting with d_ are device pointers (e.g. torch CUDA tensors), h_ are host
+ * pointers, everything in collage_problem is host memory that is copied during collage_create.
+ * Streams are cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Errors: every call returns a collage_status; no call throws across the ABI.  Invalid arguments
+ * are detected before any device work.  Errors found on the device during an asynchronous call
+ * (bin-capacity overflow, a bounded wait that gave up) are latched in a device status word and
+ * returned by the next synchronous call on the handle (collage_step, collage_sync).  The message of
+ * the last failure of a handle is returned by collage_last_error.  A handle is not thread-safe.
+ */
+#ifndef COLLAGE_H
+#define COLLAGE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int collage_status;
+#define COLLAGE_OK 0
+#define COLLAGE_ERR_INVALID_ARG (-1) /* an argument failed validation; nothing was run */
+#define COLLAGE_ERR_OOM (-2)         /* a device allocation failed */
+#define COLLAGE_ERR_CUDA (-3)        /* a CUDA runtime call failed (message has the CUDA error) */
+#define COLLAGE_ERR_OVERFLOW (-4)    /* a device capacity was exceeded and could not be regrown */
+#define COLLAGE_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define COLLAGE_ERR_STATE (-6)       /* call not valid in the handle's current state */
+
+typedef struct collage_s* collage_t;
+
+/* Element kinds (Sec. 3 "Vector Representation"; polygons and polylines are the degenerate
+ * cases the paper's examples also use: sketched paths and glyph strokes). */
+#define COLLAGE_CUBIC_PATH 0 /* closed path of N cubic Beziers, 3N control points; curve k uses
+                                points 3k, 3k+1, 3k+2 and 3k+3 (mod 3N) */
+#define COLLAGE_POLYGON 1    /* closed polygon, >= 3 vertices */
+#define COLLAGE_POLYLINE 2   /* open polyline, >= 2 vertices, drawn with half-width stroke_hw */
+
+/* One collage: the problem statement of Sec. 3, Eq. 1 (items G, container C, initial t, r, s). */
+typedef struct {
+  int n_elems;                     /* >= 1 */
+  const int* kind;                 /* [n_elems] COLLAGE_* */
+  const int* pt_off;               /* [n_elems+1] CSR offsets (in points) into pts */
+  const float* pts;                /* [2*pt_off[n_elems]] element-local x, y (unit coordinates) */
+  const float* stroke_hw;          /* [n_elems] stroke half-width of polylines, world units;
+                                      NULL = 0 */
+  const float* params0;            /* [4*n_elems] initial (tx, ty, theta, s); s > 0 */
+  const unsigned char* trainable;  /* [4*n_elems] 1 = optimise this entry; NULL = all */
+  int n_rings;                     /* container: >= 1 closed rings, nonzero fill rule */
+  const int* ring_off;             /* [n_rings+1] CSR offsets (in points) into ring_pts */
+  const float* ring_pts;           /* [2*ring_off[n_rings]] unit coordinates */
+  int grid;                        /* finest grid side in pixels; 0 = level_res[n_levels-1] */
+} collage_problem;
+
+/* Loss weights, renderer and schedule.  collage_default_options fills the paper's values:
+ * alpha, beta, gamma = 3e3, 8e4, 5e-4 (Eq. 8); w_in, w_out = 1, 100 (Sec. 4.2 containment);
+ * dilation widths 5 + 6k pixels (Sec. 4.2 even distribution) with weights k + 1. */
+typedef struct {
+  float alpha, beta, gamma, delta_down; /* Eq. 8 weights and the downward-force weight (0 = off) */
+  float tau;                            /* opacity of the overlap render (Eq. 6), in (0, 1) */
+  float w_in, w_out;                    /* containment penalty inside / outside (Eq. 5) */
+  int n_dilations;                      /* 0..8 dilation kernels of the uniform loss (Eq. 7) */
+  float dil_weight[8];
+  float pad_px;                         /* padding of the overlap render, pixels, >= 0 */
+  float rho_px;                         /* anti-aliasing half-width, pixels, > 0 (default 1) */
+  int segs_per_cubic;                   /* line segments per cubic Bezier (default 16) */
+  int n_levels;                         /* resolution pyramid (Sec. 4.3), 1..8 levels */
+  int level_res[8];                     /* level sides for a problem whose grid equals
+                                           level_res[n_levels-1]; others scale by
+                                           grid / level_res[n_levels-1] */
+  int level_iters[8];                   /* iterations per level for collage_run_schedule */
+  float lr, beta1, beta2, eps;          /* Adam (default 1e-2, 0.9, 0.999, 1e-8) */
+  float s_min, s_max;                   /* scale clamp after each step (default 0.05, 20) */
+  int deterministic;                    /* 1: gradients reduced in a fixed order (bitwise
+                                           reproducible); 0: warp-reduced float atomics */
+  int tile;                             /* raster tile side 8, 16 or 32; 0 = autotune */
+  int persistent;                       /* 1: grid-stride launches sized to the SM count */
+  int use_graphs;                       /* 1: collage_step replays a captured CUDA graph */
+} collage_options;
+
+/* Per-level sizes, for callers that allocate image buffers. */
+typedef struct {
+  int n_probs, n_elems, level, n_levels;
+  int tile;                  /* raster tile side in use */
+  long long total_pixels;    /* sum over problems of res*res at the current level */
+  int pair_capacity;         /* (tile, element) pairs the bin buffers hold */
+  int last_pairs;            /* pairs binned by the last iteration (after a sync) */
+  int kernels_per_iter;      /* kernel launches of one collage_step iteration */
+} collage_info;
+
+/* Fills *opt with the defaults listed above (one level of 1024, 50 iterations). */
+void collage_default_options(collage_options* opt);
+
+/* Validates and copies n_probs problems (n_probs > 1 is the batched form: independent collages of
+ * uneven sizes run in the same launches), flattens cubic paths into segs_per_cubic line segments
+ * each, allocates device memory, and selects level 0.  The current CUDA device is used.
+ * Returns INVALID_ARG (with the offending field in collage_last_error(NULL)) for: n_probs < 1,
+ * n_elems < 1, unknown kind, too few points, NaN/Inf or s <= 0 params, rings with < 3 points,
+ * grid not divisible as the level schedule requires, tile not in {0, 8, 16, 32}. */
+collage_status collage_create(const collage_problem* probs, int n_probs,
+                              const collage_options* opt, collage_t* out);
+
+/* Selects level `level` of the pyramid: rasterises the container into I_C and W at that level's
+ * resolution (Sec. 4 first paragraph, Eq. 5 mask), sizes the bin buffers, and drops captured
+ * graphs.  Synchronises the device.  Params and Adam state carry over (unit coordinates). */
+collage_status collage_set_level(collage_t h, int level);
+
+/* Renders the current params (Eq. 2 and the anti-aliased rasteriser) into d_img_bw (items black
+ * on white, prod(1 - c_i)) and d_img_tau (overlap render 1 - prod(1 - tau c_i^pad)); each is
+ * [total_pixels] float, problems concatenated, row-major; either may be NULL.  Asynchronous. */
+collage_status collage_render(collage_t h, void* stream, float* d_img_bw, float* d_img_tau);
+
+/* One forward + backward pass at the current params: d_loss_terms [n_probs*5] receives
+ * (L_c, L_o, L_u, L_down, L) per problem (Eqs. 5, 6, 7, force, 8) and d_dparams [4*n_elems] the
+ * gradient dL/d(tx, ty, theta, s).  Either may be NULL.  Params are not changed.  Asynchronous. */
+collage_status collage_loss_backward(collage_t h, void* stream, float* d_loss_terms,
+                                     float* d_dparams);
+
+/* n_iters >= 0 iterations of forward + backward + Adam (Eq. 4 with Adam) at the current level,
+ * replaying a captured CUDA graph when use_graphs is set.  Synchronises the stream at the end to
+ * check the device status; a bin overflow regrows the buffers and resumes, so exactly n_iters
+ * successful iterations run. */
+collage_status collage_step(collage_t h, void* stream, int n_iters);
+
+/* Runs every level of the schedule from the current one: set_level + level_iters[l] steps. */
+collage_status collage_run_schedule(collage_t h, void* stream);
+
+/* Host-buffer form of collage_step for callers without device memory: copies h_params_in
+ * [4*n_elems] (NULL = keep) to the device, runs n_iters iterations, copies the params to
+ * h_params_out [4*n_elems] and the last loss terms to h_loss_out [n_probs*5] (either NULL = skip)
+ * and synchronises.  Pinned host memory is faster but not required. */
+collage_status collage_step_host(collage_t h, void* stream, int n_iters, const float* h_params_in,
+                                 float* h_params_out, float* h_loss_out);
+
+/* Loss terms of the most recent iteration, [n_probs*5] (device). */
+collage_status collage_get_loss(collage_t h, void* stream, float* d_loss_terms);
+collage_status collage_get_params(collage_t h, void* stream, float* d_params);
+collage_status collage_set_params(collage_t h, void* stream, const float* d_params);
+
+/* Checkpoint: d_state [12*n_elems] = params, Adam m, Adam v (device); *h_step and *h_level are
+ * the Adam step count and the level.  set_state restores all of it (and sets the level). */
+collage_status collage_get_state(collage_t h, void* stream, float* d_state, int* h_step,
+                                 int* h_level);
+collage_status collage_set_state(collage_t h, void* stream, const float* d_state, int h_step,
+                                 int h_level);
+
+/* The sorted (tile, element) bin list of the last binning: d_tile, d_elem [cap] int32; tiles are
+ * numbered problem after problem, row-major within a problem; *h_n receives the pair count.
+ * Synchronises the stream. */
+collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_elem, int cap,
+                                int* h_n);
+
+/* Device time per stage, averaged over n_iters eager iterations, into h_ms[COLLAGE_N_STAGES]
+ * (see COLLAGE_STAGE_*); the kernels run on `stream`, timed with events on that stream. */
+#define COLLAGE_N_STAGES 8
+#define COLLAGE_STAGE_TRANSFORM 0 /* transform, bbox, tile counts */
+#define COLLAGE_STAGE_BIN 1       /* scan, emit, key sort, tile ranges */
+#define COLLAGE_STAGE_RASTER_FWD 2
+#define COLLAGE_STAGE_DILATE 3    /* distribution term forward and backward */
+#define COLLAGE_STAGE_RASTER_BWD 4
+#define COLLAGE_STAGE_REDUCE 5    /* deterministic gradient reduction */
+#define COLLAGE_STAGE_LOSS 6      /* loss assembly */
+#define COLLAGE_STAGE_ADAM 7
+collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float* h_ms);
+
+/* Times each raster tile size on the current level and keeps the fastest (the autotuner);
+ * h_best_ms receives its iteration time (may be NULL).  Params are restored afterwards. */
+collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
+
+collage_status collage_get_info(collage_t h, collage_info* out);
+/* Waits for the stream and returns any latched device error. */
+collage_status collage_sync(collage_t h, void* stream);
+/* Message of the last error on h (h = NULL: the last collage_create failure of this thread). */
+const char* collage_last_error(collage_t h);
+void collage_destroy(collage_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLLAGE_H */

@@ -1,0 +1,912 @@
+// Host side of libcollage: argument validation, flattening of cubic paths, device buffers, the
+// per-level setup (container raster, bin capacity), the iteration sequence, CUDA-graph capture,
+// stage timing, the tile autotuner and the C ABI of include/collage.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "collage.h"
+#include "internal.h"
+
+using namespace collage;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum Mode { kRender = 0, kLossBwd = 1, kStep = 2 };
+
+}  // namespace
+
+struct collage_s {
+  collage_options opt{};
+  int P = 0, N = 0, V = 0;
+  // host copies of the problem
+  std::vector<int> elem_prob, elem_voff, prob_elem_base, prob_grid, ring_off, prob_ring_base;
+  std::vector<uint8_t> elem_closed;
+  std::vector<float> elem_hw, elem_rbin;
+  std::vector<float2> vloc;
+  std::vector<double> ring_pts;
+  bool has_trainable = false;
+  // level state
+  int level = -1;
+  std::vector<int> res, ntx, tile_base, dtile_base;
+  std::vector<long long> pix_base;
+  int raster_grid = 0;
+  int sms = 1;
+  // device memory
+  Dev d{};
+  size_t pix_cap = 0, tile_cap = 0, dtile_cap = 0, pair_cap = 0, saved_tile = 0;
+  // per-level arrays (device), sized P / P+1
+  int* d_prob_res = nullptr;
+  int* d_prob_ntx = nullptr;
+  int* d_prob_tile_base = nullptr;
+  int* d_prob_dtile_base = nullptr;
+  long long* d_prob_pix_base = nullptr;
+  int* ctl = nullptr;        // device: status, step, total_pairs, pad
+  int* h_ctl = nullptr;      // pinned mirror
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+  std::vector<void*> owned;      // fixed-size allocations
+  std::vector<void*> level_bufs; // per-pixel / per-tile buffers, regrown with the level size
+  std::vector<void*> pair_bufs;  // per-pair buffers, regrown with the bin capacity
+
+  ~collage_s();
+};
+
+namespace {
+
+collage_status fail(collage_t h, collage_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+collage_status cuda_fail(collage_t h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(h, e == cudaErrorMemoryAllocation ? COLLAGE_ERR_OOM : COLLAGE_ERR_CUDA, m);
+}
+
+#define CK(h, expr)                                       \
+  do {                                                    \
+    cudaError_t e_ = (expr);                              \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr); \
+  } while (0)
+
+template <class T>
+cudaError_t dmalloc(std::vector<void*>& list, T*& p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(n, 1));
+  if (e != cudaSuccess) return e;
+  list.push_back(q);
+  p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t upload(std::vector<void*>& list, T*& p, const std::vector<T>& v) {
+  cudaError_t e = dmalloc(list, p, v.size());
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_list(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+bool is_finite_f(float x) { return std::isfinite(x); }
+
+void drop_graph(collage_t h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+}  // namespace
+
+collage_s::~collage_s() {
+  if (graph) cudaGraphExecDestroy(graph);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (h_ctl) cudaFreeHost(h_ctl);
+  free_list(pair_bufs);
+  free_list(level_bufs);
+  free_list(owned);
+}
+
+// --------------------------------------------------------------------------------------------
+// Options and validation
+// --------------------------------------------------------------------------------------------
+extern "C" void collage_default_options(collage_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->alpha = 3e3f;
+  o->beta = 8e4f;
+  o->gamma = 5e-4f;
+  o->delta_down = 0.0f;
+  o->tau = 0.5f;
+  o->w_in = 1.0f;
+  o->w_out = 100.0f;
+  o->n_dilations = 4;
+  for (int k = 0; k < 8; ++k) o->dil_weight[k] = (float)(k + 1);
+  o->pad_px = 0.0f;
+  o->rho_px = 1.0f;
+  o->segs_per_cubic = 16;
+  o->n_levels = 1;
+  o->level_res[0] = 1024;
+  o->level_iters[0] = 50;
+  o->lr = 1e-2f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->s_min = 0.05f;
+  o->s_max = 20.0f;
+  o->deterministic = 0;
+  o->tile = 16;
+  o->persistent = 1;
+  o->use_graphs = 1;
+}
+
+static std::string check_options(const collage_options& o) {
+  if (o.n_levels < 1 || o.n_levels > 8) return "n_levels must be in 1..8";
+  for (int l = 0; l < o.n_levels; ++l) {
+    if (o.level_res[l] < 1) return "level_res[" + std::to_string(l) + "] must be >= 1";
+    if (o.level_iters[l] < 0) return "level_iters[" + std::to_string(l) + "] must be >= 0";
+  }
+  if (!(o.tile == 0 || o.tile == 8 || o.tile == 16 || o.tile == 32)) return "tile must be 0, 8, 16 or 32";
+  if (o.n_dilations < 0 || o.n_dilations > 8) return "n_dilations must be in 0..8";
+  const float f[] = {o.alpha, o.beta, o.gamma, o.delta_down, o.w_in, o.w_out, o.lr, o.eps};
+  for (float x : f)
+    if (!is_finite_f(x)) return "loss weights, penalties, lr and eps must be finite";
+  for (int k = 0; k < o.n_dilations; ++k)
+    if (!is_finite_f(o.dil_weight[k])) return "dil_weight must be finite";
+  if (!(o.rho_px > 0.0f) || !is_finite_f(o.rho_px)) return "rho_px must be > 0";
+  if (!(o.pad_px >= 0.0f) || !is_finite_f(o.pad_px)) return "pad_px must be >= 0";
+  if (!(o.tau > 0.0f && o.tau < 1.0f)) return "tau must be in (0, 1)";
+  if (o.segs_per_cubic < 1 || o.segs_per_cubic > 4096) return "segs_per_cubic must be in 1..4096";
+  if (!(o.beta1 >= 0.0f && o.beta1 < 1.0f) || !(o.beta2 >= 0.0f && o.beta2 < 1.0f)) return "Adam betas must be in [0, 1)";
+  if (!(o.s_min > 0.0f) || !(o.s_max >= o.s_min) || !is_finite_f(o.s_max)) return "need 0 < s_min <= s_max";
+  return "";
+}
+
+static std::string check_problem(const collage_problem& p, int idx, const collage_options& o) {
+  const std::string at = "problem " + std::to_string(idx) + ": ";
+  if (p.n_elems < 1) return at + "n_elems must be >= 1";
+  if (!p.kind || !p.pt_off || !p.pts || !p.params0) return at + "kind, pt_off, pts and params0 are required";
+  if (p.pt_off[0] != 0) return at + "pt_off[0] must be 0";
+  for (int e = 0; e < p.n_elems; ++e) {
+    const int np = p.pt_off[e + 1] - p.pt_off[e];
+    const std::string ae = at + "element " + std::to_string(e) + ": ";
+    switch (p.kind[e]) {
+      case COLLAGE_CUBIC_PATH:
+        if (np < 3 || np % 3) return ae + "a cubic path needs 3N >= 3 control points";
+        break;
+      case COLLAGE_POLYGON:
+        if (np < 3) return ae + "a polygon needs >= 3 points";
+        break;
+      case COLLAGE_POLYLINE:
+        if (np < 2) return ae + "a polyline needs >= 2 points";
+        if (p.stroke_hw && !(p.stroke_hw[e] >= 0.0f && is_finite_f(p.stroke_hw[e]))) return ae + "stroke_hw must be finite and >= 0";
+        break;
+      default:
+        return ae + "unknown kind";
+    }
+    for (int k = 2 * p.pt_off[e]; k < 2 * p.pt_off[e + 1]; ++k)
+      if (!is_finite_f(p.pts[k])) return ae + "points must be finite";
+    const float* q = p.params0 + 4 * e;
+    for (int k = 0; k < 4; ++k)
+      if (!is_finite_f(q[k])) return ae + "params must be finite";
+    if (!(q[3] > 0.0f)) return ae + "scale s must be > 0";
+  }
+  if (p.n_rings < 1 || !p.ring_off || !p.ring_pts) return at + "a container needs >= 1 ring";
+  if (p.ring_off[0] != 0) return at + "ring_off[0] must be 0";
+  for (int r = 0; r < p.n_rings; ++r) {
+    if (p.ring_off[r + 1] - p.ring_off[r] < 3) return at + "each container ring needs >= 3 points";
+    for (int k = 2 * p.ring_off[r]; k < 2 * p.ring_off[r + 1]; ++k)
+      if (!is_finite_f(p.ring_pts[k])) return at + "container points must be finite";
+  }
+  if (p.grid < 0) return at + "grid must be >= 0";
+  const long long g = p.grid ? p.grid : o.level_res[o.n_levels - 1];
+  const long long last = o.level_res[o.n_levels - 1];
+  for (int l = 0; l < o.n_levels; ++l) {
+    if ((g * o.level_res[l]) % last) return at + "grid * level_res[l] must be divisible by level_res[last]";
+    if (g * o.level_res[l] / last < 1) return at + "a level resolution rounds to 0";
+    if (g * o.level_res[l] / last > 32768) return at + "a level resolution exceeds 32768";
+  }
+  return "";
+}
+
+// --------------------------------------------------------------------------------------------
+// Flattening (Sec. 3 "Vector Representation"): curve k of a closed cubic path uses control points
+// 3k, 3k+1, 3k+2, 3k+3 (mod 3N), sampled at t = j / segs (j = 0..segs-1), Bernstein form, double.
+// --------------------------------------------------------------------------------------------
+static void flatten(const collage_problem& p, int e, int spc, std::vector<float2>& out, float& rbin) {
+  const float* pts = p.pts + 2 * p.pt_off[e];
+  const int np = p.pt_off[e + 1] - p.pt_off[e];
+  double rmax = 0.0;
+  for (int k = 0; k < np; ++k) {
+    const double x = pts[2 * k], y = pts[2 * k + 1];
+    rmax = std::max(rmax, std::sqrt(x * x + y * y));
+  }
+  rbin = (float)rmax;
+  if (p.kind[e] != COLLAGE_CUBIC_PATH) {
+    for (int k = 0; k < np; ++k) out.push_back(make_float2(pts[2 * k], pts[2 * k + 1]));
+    return;
+  }
+  for (int k = 0; k < np / 3; ++k) {
+    const float* c[4];
+    for (int i = 0; i < 4; ++i) c[i] = pts + 2 * ((3 * k + i) % np);
+    for (int j = 0; j < spc; ++j) {
+      const double t = (double)j / spc, u = 1.0 - t;
+      const double b[4] = {u * u * u, 3.0 * u * u * t, 3.0 * u * t * t, t * t * t};
+      double x = 0.0, y = 0.0;
+      for (int i = 0; i < 4; ++i) {
+        x += b[i] * c[i][0];
+        y += b[i] * c[i][1];
+      }
+      out.push_back(make_float2((float)x, (float)y));
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// Level setup
+// --------------------------------------------------------------------------------------------
+static int sort_passes(int total_tiles) {
+  unsigned m = total_tiles > 1 ? (unsigned)(total_tiles - 1) : 1u;
+  int bits = 0;
+  while (m) {
+    ++bits;
+    m >>= 1;
+  }
+  return std::max(1, (bits + kSortBits - 1) / kSortBits);
+}
+
+static collage_status ensure_pairs(collage_t h, size_t cap) {
+  const size_t tt = (size_t)h->d.tile * h->d.tile;
+  if (cap <= h->pair_cap && tt == h->saved_tile) return COLLAGE_OK;
+  drop_graph(h);
+  CK(h, cudaDeviceSynchronize());
+  free_list(h->pair_bufs);
+  h->pair_cap = 0;
+  Dev& d = h->d;
+  CK(h, dmalloc(h->pair_bufs, d.keys0, cap));
+  CK(h, dmalloc(h->pair_bufs, d.vals0, cap));
+  CK(h, dmalloc(h->pair_bufs, d.keys1, cap));
+  CK(h, dmalloc(h->pair_bufs, d.vals1, cap));
+  CK(h, dmalloc(h->pair_bufs, d.elem_of, cap));
+  CK(h, dmalloc(h->pair_bufs, d.partial, cap));
+  CK(h, dmalloc(h->pair_bufs, d.saved, cap * tt));
+  h->pair_cap = cap;
+  h->saved_tile = tt;
+  d.cap = (int)std::min<size_t>(cap, 0x7fffffff);
+  d.sort_blocks = (int)std::min<size_t>(std::max<size_t>((cap + 4095) / 4096, 1), (size_t)h->sms);
+  return COLLAGE_OK;
+}
+
+static collage_status read_ctl(collage_t h, cudaStream_t s) {
+  CK(h, cudaMemcpyAsync(h->h_ctl, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  return COLLAGE_OK;
+}
+
+static collage_status setup_level(collage_t h, int level) {
+  drop_graph(h);
+  const collage_options& o = h->opt;
+  Dev& d = h->d;
+  const int T = d.tile;
+  const long long last = o.level_res[o.n_levels - 1];
+  h->res.assign(h->P, 0);
+  h->ntx.assign(h->P, 0);
+  h->tile_base.assign(h->P + 1, 0);
+  h->dtile_base.assign(h->P + 1, 0);
+  h->pix_base.assign(h->P + 1, 0);
+  for (int p = 0; p < h->P; ++p) {
+    const long long g = h->prob_grid[p];
+    const int r = (int)(g * o.level_res[level] / last);
+    h->res[p] = r;
+    h->ntx[p] = (r + T - 1) / T;
+    h->tile_base[p + 1] = h->tile_base[p] + h->ntx[p] * h->ntx[p];
+    const int nd = (r + 31) / 32;
+    h->dtile_base[p + 1] = h->dtile_base[p] + nd * nd;
+    h->pix_base[p + 1] = h->pix_base[p] + (long long)r * r;
+  }
+  d.total_tiles = h->tile_base[h->P];
+  d.total_dtiles = h->dtile_base[h->P];
+  d.total_pix = h->pix_base[h->P];
+  d.n_sort_passes = sort_passes(d.total_tiles);
+  if ((size_t)d.total_pix > h->pix_cap || (size_t)d.total_tiles > h->tile_cap ||
+      (size_t)d.total_dtiles > h->dtile_cap) {
+    // regrow every level-sized buffer
+    CK(h, cudaDeviceSynchronize());
+    free_list(h->level_bufs);
+    const size_t np = (size_t)d.total_pix, nt = (size_t)d.total_tiles, nd = (size_t)d.total_dtiles;
+    CK(h, dmalloc(h->level_bufs, d.covc, np));
+    CK(h, dmalloc(h->level_bufs, d.img_I, np));
+    CK(h, dmalloc(h->level_bufs, d.img_Pt, np));
+    CK(h, dmalloc(h->level_bufs, d.gOu, np));
+    CK(h, dmalloc(h->level_bufs, d.dil_m, np));
+    CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
+    CK(h, dmalloc(h->level_bufs, d.range, nt));
+    CK(h, dmalloc(h->level_bufs, d.lossA, nt));
+    CK(h, dmalloc(h->level_bufs, d.lossU, nd));
+    h->pix_cap = np;
+    h->tile_cap = nt;
+    h->dtile_cap = nd;
+  }
+  CK(h, cudaMemcpy(h->d_prob_res, h->res.data(), sizeof(int) * h->P, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->d_prob_ntx, h->ntx.data(), sizeof(int) * h->P, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->d_prob_tile_base, h->tile_base.data(), sizeof(int) * (h->P + 1), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->d_prob_dtile_base, h->dtile_base.data(), sizeof(int) * (h->P + 1), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->d_prob_pix_base, h->pix_base.data(), sizeof(long long) * (h->P + 1), cudaMemcpyHostToDevice));
+  CK(h, prepare_dilate(o.n_dilations));
+  cudaStream_t s = h->cap_stream;
+  CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));  // clear latched status
+  CK(h, launch_container(d, s));
+  // size the pair buffers from the current params: count with an unbounded capacity
+  Dev probe = d;
+  probe.cap = 0x7fffffff;
+  CK(h, launch_transform(probe, s, false));
+  CK(h, launch_scan(probe, s));
+  collage_status st = read_ctl(h, s);
+  if (st) return st;
+  if (h->h_ctl[0] & kStatusBadParam) return fail(h, COLLAGE_ERR_INVALID_ARG, "params are not finite or s <= 0");
+  const size_t need = (size_t)h->h_ctl[2];
+  st = ensure_pairs(h, std::max<size_t>(need + need / 2 + 256, 1024));
+  if (st) return st;
+  h->raster_grid = o.persistent ? std::min(d.total_tiles, raster_fwd_max_grid(T)) : d.total_tiles;
+  h->level = level;
+  return COLLAGE_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// One iteration: transform -> bin -> raster fwd (+ losses) -> dilation -> adjoint -> loss -> Adam
+// --------------------------------------------------------------------------------------------
+static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* out_bw, float* out_tau,
+                                cudaEvent_t* ev = nullptr) {
+  const Dev& d = h->d;
+  const bool bwd = mode != kRender;
+  const bool dil = bwd && d.L.gamma != 0.0f && d.L.n_dil > 0;
+  cudaError_t e;
+#define STEP_(x)                      \
+  if ((e = (x)) != cudaSuccess) return e;
+#define MARK_(i) \
+  if (ev) STEP_(cudaEventRecord(ev[i], s));
+  MARK_(0);
+  STEP_(launch_transform(d, s, bwd && !d.deterministic));
+  MARK_(1);
+  STEP_(launch_scan(d, s));
+  STEP_(launch_bin(d, s));
+  MARK_(2);
+  STEP_(launch_raster_fwd(d, s, h->raster_grid, out_bw, out_tau));
+  MARK_(3);
+  if (dil) {
+    STEP_(launch_dilate(d, s, false));
+    STEP_(launch_dilate(d, s, true));
+  }
+  MARK_(4);
+  if (bwd) STEP_(launch_raster_bwd(d, s, h->raster_grid));
+  MARK_(5);
+  if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
+  MARK_(6);
+  if (bwd) STEP_(launch_loss(d, s, mode == kStep));
+  MARK_(7);
+  if (mode == kStep) STEP_(launch_adam(d, s));
+  MARK_(8);
+#undef STEP_
+#undef MARK_
+  return cudaSuccess;
+}
+
+static collage_status ensure_graph(collage_t h) {
+  if (h->graph) return COLLAGE_OK;
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_iter(h, h->cap_stream, kStep, nullptr, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, e, "capture");
+  }
+  CK(h, e2);
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(h, e);
+  return COLLAGE_OK;
+}
+
+// After a batch of work: check the latched status; grow the pair buffers when the last binning
+// used more than 3/4 of them.  Returns OVERFLOW if the batch overflowed (caller re-runs).
+static collage_status check_and_grow(collage_t h, cudaStream_t s, bool* overflowed) {
+  *overflowed = false;
+  collage_status st = read_ctl(h, s);
+  if (st) return st;
+  const int status = h->h_ctl[0];
+  const size_t need = (size_t)h->h_ctl[2];
+  if (status & kStatusInternal) return fail(h, COLLAGE_ERR_STATE, "internal bounds check failed");
+  if (status & kStatusBadParam) {
+    CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));
+    return fail(h, COLLAGE_ERR_INVALID_ARG, "params became non-finite or s <= 0");
+  }
+  if (status & kStatusOverflow) {
+    *overflowed = true;
+    CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));
+    CK(h, cudaStreamSynchronize(s));
+    if (need + need / 2 + 256 > 0x7fffffff / 2) return fail(h, COLLAGE_ERR_OVERFLOW, "bin pairs exceed 2^30");
+    return ensure_pairs(h, need + need / 2 + 256);
+  }
+  if (need * 4 > h->pair_cap * 3) return ensure_pairs(h, need + need / 2 + 256);
+  return COLLAGE_OK;
+}
+
+static collage_status run_checked(collage_t h, cudaStream_t s, int mode, float* out_bw, float* out_tau) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    CK(h, enqueue_iter(h, s, mode, out_bw, out_tau));
+    bool over = false;
+    collage_status st = check_and_grow(h, s, &over);
+    if (st) return st;
+    if (!over) return COLLAGE_OK;
+  }
+  return fail(h, COLLAGE_ERR_OVERFLOW, "bin capacity kept overflowing");
+}
+
+// --------------------------------------------------------------------------------------------
+// C ABI
+// --------------------------------------------------------------------------------------------
+extern "C" collage_status collage_create(const collage_problem* probs, int n_probs,
+                                         const collage_options* opt, collage_t* out) {
+  if (!out) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!probs || n_probs < 1) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "need n_probs >= 1 problems");
+  collage_options o;
+  if (opt) o = *opt;
+  else collage_default_options(&o);
+  std::string m = check_options(o);
+  if (!m.empty()) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "options: " + m);
+  long long total_e = 0;
+  for (int p = 0; p < n_probs; ++p) {
+    m = check_problem(probs[p], p, o);
+    if (!m.empty()) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, m);
+    total_e += probs[p].n_elems;
+  }
+  if (total_e > (1LL << 26)) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "too many elements");
+
+  collage_t h = new collage_s();
+  h->opt = o;
+  if (h->opt.tile == 0) h->opt.tile = 16;  // the autotuner may change it later
+  h->P = n_probs;
+  h->prob_elem_base.push_back(0);
+  h->prob_ring_base.push_back(0);
+  h->ring_off.push_back(0);
+  std::vector<float4> q;
+  std::vector<uchar4> tr;
+  for (int p = 0; p < n_probs; ++p) {
+    const collage_problem& pr = probs[p];
+    if (pr.trainable) h->has_trainable = true;
+  }
+  for (int p = 0; p < n_probs; ++p) {
+    const collage_problem& pr = probs[p];
+    for (int e = 0; e < pr.n_elems; ++e) {
+      h->elem_prob.push_back(p);
+      h->elem_voff.push_back((int)h->vloc.size());
+      h->elem_closed.push_back(pr.kind[e] == COLLAGE_POLYLINE ? 0 : 1);
+      h->elem_hw.push_back(pr.kind[e] == COLLAGE_POLYLINE && pr.stroke_hw ? pr.stroke_hw[e] : 0.0f);
+      float rb = 0.0f;
+      flatten(pr, e, o.segs_per_cubic, h->vloc, rb);
+      h->elem_rbin.push_back(rb);
+      const float* pp = pr.params0 + 4 * e;
+      q.push_back(make_float4(pp[0], pp[1], pp[2], pp[3]));
+      if (h->has_trainable) {
+        const unsigned char* t = pr.trainable ? pr.trainable + 4 * e : nullptr;
+        tr.push_back(t ? make_uchar4(t[0] != 0, t[1] != 0, t[2] != 0, t[3] != 0) : make_uchar4(1, 1, 1, 1));
+      }
+    }
+    h->prob_elem_base.push_back((int)h->elem_prob.size());
+    for (int r = 0; r < pr.n_rings; ++r) {
+      for (int k = pr.ring_off[r]; k < pr.ring_off[r + 1]; ++k) {
+        h->ring_pts.push_back(pr.ring_pts[2 * k]);
+        h->ring_pts.push_back(pr.ring_pts[2 * k + 1]);
+      }
+      h->ring_off.push_back((int)(h->ring_pts.size() / 2));
+    }
+    h->prob_ring_base.push_back((int)h->ring_off.size() - 1);
+    h->prob_grid.push_back(pr.grid ? pr.grid : o.level_res[o.n_levels - 1]);
+  }
+  h->elem_voff.push_back((int)h->vloc.size());
+  h->N = (int)h->elem_prob.size();
+  h->V = (int)h->vloc.size();
+
+  collage_status st = COLLAGE_OK;
+  auto bail = [&](collage_status s2) {
+    g_create_error = h->err;
+    delete h;
+    return s2;
+  };
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) {
+    cuda_fail(h, ce, "cudaGetDevice");
+    return bail(COLLAGE_ERR_CUDA);
+  }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (h->sms < 1) h->sms = 1;
+  Dev& d = h->d;
+  d.n_elems = h->N;
+  d.n_probs = h->P;
+  d.tile = h->opt.tile;
+  d.deterministic = o.deterministic ? 1 : 0;
+  d.lr = o.lr;
+  d.b1 = o.beta1;
+  d.b2 = o.beta2;
+  d.eps = o.eps;
+  d.s_min = o.s_min;
+  d.s_max = o.s_max;
+  d.L.alpha = o.alpha;
+  d.L.beta = o.beta;
+  d.L.gamma = o.gamma;
+  d.L.delta = o.delta_down;
+  d.L.tau = o.tau;
+  d.L.w_in = o.w_in;
+  d.L.w_out = o.w_out;
+  d.L.n_dil = o.n_dilations;
+  for (int k = 0; k < kMaxDil; ++k) d.L.dil_w[k] = o.dil_weight[k];
+  d.L.pad_px = o.pad_px;
+  d.L.rho_px = o.rho_px;
+#define CKC(x)                                   \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) {                     \
+      return bail(cuda_fail(h, e_, #x));         \
+    }                                            \
+  } while (0)
+  int* p_elem_prob;
+  int* p_elem_voff;
+  uint8_t* p_closed;
+  float* p_hw;
+  float* p_rbin;
+  float2* p_vloc;
+  int* p_peb;
+  double* p_ring;
+  int* p_roff;
+  int* p_prb;
+  CKC(upload(h->owned, p_elem_prob, h->elem_prob));
+  CKC(upload(h->owned, p_elem_voff, h->elem_voff));
+  CKC(upload(h->owned, p_closed, h->elem_closed));
+  CKC(upload(h->owned, p_hw, h->elem_hw));
+  CKC(upload(h->owned, p_rbin, h->elem_rbin));
+  CKC(upload(h->owned, p_vloc, h->vloc));
+  CKC(upload(h->owned, p_peb, h->prob_elem_base));
+  CKC(upload(h->owned, p_ring, h->ring_pts));
+  CKC(upload(h->owned, p_roff, h->ring_off));
+  CKC(upload(h->owned, p_prb, h->prob_ring_base));
+  d.elem_prob = p_elem_prob;
+  d.elem_voff = p_elem_voff;
+  d.elem_closed = p_closed;
+  d.elem_hw = p_hw;
+  d.elem_rbin = p_rbin;
+  d.vloc = p_vloc;
+  d.prob_elem_base = p_peb;
+  d.ring_pts = p_ring;
+  d.ring_off = p_roff;
+  d.prob_ring_base = p_prb;
+  CKC(upload(h->owned, d.q, q));
+  CKC(dmalloc(h->owned, d.m, h->N));
+  CKC(dmalloc(h->owned, d.v, h->N));
+  CKC(cudaMemset(d.m, 0, sizeof(float4) * h->N));
+  CKC(cudaMemset(d.v, 0, sizeof(float4) * h->N));
+  if (h->has_trainable) {
+    uchar4* p_tr;
+    CKC(upload(h->owned, p_tr, tr));
+    d.trainable = p_tr;
+  }
+  CKC(dmalloc(h->owned, d.vrel, h->V));
+  CKC(dmalloc(h->owned, d.tpx, h->N));
+  CKC(dmalloc(h->owned, d.bbox, h->N));
+  CKC(dmalloc(h->owned, d.rect, h->N));
+  CKC(dmalloc(h->owned, d.cnt, h->N));
+  CKC(dmalloc(h->owned, d.off, h->N + 1));
+  CKC(dmalloc(h->owned, d.dq, h->N));
+  CKC(cudaMemset(d.dq, 0, sizeof(float4) * h->N));
+  CKC(dmalloc(h->owned, d.loss_terms, 5 * h->P));
+  CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
+  CKC(dmalloc(h->owned, h->ctl, 4));
+  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 4));
+  d.status = h->ctl;
+  d.step = h->ctl + 1;
+  d.total_pairs = h->ctl + 2;
+  CKC(dmalloc(h->owned, d.sort_hist, (size_t)kSortBins * h->sms));
+  CKC(dmalloc(h->owned, h->d_prob_res, h->P));
+  CKC(dmalloc(h->owned, h->d_prob_ntx, h->P));
+  CKC(dmalloc(h->owned, h->d_prob_tile_base, h->P + 1));
+  CKC(dmalloc(h->owned, h->d_prob_dtile_base, h->P + 1));
+  CKC(dmalloc(h->owned, h->d_prob_pix_base, h->P + 1));
+  d.prob_res = h->d_prob_res;
+  d.prob_ntx = h->d_prob_ntx;
+  d.prob_tile_base = h->d_prob_tile_base;
+  d.prob_dtile_base = h->d_prob_dtile_base;
+  d.prob_pix_base = h->d_prob_pix_base;
+  CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
+  CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+#undef CKC
+  st = setup_level(h, 0);
+  if (st) return bail(st);
+  *out = h;
+  return COLLAGE_OK;
+}
+
+extern "C" void collage_destroy(collage_t h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  delete h;
+}
+
+extern "C" const char* collage_last_error(collage_t h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" collage_status collage_set_level(collage_t h, int level) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  if (level < 0 || level >= h->opt.n_levels) return fail(h, COLLAGE_ERR_INVALID_ARG, "level out of range");
+  CK(h, cudaDeviceSynchronize());
+  return setup_level(h, level);
+}
+
+extern "C" collage_status collage_render(collage_t h, void* stream, float* d_img_bw, float* d_img_tau) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  return run_checked(h, (cudaStream_t)stream, kRender, d_img_bw, d_img_tau);
+}
+
+extern "C" collage_status collage_loss_backward(collage_t h, void* stream, float* d_loss_terms,
+                                                float* d_dparams) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  collage_status st = run_checked(h, s, kLossBwd, nullptr, nullptr);
+  if (st) return st;
+  if (d_loss_terms)
+    CK(h, cudaMemcpyAsync(d_loss_terms, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToDevice, s));
+  if (d_dparams) CK(h, launch_copy_grad(h->d, s, d_dparams));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_step(collage_t h, void* stream, int n_iters) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  if (n_iters < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "n_iters must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  int remaining = n_iters;
+  for (int attempt = 0; remaining > 0 && attempt < 8; ++attempt) {
+    collage_status st = read_ctl(h, s);
+    if (st) return st;
+    const int step0 = h->h_ctl[1];
+    if (h->opt.use_graphs) {
+      st = ensure_graph(h);
+      if (st) return st;
+      for (int i = 0; i < remaining; ++i) CK(h, cudaGraphLaunch(h->graph, s));
+    } else {
+      for (int i = 0; i < remaining; ++i) CK(h, enqueue_iter(h, s, kStep, nullptr, nullptr));
+    }
+    bool over = false;
+    st = check_and_grow(h, s, &over);
+    if (st) return st;
+    st = read_ctl(h, s);
+    if (st) return st;
+    remaining -= h->h_ctl[1] - step0;
+    if (!over && remaining > 0) return fail(h, COLLAGE_ERR_STATE, "iterations went missing");
+  }
+  if (remaining > 0) return fail(h, COLLAGE_ERR_OVERFLOW, "bin capacity kept overflowing");
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_run_schedule(collage_t h, void* stream) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  for (int l = std::max(h->level, 0); l < h->opt.n_levels; ++l) {
+    if (l != h->level) {
+      collage_status st = collage_set_level(h, l);
+      if (st) return st;
+    }
+    collage_status st = collage_step(h, stream, h->opt.level_iters[l]);
+    if (st) return st;
+  }
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_iters,
+                                            const float* h_params_in, float* h_params_out,
+                                            float* h_loss_out) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h_params_in)
+    CK(h, cudaMemcpyAsync(h->d.q, h_params_in, sizeof(float4) * h->N, cudaMemcpyHostToDevice, s));
+  collage_status st = collage_step(h, stream, n_iters);
+  if (st) return st;
+  if (h_params_out)
+    CK(h, cudaMemcpyAsync(h_params_out, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToHost, s));
+  if (h_loss_out)
+    CK(h, cudaMemcpyAsync(h_loss_out, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_loss(collage_t h, void* stream, float* d_loss_terms) {
+  if (!h || !d_loss_terms) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, cudaMemcpyAsync(d_loss_terms, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToDevice,
+                        (cudaStream_t)stream));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_params(collage_t h, void* stream, float* d_params) {
+  if (!h || !d_params) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, cudaMemcpyAsync(d_params, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_set_params(collage_t h, void* stream, const float* d_params) {
+  if (!h || !d_params) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, cudaMemcpyAsync(h->d.q, d_params, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_state(collage_t h, void* stream, float* d_state, int* h_step,
+                                            int* h_level) {
+  if (!h || !d_state) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = sizeof(float4) * h->N;
+  CK(h, cudaMemcpyAsync(d_state, h->d.q, n, cudaMemcpyDeviceToDevice, s));
+  CK(h, cudaMemcpyAsync((char*)d_state + n, h->d.m, n, cudaMemcpyDeviceToDevice, s));
+  CK(h, cudaMemcpyAsync((char*)d_state + 2 * n, h->d.v, n, cudaMemcpyDeviceToDevice, s));
+  collage_status st = read_ctl(h, s);
+  if (st) return st;
+  if (h_step) *h_step = h->h_ctl[1];
+  if (h_level) *h_level = h->level;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_set_state(collage_t h, void* stream, const float* d_state, int h_step,
+                                            int h_level) {
+  if (!h || !d_state) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  if (h_step < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "step must be >= 0");
+  if (h_level != h->level) {
+    collage_status st = collage_set_level(h, h_level);
+    if (st) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = sizeof(float4) * h->N;
+  CK(h, cudaMemcpyAsync(h->d.q, d_state, n, cudaMemcpyDeviceToDevice, s));
+  CK(h, cudaMemcpyAsync(h->d.m, (const char*)d_state + n, n, cudaMemcpyDeviceToDevice, s));
+  CK(h, cudaMemcpyAsync(h->d.v, (const char*)d_state + 2 * n, n, cudaMemcpyDeviceToDevice, s));
+  h->h_ctl[1] = h_step;
+  CK(h, cudaMemcpyAsync(h->d.step, &h->h_ctl[1], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(h, cudaStreamSynchronize(s));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_elem, int cap,
+                                           int* h_n) {
+  if (!h || !h_n) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  collage_status st = read_ctl(h, s);
+  if (st) return st;
+  const int n = h->h_ctl[2];
+  *h_n = n;
+  if (!d_tile && !d_elem) return COLLAGE_OK;
+  if (cap < n) return fail(h, COLLAGE_ERR_INVALID_ARG, "cap is smaller than the pair count");
+  std::vector<uint32_t> k(n), v(n);
+  std::vector<int> eo(n), te(n), ee(n);
+  if (n) {
+    CK(h, cudaMemcpy(k.data(), sorted_keys(h->d), sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(v.data(), sorted_vals(h->d), sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(eo.data(), h->d.elem_of, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  }
+  for (int i = 0; i < n; ++i) {
+    te[i] = (int)k[i];
+    ee[i] = eo[v[i]];
+  }
+  if (d_tile && n) CK(h, cudaMemcpy(d_tile, te.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  if (d_elem && n) CK(h, cudaMemcpy(d_elem, ee.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float* h_ms) {
+  if (!h || !h_ms || n_iters < 1) return fail(h, COLLAGE_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  constexpr int NE = 9;
+  cudaEvent_t ev[NE];
+  for (int i = 0; i < NE; ++i) CK(h, cudaEventCreate(&ev[i]));
+  double acc[NE - 1] = {0};
+  collage_status st = COLLAGE_OK;
+  for (int it = 0; it < n_iters && !st; ++it) {
+    cudaError_t e = enqueue_iter(h, s, kStep, nullptr, nullptr, ev);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h, e, "enqueue");
+      break;
+    }
+    e = cudaEventSynchronize(ev[NE - 1]);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h, e, "sync");
+      break;
+    }
+    for (int i = 0; i < NE - 1; ++i) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+  }
+  for (int i = 0; i < NE; ++i) cudaEventDestroy(ev[i]);
+  if (st) return st;
+  // events: 0 transform 1 bin 2 raster_fwd 3 dilate 4 raster_bwd 5 reduce 6 loss 7 adam 8
+  for (int i = 0; i < COLLAGE_N_STAGES; ++i) h_ms[i] = (float)(acc[i] / n_iters);
+  bool over = false;
+  return check_and_grow(h, s, &over);
+}
+
+extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int tiles[3] = {8, 16, 32};
+  float best = 1e30f;
+  int best_tile = h->d.tile;
+  cudaEvent_t a, b;
+  CK(h, cudaEventCreate(&a));
+  CK(h, cudaEventCreate(&b));
+  for (int T : tiles) {
+    CK(h, cudaDeviceSynchronize());
+    h->d.tile = T;
+    collage_status st = setup_level(h, h->level);
+    if (st) return st;
+    for (int i = 0; i < 2; ++i) {
+      st = run_checked(h, s, kLossBwd, nullptr, nullptr);
+      if (st) return st;
+    }
+    CK(h, cudaEventRecord(a, s));
+    const int reps = 10;
+    for (int i = 0; i < reps; ++i) CK(h, enqueue_iter(h, s, kLossBwd, nullptr, nullptr));
+    CK(h, cudaEventRecord(b, s));
+    CK(h, cudaEventSynchronize(b));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    ms /= reps;
+    if (ms < best) {
+      best = ms;
+      best_tile = T;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CK(h, cudaDeviceSynchronize());
+  h->d.tile = best_tile;
+  h->opt.tile = best_tile;
+  collage_status st = setup_level(h, h->level);
+  if (st) return st;
+  if (h_best_ms) *h_best_ms = best;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
+  if (!h || !out) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  out->n_probs = h->P;
+  out->n_elems = h->N;
+  out->level = h->level;
+  out->n_levels = h->opt.n_levels;
+  out->tile = h->d.tile;
+  out->total_pixels = h->d.total_pix;
+  out->pair_capacity = h->d.cap;
+  out->last_pairs = h->h_ctl ? h->h_ctl[2] : 0;
+  // transform, scan, emit, 3 per radix pass, ranges, raster fwd, (2 dilation), raster bwd,
+  // (gradient reduce), loss, Adam
+  const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
+  out->kernels_per_iter = 3 + 3 * h->d.n_sort_passes + 1 + 1 + (dil ? 2 : 0) + 1 +
+                          (h->d.deterministic ? 1 : 0) + 2;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_sync(collage_t h, void* stream) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  bool over = false;
+  collage_status st = check_and_grow(h, (cudaStream_t)stream, &over);
+  if (st) return st;
+  if (over) return fail(h, COLLAGE_ERR_OVERFLOW, "the last asynchronous call overflowed the bins; it was regrown, repeat the call");
+  return COLLAGE_OK;
+}

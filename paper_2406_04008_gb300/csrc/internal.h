@@ -1,0 +1,120 @@
+// Internal device-side layout of libcollage (not part of the C ABI).
+//
+// HBM layout, all problems of a handle concatenated:
+//   per element g (SoA):   prob, vertex offset, closed flag, stroke half-width, bin radius,
+//                          params q / Adam m, v (float4), world translation in pixels (hi, lo),
+//                          pixel bbox, tile rectangle, pair count and offset, gradient dq
+//   per flattened vertex:  local position (unit coords), per-iteration position relative to the
+//                          element translation in pixels (float, rounded from double)
+//   per (tile, element) pair, capacity `cap`: sort keys / values (ping-pong), element of each
+//                          emitted pair, deterministic gradient partials, and per pixel of the
+//                          tile the signed distance + closest segment saved by the forward pass
+//   per pixel (level):     container coverage, Ihat, prod(1 - tau c^pad), uniform-loss scratch
+//   per tile:              [begin, end) into the sorted pairs, loss partials
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace collage {
+
+constexpr int kMaxDil = 8;
+constexpr int kSortBits = 8;            // radix digit
+constexpr int kSortBins = 1 << kSortBits;
+constexpr int kSortThreads = 256;
+constexpr int kStatusOverflow = 1;      // device status bits
+constexpr int kStatusBadParam = 2;
+constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bug)
+
+struct LossParams {
+  float alpha, beta, gamma, delta;
+  float tau, w_in, w_out;
+  int n_dil;
+  float dil_w[kMaxDil];
+  float pad_px, rho_px;
+};
+
+struct Dev {
+  // ---- problem (fixed at create) ----
+  int n_elems, n_probs;
+  const int* elem_prob;
+  const int* elem_voff;         // [n+1]
+  const uint8_t* elem_closed;
+  const float* elem_hw;         // unit coords
+  const float* elem_rbin;       // bin radius (largest |control point|), float
+  const float2* vloc;           // flattened local vertices, unit coords
+  const int* prob_elem_base;    // [P+1]
+  const double* ring_pts;       // container rings, unit coords (double)
+  const int* ring_off;          // [total rings + 1]
+  const int* prob_ring_base;    // [P+1] into ring_off
+  // ---- level ----
+  const int* prob_res;          // [P]
+  const int* prob_ntx;          // [P] tiles per side
+  const int* prob_tile_base;    // [P+1]
+  const long long* prob_pix_base;  // [P+1]
+  const int* prob_dtile_base;   // [P+1] dilation tiles
+  int total_tiles, total_dtiles;
+  long long total_pix;
+  int tile;                     // raster tile side
+  int n_sort_passes;
+  // ---- params / optimiser ----
+  float4* q;
+  float4* m;
+  float4* v;
+  const uchar4* trainable;      // may be null
+  float lr, b1, b2, eps, s_min, s_max;
+  // ---- per iteration ----
+  float2* vrel;                 // [V] px, relative to the element translation
+  float4* tpx;                  // [n] translation in px: (hi.x, hi.y, lo.x, lo.y)
+  float4* bbox;                 // [n] px bbox grown by the coverage margin
+  int4* rect;                   // [n] tile rectangle (tx0, ty0, tx1, ty1), empty if tx1 < tx0
+  int* cnt;                     // [n] pairs per element
+  int* off;                     // [n+1] exclusive scan of cnt
+  int* total_pairs;             // [1]
+  int cap;                      // pair capacity
+  uint32_t* keys0;
+  uint32_t* vals0;
+  uint32_t* keys1;
+  uint32_t* vals1;
+  int* elem_of;                 // [cap] emit position -> element
+  uint32_t* sort_hist;          // [kSortBins * sort_blocks]
+  int sort_blocks;
+  uint2* range;                 // [total_tiles] [begin, end) into the sorted pairs
+  float2* saved;                // [cap * tile*tile] (sd px, closest segment as int bits)
+  float* covc;                  // [pix] container coverage
+  float* img_I;                 // [pix] Ihat = prod(1 - c)
+  float* img_Pt;                // [pix] prod(1 - tau c^pad)
+  float* gOu;                   // [pix] dL_u/dO
+  float* dil_m;                 // [pix] M_C (1 - O), masked per kernel by dil_mask
+  uint8_t* dil_mask;            // [pix] bit k: B_k < 1
+  float4* lossA;                // [total_tiles] (sum W(I-Ic)^2, sum relu(A-tau), sum O(1-y), 0)
+  float* lossU;                 // [total_dtiles] weighted uniform-loss partial
+  float4* dq;                   // [n] gradient
+  float4* partial;              // [cap] deterministic gradient partials, at emit position
+  float* loss_terms;            // [P*5]
+  int* status;                  // [1]
+  int* step;                    // [1] Adam step count
+  LossParams L;
+  int deterministic;
+};
+
+// The sorted keys / values after the last pass.
+__host__ __device__ inline const uint32_t* sorted_keys(const Dev& d) { return (d.n_sort_passes & 1) ? d.keys1 : d.keys0; }
+__host__ __device__ inline const uint32_t* sorted_vals(const Dev& d) { return (d.n_sort_passes & 1) ? d.vals1 : d.vals0; }
+
+// ---- launchers (each enqueues on `s`, returns the launch error) ----
+cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
+cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // pair counts -> offsets, total
+cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit, sort, ranges
+cudaError_t launch_container(const Dev& d, cudaStream_t s);
+cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int grid, float* out_bw,
+                              float* out_tau);
+cudaError_t prepare_dilate(int n_dil);  // sets dynamic shared memory limits (not capturable)
+cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward);
+cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int grid);
+cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s);
+cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step);
+cudaError_t launch_adam(const Dev& d, cudaStream_t s);
+cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
+int raster_fwd_max_grid(int tile);  // resident blocks for a persistent grid (per SM)
+
+}  // namespace collage

@@ -1,0 +1,309 @@
+// Even-distribution term (Eq. 7), loss assembly (Eq. 8), deterministic gradient reduction and the
+// Adam update that stands in for the descent step of Eq. 4.
+//
+// Eq. 7 as implemented: K box kernels of widths 5 + 6k pixels (k = 0..K-1) dilate the occupancy
+// O = 1 - Ihat; D_k = min(1, B_k) with B_k the zero-padded box sum; the term sums
+// w_k M_C (1 - O) (1 - D_k) over the container.  Its adjoint is
+//   dL_u/dO(q) = sum_k w_k [ -M_C(q)(1 - D_k(q)) - sum_{p in box_k(q)} M_C(p)(1 - O(p)) [B_k(p) < 1] ].
+// Both passes stage a 32 x 32 tile plus a halo of the largest radius in shared memory and form the
+// box sums separably (rows, then columns).
+#include "internal.h"
+
+namespace collage {
+
+constexpr int kDT = 32;       // dilation tile side
+constexpr int kDThreads = 256;
+constexpr int kDPPT = kDT * kDT / kDThreads;
+
+__device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
+  int lo = 0, hi = P - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ int dil_radius(int k) { return 2 + 3 * k; }  // (5 + 6k - 1) / 2
+
+// Horizontal box sums of `src` (side S, rows [r_lo, r_hi)) into H (S x kDT), radius r, halo h.
+__device__ __forceinline__ void hsum(const float* src, float* H, int S, int h, int r) {
+  for (int idx = threadIdx.x; idx < S * kDT; idx += blockDim.x) {
+    const int rr = idx / kDT, c = idx % kDT;
+    if (rr < h - r || rr >= h + kDT + r) continue;
+    const float* row = src + rr * S + c + h;
+    float s = 0.0f;
+    for (int dc = -r; dc <= r; ++dc) s += row[dc];
+    H[idx] = s;
+  }
+}
+
+__device__ __forceinline__ float vsum(const float* H, int h, int r, int rr, int c) {
+  float s = 0.0f;
+  for (int dr = -r; dr <= r; ++dr) s += H[(rr + h + dr) * kDT + c];
+  return s;
+}
+
+__global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
+  extern __shared__ float sm[];
+  __shared__ float s_red[kDThreads / 32];
+  if (*d.status & kStatusOverflow) return;
+  const int K = d.L.n_dil, h = dil_radius(K - 1), S = kDT + 2 * h;
+  float* sO = sm;
+  float* H = sm + S * S;
+  for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
+    const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
+    const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
+    const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
+    const long long pb = d.prob_pix_base[p];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+      const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
+      sO[idx] = (X >= 0 && Y >= 0 && X < res && Y < res) ? 1.0f - d.img_I[pb + (long long)Y * res + X] : 0.0f;
+    }
+    __syncthreads();
+    float lu = 0.0f, gdir[kDPPT], mval[kDPPT];
+    unsigned mask[kDPPT];
+#pragma unroll
+    for (int i = 0; i < kDPPT; ++i) {
+      const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
+      const int X = x0 + c, Y = y0 + rr;
+      const bool in = X < res && Y < res;
+      const float O = sO[(rr + h) * S + c + h];
+      const float M = in ? d.covc[pb + (long long)Y * res + X] : 0.0f;
+      mval[i] = M * (1.0f - O);
+      gdir[i] = 0.0f;
+      mask[i] = 0u;
+    }
+    for (int k = 0; k < K; ++k) {
+      const int r = dil_radius(k);
+      hsum(sO, H, S, h, r);
+      __syncthreads();
+      const float w = d.L.dil_w[k];
+#pragma unroll
+      for (int i = 0; i < kDPPT; ++i) {
+        const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
+        if (x0 + c >= res || y0 + rr >= res) continue;
+        const float B = vsum(H, h, r, rr, c);
+        const float D = fminf(1.0f, B);
+        lu += w * mval[i] * (1.0f - D);
+        if (B < 1.0f) mask[i] |= 1u << k;
+        // direct part of the adjoint: d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
+        gdir[i] -= w * (1.0f - D);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < kDPPT; ++i) {
+      const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
+      const int X = x0 + c, Y = y0 + rr;
+      if (X >= res || Y >= res) continue;
+      const long long pix = pb + (long long)Y * res + X;
+      const float M = d.covc[pix];
+      d.dil_m[pix] = mval[i];
+      d.dil_mask[pix] = (uint8_t)mask[i];
+      d.gOu[pix] = M * gdir[i];
+    }
+    // fixed-order block sum
+    for (int o = 16; o; o >>= 1) lu += __shfl_xor_sync(0xffffffffu, lu, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = lu;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.0f;
+      for (int i = 0; i < kDThreads / 32; ++i) s += s_red[i];
+      d.lossU[dt] = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
+  extern __shared__ float sm[];
+  if (*d.status & kStatusOverflow) return;
+  const int K = d.L.n_dil, h = dil_radius(K - 1), S = kDT + 2 * h;
+  float* sG = sm;            // G_k for the current k
+  float* H = sm + S * S;
+  float* sM = H + S * kDT;   // M_C (1 - O)
+  uint8_t* sMask = reinterpret_cast<uint8_t*>(sM + S * S);
+  for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
+    const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
+    const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
+    const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
+    const long long pb = d.prob_pix_base[p];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+      const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
+      const bool in = X >= 0 && Y >= 0 && X < res && Y < res;
+      const long long pix = pb + (long long)Y * res + X;
+      sM[idx] = in ? d.dil_m[pix] : 0.0f;
+      sMask[idx] = in ? d.dil_mask[pix] : (uint8_t)0;
+    }
+    float acc[kDPPT];
+#pragma unroll
+    for (int i = 0; i < kDPPT; ++i) acc[i] = 0.0f;
+    for (int k = 0; k < K; ++k) {
+      const int r = dil_radius(k);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x)
+        sG[idx] = (sMask[idx] >> k) & 1u ? sM[idx] : 0.0f;
+      __syncthreads();
+      hsum(sG, H, S, h, r);
+      __syncthreads();
+      const float w = d.L.dil_w[k];
+#pragma unroll
+      for (int i = 0; i < kDPPT; ++i) {
+        const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
+        acc[i] -= w * vsum(H, h, r, rr, c);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kDPPT; ++i) {
+      const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
+      const int X = x0 + c, Y = y0 + rr;
+      if (X >= res || Y >= res) continue;
+      const long long pix = pb + (long long)Y * res + X;
+      d.gOu[pix] += acc[i];
+    }
+  }
+}
+
+// One block per problem: fixed-order double sums of the tile partials, then Eq. 8.
+__global__ void __launch_bounds__(256) k_loss(Dev d, int count_step) {
+  __shared__ double s_red[4][8];
+  const int p = blockIdx.x;
+  const int t0 = d.prob_tile_base[p], t1 = d.prob_tile_base[p + 1];
+  const bool use_u = d.L.gamma != 0.0f && d.L.n_dil > 0;
+  double a = 0, b = 0, c = 0, u = 0;
+  for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
+    const float4 v = d.lossA[t];
+    a += v.x;
+    b += v.y;
+    c += v.z;
+  }
+  if (use_u)
+    for (int t = d.prob_dtile_base[p] + (int)threadIdx.x; t < d.prob_dtile_base[p + 1]; t += blockDim.x)
+      u += d.lossU[t];
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][w] = a;
+    s_red[1][w] = b;
+    s_red[2][w] = c;
+    s_red[3][w] = u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0, B = 0, C = 0, U = 0;
+    for (int i = 0; i < 8; ++i) {
+      A += s_red[0][i];
+      B += s_red[1][i];
+      C += s_red[2][i];
+      U += s_red[3][i];
+    }
+    const double np = (double)d.prob_res[p] * (double)d.prob_res[p];
+    const double Lc = A / np, Lo = B / np, Ld = C / np;
+    const double L = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * U + d.L.delta * Ld;
+    float* out = d.loss_terms + 5 * p;
+    out[0] = (float)Lc;
+    out[1] = (float)Lo;
+    out[2] = (float)U;
+    out[3] = (float)Ld;
+    out[4] = (float)L;
+    if (count_step && p == 0 && !(*d.status & kStatusOverflow)) *d.step += 1;
+  }
+}
+
+// Deterministic mode: each element sums its (tile, element) partials in emission order.
+__global__ void k_grad_reduce(Dev d) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
+  const int b = d.off[g], n = d.cnt[g];
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = 0; i < n; ++i) {
+    const float4 v = d.partial[b + i];
+    r.x += v.x;
+    r.y += v.y;
+    r.z += v.z;
+    r.w += v.w;
+  }
+  d.dq[g] = r;
+}
+
+// Adam (bias-corrected, the update torch.optim.Adam performs), then the clamp of s.
+__global__ void k_adam(Dev d) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
+  const int t = *d.step;
+  const float bc1 = 1.0f - powf(d.b1, (float)t), bc2 = 1.0f - powf(d.b2, (float)t);
+  const float step_size = d.lr / bc1, bc2s = sqrtf(bc2);
+  float4 q = d.q[g], m = d.m[g], v = d.v[g];
+  const float4 gr = d.dq[g];
+  const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
+  float* qp = &q.x;
+  float* mp = &m.x;
+  float* vp = &v.x;
+  const float gg[4] = {gr.x, gr.y, gr.z, gr.w};
+  const unsigned char tt[4] = {tr.x, tr.y, tr.z, tr.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!tt[k]) continue;
+    mp[k] = d.b1 * mp[k] + (1.0f - d.b1) * gg[k];
+    vp[k] = d.b2 * vp[k] + (1.0f - d.b2) * gg[k] * gg[k];
+    const float denom = sqrtf(vp[k]) / bc2s + d.eps;
+    qp[k] -= step_size * mp[k] / denom;
+  }
+  q.w = fminf(fmaxf(q.w, d.s_min), d.s_max);
+  d.q[g] = q;
+  d.m[g] = m;
+  d.v[g] = v;
+}
+
+static size_t dilate_smem(int K, bool backward) {
+  const int h = dil_radius(K - 1), S = kDT + 2 * h;
+  size_t f = (size_t)S * S + (size_t)S * kDT;
+  if (backward) f += (size_t)S * S + ((size_t)S * S + 3) / 4;
+  return f * sizeof(float);
+}
+
+cudaError_t prepare_dilate(int n_dil) {
+  if (n_dil <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_dilate_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dilate_smem(n_dil, true));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_dilate_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dilate_smem(n_dil, false));
+}
+
+cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward) {
+  if (d.L.n_dil <= 0) return cudaSuccess;
+  const size_t sm = dilate_smem(d.L.n_dil, backward);
+  if (backward) k_dilate_bwd<<<d.total_dtiles, kDThreads, sm, s>>>(d);
+  else k_dilate_fwd<<<d.total_dtiles, kDThreads, sm, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step) {
+  k_loss<<<d.n_probs, 256, 0, s>>>(d, count_step ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s) {
+  k_grad_reduce<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const Dev& d, cudaStream_t s) {
+  k_adam<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out) {
+  return cudaMemcpyAsync(out, d.dq, sizeof(float4) * (size_t)d.n_elems, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace collage

@@ -1,0 +1,504 @@
+// Tile rasteriser (forward), its adjoint, and the container raster.
+//
+// Coverage of element i at pixel p is c = S(sd / rho) with sd the signed distance (winding number
+// for the sign, positive inside; hw - d for open strokes) and S(x) = (1 + x)^2 (2 - x) / 4 on
+// [-1, 1] (the same cubic as 1/2 + 3x/4 - x^3/4, written in factored form so that 1 - S(x) =
+// S(-x) keeps full relative precision near x = 1).  This is the anti-aliased, differentiable
+// rasteriser the method builds on (Sec. 3 "Differentiable Rendering"); the composites and
+// per-pixel losses are those of Sec. 4.2 (Eqs. 5, 6 and the force term of Sec. 5).
+//
+// Precision: each element's vertices are stored relative to its translation, in pixels, and the
+// pixel is brought into that frame as (p - t_hi) - t_lo, so every FP32 quantity is a few tens of
+// pixels at most and the signed distance carries an error of ~1e-6 px at any grid size.
+//
+// The forward pass saves, for every (tile, element) pair and pixel of the tile, the signed
+// distance and the closest segment; the adjoint reads them back instead of repeating the segment
+// loop, so only one pass over the pixel-segment pairs happens per iteration.
+#include <cfloat>
+
+#include "internal.h"
+
+namespace collage {
+
+__device__ __forceinline__ float Sfun(float x) {
+  x = fminf(fmaxf(x, -1.0f), 1.0f);
+  const float a = 1.0f + x;
+  return 0.25f * a * a * (2.0f - x);
+}
+__device__ __forceinline__ float dSfun(float x) {
+  x = fminf(fmaxf(x, -1.0f), 1.0f);
+  return 0.75f * (1.0f - x) * (1.0f + x);
+}
+
+__device__ __forceinline__ int find_prob(const int* base, int P, int tile) {
+  int lo = 0, hi = P - 1;  // last p with base[p] <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Distance / winding update of one point against one staged segment (a, a + e) whose end point
+// has y = b_y.  Winding: the segment crosses the +x ray from the point when the two end points lie
+// on different sides of it (half-open in y); cross(e, w) > 0 puts the crossing right of the point
+// for an upward segment, < 0 for a downward one.
+struct SegQuery {
+  float best;  // squared distance
+  int idx;
+  int wn;
+};
+
+__device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, float4 s, float2 s2,
+                                           int j, bool winding) {
+  const float wx = dx - s.x, wy = dy - s.y;
+  const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
+  const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
+  const float d2 = fmaf(qx, qx, qy * qy);
+  if (d2 < Q.best) {
+    Q.best = d2;
+    Q.idx = j;
+  }
+  if (winding) {
+    const bool a_le = wy >= 0.0f;         // a.y <= p.y
+    const bool b_le = dy - s2.x >= 0.0f;  // b.y <= p.y
+    const float cr = s.z * wy - s.w * wx;
+    if (a_le && !b_le && cr > 0.0f) Q.wn += 1;
+    if (!a_le && b_le && cr < 0.0f) Q.wn -= 1;
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ float block_sum(float x, float* red) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = x;
+  __syncthreads();
+  float s = 0.0f;
+  for (int i = 0; i < NT / 32; ++i) s += red[i];  // fixed order
+  return s;
+}
+
+constexpr int kSegCap = 1024;
+
+// ------------------------------------------------------------------------------------------------
+// Forward: per tile, per binned element (in element order), per pixel: signed distance, coverage,
+// composites Ihat = prod(1 - c) and prod(1 - tau c^pad); then the per-pixel loss terms.
+// ------------------------------------------------------------------------------------------------
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) k_raster_fwd(Dev d, float* out_bw, float* out_tau) {
+  constexpr int NP = T * T, PPT = NP / NT;
+  __shared__ float4 s_seg[kSegCap];
+  __shared__ float2 s_seg2[kSegCap];
+  __shared__ float s_red[NT / 32];
+  if (*d.status & kStatusOverflow) return;
+  const uint32_t* vals = sorted_vals(d);
+  const float rho = d.L.rho_px, inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
+    const int p = find_prob(d.prob_tile_base, d.n_probs, tile);
+    const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
+    const int tx = lt % ntx, ty = lt / ntx;
+    const long long pixbase = d.prob_pix_base[p];
+    float px[PPT], py[PPT], keep[PPT], keept[PPT];
+    int zc[PPT];
+    bool in[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int local = threadIdx.x + k * NT;
+      const int X = tx * T + local % T, Y = ty * T + local / T;
+      in[k] = X < res && Y < res;
+      px[k] = (float)X + 0.5f;
+      py[k] = (float)Y + 0.5f;
+      keep[k] = 1.0f;
+      keept[k] = 1.0f;
+      zc[k] = 0;
+    }
+    const uint2 rg = d.range[tile];
+    for (uint32_t pr = rg.x; pr < rg.y; ++pr) {
+      const int g = d.elem_of[vals[pr]];
+      const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
+      const bool closed = d.elem_closed[g] != 0;
+      const int ns = closed ? nv : nv - 1;
+      const float4 tp = d.tpx[g], bb = d.bbox[g];
+      const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)res;
+      float dx[PPT], dy[PPT];
+      bool act[PPT];
+      SegQuery Q[PPT];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        dx[k] = (px[k] - tp.x) - tp.z;
+        dy[k] = (py[k] - tp.y) - tp.w;
+        act[k] = in[k] && px[k] >= bb.x && px[k] <= bb.z && py[k] >= bb.y && py[k] <= bb.w;
+        any |= act[k];
+        Q[k].best = FLT_MAX;
+        Q[k].idx = 0;
+        Q[k].wn = 0;
+      }
+      for (int c0 = 0; c0 < ns; c0 += kSegCap) {
+        const int cn = min(kSegCap, ns - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cn; j += NT) {
+          const int a_i = c0 + j, b_i = (a_i + 1 == nv) ? 0 : a_i + 1;
+          const float2 a = d.vrel[v0 + a_i], b = d.vrel[v0 + b_i];
+          const float ex = b.x - a.x, ey = b.y - a.y;
+          const float ee = ex * ex + ey * ey;
+          s_seg[j] = make_float4(a.x, a.y, ex, ey);
+          s_seg2[j] = make_float2(b.y, ee > 0.0f ? 1.0f / ee : 0.0f);
+        }
+        __syncthreads();
+        if (any) {
+          if (closed) {
+            for (int j = 0; j < cn; ++j) {
+              const float4 s = s_seg[j];
+              const float2 s2 = s_seg2[j];
+#pragma unroll
+              for (int k = 0; k < PPT; ++k)
+                if (act[k]) seg_update(Q[k], dx[k], dy[k], s, s2, c0 + j, true);
+            }
+          } else {
+            for (int j = 0; j < cn; ++j) {
+              const float4 s = s_seg[j];
+              const float2 s2 = s_seg2[j];
+#pragma unroll
+              for (int k = 0; k < PPT; ++k)
+                if (act[k]) seg_update(Q[k], dx[k], dy[k], s, s2, c0 + j, false);
+            }
+          }
+        }
+      }
+      float2* sv = d.saved + (size_t)pr * NP;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        float sd = -1e30f;
+        if (act[k]) {
+          const float dist = sqrtf(Q[k].best);
+          sd = closed ? (Q[k].wn != 0 ? dist : -dist) : hwpx - dist;
+        }
+        const float x = sd * inv_rho;
+        const float omc = Sfun(-x), cp = Sfun((sd + pad) * inv_rho);
+        if (omc == 0.0f) zc[k] += 1;
+        else keep[k] *= omc;
+        keept[k] *= 1.0f - tau * cp;
+        sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(Q[k].idx));
+      }
+    }
+    // per-pixel loss terms (Eq. 5, Eq. 6 surrogate, downward force)
+    float lc = 0.0f, lo = 0.0f, ld = 0.0f;
+    const float inv_res = 1.0f / (float)res;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if (!in[k]) continue;
+      const long long pix = pixbase + (long long)(py[k] - 0.5f) * res + (long long)(px[k] - 0.5f);
+      const float ihat = zc[k] ? 0.0f : keep[k];
+      const float cov = d.covc[pix];
+      const float ic = 1.0f - cov;
+      const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
+      const float df = ihat - ic;
+      lc += W * df * df;
+      const float A = 1.0f - keept[k];
+      lo += A > tau ? A - tau : 0.0f;
+      ld += (1.0f - ihat) * (1.0f - py[k] * inv_res);
+      d.img_I[pix] = ihat;
+      d.img_Pt[pix] = keept[k];
+      if (out_bw) out_bw[pix] = ihat;
+      if (out_tau) out_tau[pix] = A;
+    }
+    lc = block_sum<NT>(lc, s_red);
+    lo = block_sum<NT>(lo, s_red);
+    ld = block_sum<NT>(ld, s_red);
+    if (threadIdx.x == 0) d.lossA[tile] = make_float4(lc, lo, ld, 0.0f);
+    (void)rho;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Adjoint: dL/dIhat and dL/dA_tau per pixel, then per (tile, element) the chain
+// dL/dc -> dc/dsd -> dsd/d(closest segment) -> d/d(tx, ty, theta, s) of Eq. 2, reduced over the
+// tile's pixels in a fixed order and added to the element's gradient.
+// ------------------------------------------------------------------------------------------------
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
+  constexpr int NP = T * T, PPT = NP / NT;
+  __shared__ float s_red[4][NT / 32];
+  if (*d.status & kStatusOverflow) return;
+  const uint32_t* vals = sorted_vals(d);
+  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
+    const uint2 rg = d.range[tile];
+    if (rg.x == rg.y) continue;
+    const int p = find_prob(d.prob_tile_base, d.n_probs, tile);
+    const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
+    const int tx = lt % ntx, ty = lt / ntx;
+    const long long pixbase = d.prob_pix_base[p];
+    const float inv_np = 1.0f / ((float)res * (float)res);
+    float px[PPT], py[PPT], ihat[PPT], pt[PPT], gI[PPT], gA[PPT];
+    bool in[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int local = threadIdx.x + k * NT;
+      const int X = tx * T + local % T, Y = ty * T + local / T;
+      in[k] = X < res && Y < res;
+      px[k] = (float)X + 0.5f;
+      py[k] = (float)Y + 0.5f;
+      ihat[k] = pt[k] = gI[k] = gA[k] = 0.0f;
+      if (in[k]) {
+        const long long pix = pixbase + (long long)Y * res + X;
+        ihat[k] = d.img_I[pix];
+        pt[k] = d.img_Pt[pix];
+        const float cov = d.covc[pix];
+        const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
+        const float gou = d.L.gamma != 0.0f ? d.gOu[pix] : 0.0f;
+        // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
+        gI[k] = d.L.alpha * inv_np * 2.0f * W * (ihat[k] - (1.0f - cov)) - d.L.gamma * gou -
+                d.L.delta * inv_np * (1.0f - py[k] / (float)res);
+        gA[k] = (1.0f - pt[k]) > tau ? d.L.beta * inv_np : 0.0f;
+      }
+    }
+    for (uint32_t pr = rg.x; pr < rg.y; ++pr) {
+      const int emit = (int)vals[pr];
+      const int g = d.elem_of[emit];
+      const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
+      const bool closed = d.elem_closed[g] != 0;
+      const float4 tp = d.tpx[g];
+      const float s_inv = 1.0f / d.q[g].w;
+      const float2* sv = d.saved + (size_t)pr * NP;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const float2 rec = sv[threadIdx.x + k * NT];
+        const float sd = rec.x;
+        const float x = sd * inv_rho, xp = (sd + pad) * inv_rho;
+        if (!in[k] || !(fabsf(x) < 1.0f || fabsf(xp) < 1.0f)) continue;
+        const float omc = Sfun(-x), cp = Sfun(xp);
+        // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)
+        const float gc = omc > 0.0f ? -gI[k] * ihat[k] / omc : 0.0f;
+        // dA/dc^pad_i = tau prod_{j != i}(1 - tau c^pad_j)
+        const float gcp = gA[k] * tau * pt[k] / (1.0f - tau * cp);
+        const float gsd = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
+        if (gsd == 0.0f) continue;
+        const int j = __float_as_int(rec.y);
+        const float2 a = d.vrel[v0 + j], b = d.vrel[v0 + (j + 1 == nv ? 0 : j + 1)];
+        const float dx = (px[k] - tp.x) - tp.z, dy = (py[k] - tp.y) - tp.w;
+        const float ex = b.x - a.x, ey = b.y - a.y, ee = ex * ex + ey * ey;
+        const float wx = dx - a.x, wy = dy - a.y;
+        const float u = ee > 0.0f ? __saturatef((wx * ex + wy * ey) / ee) : 0.0f;
+        const float qx = fmaf(u, ex, a.x), qy = fmaf(u, ey, a.y);  // closest point, rel. to t
+        // unit normal from the closest point towards the pixel: for a closest point inside the
+        // segment it is the segment's perpendicular on the pixel's side (well conditioned even
+        // when the pixel is almost on the outline); at an end point it is the direction to the pixel
+        float nx, ny;
+        if (u > 0.0f && u < 1.0f) {
+          const float inv_len = rsqrtf(ee);
+          const float side = ex * wy - ey * wx >= 0.0f ? inv_len : -inv_len;
+          nx = -ey * side;
+          ny = ex * side;
+        } else {
+          const float rx = dx - qx, ry = dy - qy;
+          const float dist = sqrtf(rx * rx + ry * ry);
+          if (!(dist > 0.0f)) continue;
+          nx = rx / dist;
+          ny = ry / dist;
+        }
+        // sd = sig * dist (closed: sig = +-1 by the winding; open: sd = hw - dist, sig = -1)
+        const float sig = closed ? (sd > 0.0f ? 1.0f : -1.0f) : -1.0f;
+        const float gs = -sig * gsd;
+        a0 += gs * nx * (float)res;                 // d(dist)/dt = -n, t in unit coords
+        a1 += gs * ny * (float)res;
+        a2 += gs * (ny * qx - nx * qy);             // d(dist)/dtheta = -n . J q
+        a3 += gs * (nx * qx + ny * qy) * s_inv;     // d(dist)/ds = -n . q / s
+      }
+      // fixed-order block reduction of the four sums
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+      }
+      if (lane == 0) {
+        s_red[0][wid] = a0;
+        s_red[1][wid] = a1;
+        s_red[2][wid] = a2;
+        s_red[3][wid] = a3;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < NT / 32; ++i) {
+          r.x += s_red[0][i];
+          r.y += s_red[1][i];
+          r.z += s_red[2][i];
+          r.w += s_red[3][i];
+        }
+        if (d.deterministic) {
+          d.partial[emit] = r;
+        } else {
+          atomicAdd(&d.dq[g].x, r.x);
+          atomicAdd(&d.dq[g].y, r.y);
+          atomicAdd(&d.dq[g].z, r.z);
+          atomicAdd(&d.dq[g].w, r.w);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Container: coverage of every pixel by the container rings (nonzero rule), once per level.
+// Ring vertices are brought into the tile's frame in double and rounded once.
+// ------------------------------------------------------------------------------------------------
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) k_container(Dev d) {
+  constexpr int NP = T * T, PPT = NP / NT;
+  __shared__ float4 s_seg[kSegCap];
+  __shared__ float2 s_seg2[kSegCap];
+  const float inv_rho = 1.0f / d.L.rho_px;
+  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
+    const int p = find_prob(d.prob_tile_base, d.n_probs, tile);
+    const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
+    const int tx = lt % ntx, ty = lt / ntx;
+    const double ox = (double)(tx * T), oy = (double)(ty * T);
+    SegQuery Q[PPT];
+    float dx[PPT], dy[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int local = threadIdx.x + k * NT;
+      dx[k] = (float)(local % T) + 0.5f;
+      dy[k] = (float)(local / T) + 0.5f;
+      Q[k].best = FLT_MAX;
+      Q[k].idx = 0;
+      Q[k].wn = 0;
+    }
+    const int r0 = d.prob_ring_base[p], r1 = d.prob_ring_base[p + 1];
+    for (int r = r0; r < r1; ++r) {
+      const int b0 = d.ring_off[r], nv = d.ring_off[r + 1] - b0;
+      for (int c0 = 0; c0 < nv; c0 += kSegCap) {
+        const int cn = min(kSegCap, nv - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cn; j += NT) {
+          const int ai = b0 + c0 + j, bi = b0 + (c0 + j + 1) % nv;
+          const double ax = d.ring_pts[2 * ai] * res - ox, ay = d.ring_pts[2 * ai + 1] * res - oy;
+          const double bx = d.ring_pts[2 * bi] * res - ox, by = d.ring_pts[2 * bi + 1] * res - oy;
+          const float fax = (float)ax, fay = (float)ay;
+          const float ex = (float)(bx - ax), ey = (float)(by - ay);
+          const float ee = ex * ex + ey * ey;
+          s_seg[j] = make_float4(fax, fay, ex, ey);
+          s_seg2[j] = make_float2((float)by, ee > 0.0f ? 1.0f / ee : 0.0f);
+        }
+        __syncthreads();
+        for (int j = 0; j < cn; ++j) {
+          const float4 s = s_seg[j];
+          const float2 s2 = s_seg2[j];
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) seg_update(Q[k], dx[k], dy[k], s, s2, j, true);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int local = threadIdx.x + k * NT;
+      const int X = tx * T + local % T, Y = ty * T + local / T;
+      if (X >= res || Y >= res) continue;
+      const float dist = sqrtf(Q[k].best);
+      const float sd = Q[k].wn != 0 ? dist : -dist;
+      d.covc[d.prob_pix_base[p] + (long long)Y * res + X] = Sfun(sd * inv_rho);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+template <int T>
+struct TileCfg;
+template <>
+struct TileCfg<8> {
+  static constexpr int NT = 64;
+};
+template <>
+struct TileCfg<16> {
+  static constexpr int NT = 128;
+};
+template <>
+struct TileCfg<32> {
+  static constexpr int NT = 256;
+};
+
+template <int T>
+static int default_grid(const Dev& d, int grid) {
+  return grid > 0 ? grid : d.total_tiles;
+}
+
+cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int grid, float* out_bw, float* out_tau) {
+  switch (d.tile) {
+    case 8:
+      k_raster_fwd<8, TileCfg<8>::NT><<<default_grid<8>(d, grid), TileCfg<8>::NT, 0, s>>>(d, out_bw, out_tau);
+      break;
+    case 16:
+      k_raster_fwd<16, TileCfg<16>::NT><<<default_grid<16>(d, grid), TileCfg<16>::NT, 0, s>>>(d, out_bw, out_tau);
+      break;
+    case 32:
+      k_raster_fwd<32, TileCfg<32>::NT><<<default_grid<32>(d, grid), TileCfg<32>::NT, 0, s>>>(d, out_bw, out_tau);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int grid) {
+  switch (d.tile) {
+    case 8:
+      k_raster_bwd<8, TileCfg<8>::NT><<<default_grid<8>(d, grid), TileCfg<8>::NT, 0, s>>>(d);
+      break;
+    case 16:
+      k_raster_bwd<16, TileCfg<16>::NT><<<default_grid<16>(d, grid), TileCfg<16>::NT, 0, s>>>(d);
+      break;
+    case 32:
+      k_raster_bwd<32, TileCfg<32>::NT><<<default_grid<32>(d, grid), TileCfg<32>::NT, 0, s>>>(d);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_container(const Dev& d, cudaStream_t s) {
+  switch (d.tile) {
+    case 8:
+      k_container<8, TileCfg<8>::NT><<<d.total_tiles, TileCfg<8>::NT, 0, s>>>(d);
+      break;
+    case 16:
+      k_container<16, TileCfg<16>::NT><<<d.total_tiles, TileCfg<16>::NT, 0, s>>>(d);
+      break;
+    case 32:
+      k_container<32, TileCfg<32>::NT><<<d.total_tiles, TileCfg<32>::NT, 0, s>>>(d);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int raster_fwd_max_grid(int tile) {
+  int dev = 0, sms = 0, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  switch (tile) {
+    case 8:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_raster_fwd<8, 64>, 64, 0);
+      break;
+    case 16:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_raster_fwd<16, 128>, 128, 0);
+      break;
+    default:
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_raster_fwd<32, 256>, 256, 0);
+      break;
+  }
+  return sms * (per > 0 ? per : 1);
+}
+
+}  // namespace collage
