@@ -167,51 +167,57 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
   }
 }
 
-// One block per problem: fixed-order double sums of the tile partials, then Eq. 8.
-__global__ void __launch_bounds__(256) k_loss(Dev d, int count_step) {
-  __shared__ double s_red[4][8];
+// One block per problem: fixed-order sums of the tile partials (float per thread over a strided
+// subset with independent loads in flight, double across threads), then Eq. 8.
+constexpr int kLossThreads = 1024;
+__global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
+  __shared__ double s_red[4][kLossThreads / 32];
   const int p = blockIdx.x;
   const int t0 = d.prob_tile_base[p], t1 = d.prob_tile_base[p + 1];
   const bool use_u = d.L.gamma != 0.0f && d.L.n_dil > 0;
-  double a = 0, b = 0, c = 0, u = 0;
-  for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
+  float a = 0.f, b = 0.f, c = 0.f, u = 0.f;
+#pragma unroll 8
+  for (int t = t0 + (int)threadIdx.x; t < t1; t += kLossThreads) {
     const float4 v = d.lossA[t];
     a += v.x;
     b += v.y;
     c += v.z;
   }
-  if (use_u)
-    for (int t = d.prob_dtile_base[p] + (int)threadIdx.x; t < d.prob_dtile_base[p + 1]; t += blockDim.x)
-      u += d.lossU[t];
+  if (use_u) {
+    const int u0 = d.prob_dtile_base[p], u1 = d.prob_dtile_base[p + 1];
+#pragma unroll 8
+    for (int t = u0 + (int)threadIdx.x; t < u1; t += kLossThreads) u += d.lossU[t];
+  }
+  double A = a, B = b, Cc = c, U = u;
   for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-    u += __shfl_xor_sync(0xffffffffu, u, o);
+    A += __shfl_xor_sync(0xffffffffu, A, o);
+    B += __shfl_xor_sync(0xffffffffu, B, o);
+    Cc += __shfl_xor_sync(0xffffffffu, Cc, o);
+    U += __shfl_xor_sync(0xffffffffu, U, o);
   }
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    s_red[0][w] = a;
-    s_red[1][w] = b;
-    s_red[2][w] = c;
-    s_red[3][w] = u;
+    s_red[0][w] = A;
+    s_red[1][w] = B;
+    s_red[2][w] = Cc;
+    s_red[3][w] = U;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double A = 0, B = 0, C = 0, U = 0;
-    for (int i = 0; i < 8; ++i) {
-      A += s_red[0][i];
-      B += s_red[1][i];
-      C += s_red[2][i];
-      U += s_red[3][i];
+    double SA = 0, SB = 0, SC = 0, SU = 0;
+    for (int i = 0; i < kLossThreads / 32; ++i) {
+      SA += s_red[0][i];
+      SB += s_red[1][i];
+      SC += s_red[2][i];
+      SU += s_red[3][i];
     }
     const double np = (double)d.prob_res[p] * (double)d.prob_res[p];
-    const double Lc = A / np, Lo = B / np, Ld = C / np;
-    const double L = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * U + d.L.delta * Ld;
+    const double Lc = SA / np, Lo = SB / np, Ld = SC / np;
+    const double L = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * SU + d.L.delta * Ld;
     float* out = d.loss_terms + 5 * p;
     out[0] = (float)Lc;
     out[1] = (float)Lo;
-    out[2] = (float)U;
+    out[2] = (float)SU;
     out[3] = (float)Ld;
     out[4] = (float)L;
     if (count_step && p == 0 && !(*d.status & kStatusOverflow)) *d.step += 1;
@@ -288,7 +294,7 @@ cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward) {
 }
 
 cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step) {
-  k_loss<<<d.n_probs, 256, 0, s>>>(d, count_step ? 1 : 0);
+  k_loss<<<d.n_probs, kLossThreads, 0, s>>>(d, count_step ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -175,7 +175,13 @@ def test_one_adam_step_matches_oracle(env):
 
 def test_autograd_function_matches_central_differences(env):
     """Adjoint of the library (through torch.autograd) against FP64 central differences of the
-    oracle loss, h = 1e-4, on 20 random elements of a 200-blob star collage."""
+    oracle loss on 20 random elements of a 200-blob star collage.
+
+    With h = 1e-4 (unit coordinates, 0.026 px on this 256^2 grid) a third of the difference
+    quotients straddle kinks of the loss (the min(1, B) of the distribution term, the relu of the
+    overlap surrogate), and the oracle's own analytic gradient misses them by the same amounts as
+    the GPU's; with h = 1e-7 the quotient resolves the local derivative (the oracle's analytic
+    gradient meets it to 2e-5) and every component must agree to 1e-3."""
     O, Collage = env
     from paper_2406_04008_gb300.collage import collage_loss
     prob = W.config_problem(2, grid=256)
@@ -187,22 +193,31 @@ def test_autograd_function_matches_central_differences(env):
     grad = params.grad.cpu().numpy()
     sc = O.Scene(prob)
     q0 = prob["params0"].astype(np.float64)
+    ref = sc.eval(q0, 256, o)["grad_a"].reshape(-1, 4)
     rng = np.random.default_rng(3)
     picks = rng.choice(len(prob["kind"]), 20, replace=False)
-    h = 1e-4
-    fd = np.zeros((20, 4))
-    for i, e in enumerate(picks):
-        for c in range(4):
-            qp, qm = q0.copy(), q0.copy()
-            qp[4 * e + c] += h
-            qm[4 * e + c] -= h
-            fd[i, c] = (sc.eval(qp, 256, o, grad=False)["terms"][4] -
-                        sc.eval(qm, 256, o, grad=False)["terms"][4]) / (2 * h)
-    gsel = grad[picks]
-    scale = np.abs(grad).max(0)
-    err = np.abs(gsel - fd) / np.maximum(np.abs(fd), 1e-2 * scale)
-    assert err.max() < 1e-2, err  # FD of a loss with kinks (relu, min, closest segment)
-    assert np.median(err) < 1e-3, np.median(err)
+    scale = np.abs(ref).max(0)
+
+    def fd(h):
+        out = np.zeros((20, 4))
+        for i, e in enumerate(picks):
+            for c in range(4):
+                qp, qm = q0.copy(), q0.copy()
+                qp[4 * e + c] += h
+                qm[4 * e + c] -= h
+                out[i, c] = (sc.eval(qp, 256, o, grad=False)["terms"][4] -
+                             sc.eval(qm, 256, o, grad=False)["terms"][4]) / (2 * h)
+        return out
+
+    def rel(a, b):
+        return np.abs(a - b) / np.maximum(np.abs(b), 1e-2 * scale)
+
+    gsel, rsel = grad[picks], ref[picks]
+    f4 = fd(1e-4)
+    assert np.median(rel(gsel, f4)) < 1e-3
+    # where the h = 1e-4 quotient disagrees, it disagrees with the oracle's gradient just as much
+    np.testing.assert_allclose(rel(gsel, f4), rel(rsel, f4), rtol=1e-2, atol=1e-3)
+    assert rel(gsel, fd(1e-7)).max() < 1e-3
     col.close()
 
 
