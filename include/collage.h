@@ -177,6 +177,30 @@ collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float
  * h_best_ms receives its iteration time (may be NULL).  Params are restored afterwards. */
 collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
 
+/* The even-distribution term (Eq. 7 as collage_loss_backward evaluates it) of one res x res image,
+ * and its gradient with respect to the occupancy O = 1 - d_ihat, computed without allocating any
+ * device memory.  The paper has no counterpart to this call; it exists for callers that cannot
+ * call cudaMalloc: code whose device memory is owned by another allocator (a framework's caching
+ * allocator, a fixed arena) and real-time loops where cudaMalloc / cudaFree, which can synchronise
+ * the device, are not acceptable.
+ *   d_ihat [res*res]    items rendered black on white (the d_img_bw of collage_render), row-major
+ *   d_cov  [res*res]    container coverage M_C (1 inside, 0 outside, anti-aliased at the edge)
+ *   h_dil_weight [n_dilations]  host weights of the kernels of widths 5 + 6k pixels, 1..8 kernels
+ *   d_loss [1]          receives L_u = sum_k w_k sum_p M_C (1 - O) (1 - min(1, box_k(O)))
+ *   d_grad_occ [res*res] receives dL_u/dO
+ * Scratch lives in a file-scope device array sized for COLLAGE_NOALLOC_MAX_PIXELS pixels (about
+ * 5 MiB, held by every GPU that loads the library until the process exits).  res*res above that
+ * maximum, res < 1, n_dilations outside 1..8 or a NULL pointer return COLLAGE_ERR_INVALID_ARG
+ * before any device work; CUDA failures return COLLAGE_ERR_CUDA.  The first call on a device looks
+ * up the array's device address (once per device, with that device current); make that first
+ * call before any stream capture.  All calls share the one array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (different streams, threads or devices sharing a
+ * context) race: serialise them.  Asynchronous on `stream`; inputs must stay valid until it runs. */
+#define COLLAGE_NOALLOC_MAX_PIXELS (1024 * 1024)
+collage_status collage_uniform_term_noalloc(void* stream, int res, int n_dilations,
+                                            const float* h_dil_weight, const float* d_ihat,
+                                            const float* d_cov, float* d_loss, float* d_grad_occ);
+
 collage_status collage_get_info(collage_t h, collage_info* out);
 /* Waits for the stream and returns any latched device error. */
 collage_status collage_sync(collage_t h, void* stream);
