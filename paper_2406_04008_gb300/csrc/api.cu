@@ -256,16 +256,6 @@ static void flatten(const collage_problem& p, int e, int spc, std::vector<float2
 // --------------------------------------------------------------------------------------------
 // Level setup
 // --------------------------------------------------------------------------------------------
-static int sort_passes(int total_tiles) {
-  unsigned m = total_tiles > 1 ? (unsigned)(total_tiles - 1) : 1u;
-  int bits = 0;
-  while (m) {
-    ++bits;
-    m >>= 1;
-  }
-  return std::max(1, (bits + kSortBits - 1) / kSortBits);
-}
-
 static collage_status ensure_pairs(collage_t h, size_t cap) {
   const size_t tt = (size_t)h->d.tile * h->d.tile;
   if (cap <= h->pair_cap && tt == h->saved_tile) return COLLAGE_OK;
@@ -274,17 +264,13 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   free_list(h->pair_bufs);
   h->pair_cap = 0;
   Dev& d = h->d;
-  CK(h, dmalloc(h->pair_bufs, d.keys0, cap));
-  CK(h, dmalloc(h->pair_bufs, d.vals0, cap));
-  CK(h, dmalloc(h->pair_bufs, d.keys1, cap));
-  CK(h, dmalloc(h->pair_bufs, d.vals1, cap));
-  CK(h, dmalloc(h->pair_bufs, d.elem_of, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_elem, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_sorted, cap));
   CK(h, dmalloc(h->pair_bufs, d.partial, cap));
   CK(h, dmalloc(h->pair_bufs, d.saved, cap * tt));
   h->pair_cap = cap;
   h->saved_tile = tt;
   d.cap = (int)std::min<size_t>(cap, 0x7fffffff);
-  d.sort_blocks = (int)std::min<size_t>(std::max<size_t>((cap + 4095) / 4096, 1), (size_t)h->sms);
   return COLLAGE_OK;
 }
 
@@ -318,7 +304,6 @@ static collage_status setup_level(collage_t h, int level) {
   d.total_tiles = h->tile_base[h->P];
   d.total_dtiles = h->dtile_base[h->P];
   d.total_pix = h->pix_base[h->P];
-  d.n_sort_passes = sort_passes(d.total_tiles);
   if ((size_t)d.total_pix > h->pix_cap || (size_t)d.total_tiles > h->tile_cap ||
       (size_t)d.total_dtiles > h->dtile_cap) {
     // regrow every level-sized buffer
@@ -332,6 +317,7 @@ static collage_status setup_level(collage_t h, int level) {
     CK(h, dmalloc(h->level_bufs, d.dil_m, np));
     CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
     CK(h, dmalloc(h->level_bufs, d.range, nt));
+    CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
     CK(h, dmalloc(h->level_bufs, d.lossA, nt));
     CK(h, dmalloc(h->level_bufs, d.lossU, nd));
     h->pix_cap = np;
@@ -348,12 +334,16 @@ static collage_status setup_level(collage_t h, int level) {
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));  // clear latched status
   CK(h, launch_container(d, s));
   // size the pair buffers from the current params: count with an unbounded capacity
+  CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
   Dev probe = d;
   probe.cap = 0x7fffffff;
   CK(h, launch_transform(probe, s, false));
   CK(h, launch_scan(probe, s));
   collage_status st = read_ctl(h, s);
   if (st) return st;
+  // the probe counted tiles without emitting: clear the counts for the first real iteration
+  CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
+  CK(h, cudaStreamSynchronize(s));
   if (h->h_ctl[0] & kStatusBadParam) return fail(h, COLLAGE_ERR_INVALID_ARG, "params are not finite or s <= 0");
   const size_t need = (size_t)h->h_ctl[2];
   st = ensure_pairs(h, std::max<size_t>(need + need / 2 + 256, 1024));
@@ -603,12 +593,11 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
     CKC(upload(h->owned, p_tr, tr));
     d.trainable = p_tr;
   }
-  CKC(dmalloc(h->owned, d.vrel, h->V));
+  CKC(dmalloc(h->owned, d.segA, h->V));
+  CKC(dmalloc(h->owned, d.segB, h->V));
   CKC(dmalloc(h->owned, d.tpx, h->N));
   CKC(dmalloc(h->owned, d.bbox, h->N));
   CKC(dmalloc(h->owned, d.rect, h->N));
-  CKC(dmalloc(h->owned, d.cnt, h->N));
-  CKC(dmalloc(h->owned, d.off, h->N + 1));
   CKC(dmalloc(h->owned, d.dq, h->N));
   CKC(cudaMemset(d.dq, 0, sizeof(float4) * h->N));
   CKC(dmalloc(h->owned, d.loss_terms, 5 * h->P));
@@ -618,7 +607,6 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.status = h->ctl;
   d.step = h->ctl + 1;
   d.total_pairs = h->ctl + 2;
-  CKC(dmalloc(h->owned, d.sort_hist, (size_t)kSortBins * h->sms));
   CKC(dmalloc(h->owned, h->d_prob_res, h->P));
   CKC(dmalloc(h->owned, h->d_prob_ntx, h->P));
   CKC(dmalloc(h->owned, h->d_prob_tile_base, h->P + 1));
@@ -793,17 +781,15 @@ extern "C" collage_status collage_get_bins(collage_t h, void* stream, int* d_til
   *h_n = n;
   if (!d_tile && !d_elem) return COLLAGE_OK;
   if (cap < n) return fail(h, COLLAGE_ERR_INVALID_ARG, "cap is smaller than the pair count");
-  std::vector<uint32_t> k(n), v(n);
-  std::vector<int> eo(n), te(n), ee(n);
-  if (n) {
-    CK(h, cudaMemcpy(k.data(), sorted_keys(h->d), sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
-    CK(h, cudaMemcpy(v.data(), sorted_vals(h->d), sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
-    CK(h, cudaMemcpy(eo.data(), h->d.elem_of, sizeof(int) * n, cudaMemcpyDeviceToHost));
-  }
-  for (int i = 0; i < n; ++i) {
-    te[i] = (int)k[i];
-    ee[i] = eo[v[i]];
-  }
+  std::vector<uint2> rg(h->d.total_tiles);
+  std::vector<int> el(n), te(n), ee(n);
+  CK(h, cudaMemcpy(rg.data(), h->d.range, sizeof(uint2) * rg.size(), cudaMemcpyDeviceToHost));
+  if (n) CK(h, cudaMemcpy(el.data(), h->d.pair_sorted, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  for (int t = 0; t < h->d.total_tiles; ++t)
+    for (uint32_t k = rg[t].x; k < rg[t].y && k < (uint32_t)n; ++k) {
+      te[k] = t;
+      ee[k] = el[k];
+    }
   if (d_tile && n) CK(h, cudaMemcpy(d_tile, te.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   if (d_elem && n) CK(h, cudaMemcpy(d_elem, ee.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   return COLLAGE_OK;
@@ -894,11 +880,10 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   out->total_pixels = h->d.total_pix;
   out->pair_capacity = h->d.cap;
   out->last_pairs = h->h_ctl ? h->h_ctl[2] : 0;
-  // transform, scan, emit, 3 per radix pass, ranges, raster fwd, (2 dilation), raster bwd,
-  // (gradient reduce), loss, Adam
+  // transform, tile scan, emit, raster fwd, (2 dilation), raster bwd, (gradient reduce), loss,
+  // Adam
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 3 + 3 * h->d.n_sort_passes + 1 + 1 + (dil ? 2 : 0) + 1 +
-                          (h->d.deterministic ? 1 : 0) + 2;
+  out->kernels_per_iter = 4 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 2;
   return COLLAGE_OK;
 }
 

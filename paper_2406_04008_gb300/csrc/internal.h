@@ -3,14 +3,14 @@
 // HBM layout, all problems of a handle concatenated:
 //   per element g (SoA):   prob, vertex offset, closed flag, stroke half-width, bin radius,
 //                          params q / Adam m, v (float4), world translation in pixels (hi, lo),
-//                          pixel bbox, tile rectangle, pair count and offset, gradient dq
-//   per flattened vertex:  local position (unit coords), per-iteration position relative to the
-//                          element translation in pixels (float, rounded from double)
-//   per (tile, element) pair, capacity `cap`: sort keys / values (ping-pong), element of each
-//                          emitted pair, deterministic gradient partials, and per pixel of the
+//                          outline box, tile rectangle, gradient dq
+//   per flattened vertex:  local position (unit coords), per-iteration segment record relative to
+//                          the element translation in pixels (float, rounded from double)
+//   per (tile, element) pair, capacity `cap`: element of each pair in emission order and in
+//                          element order, deterministic gradient partials, and per pixel of the
 //                          tile the signed distance + closest segment saved by the forward pass
 //   per pixel (level):     container coverage, Ihat, prod(1 - tau c^pad), uniform-loss scratch
-//   per tile:              [begin, end) into the sorted pairs, loss partials
+//   per tile:              counting-sort count, [begin, end) into the pairs, loss partials
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,9 +18,6 @@
 namespace collage {
 
 constexpr int kMaxDil = 8;
-constexpr int kSortBits = 8;            // radix digit
-constexpr int kSortBins = 1 << kSortBits;
-constexpr int kSortThreads = 256;
 constexpr int kStatusOverflow = 1;      // device status bits
 constexpr int kStatusBadParam = 2;
 constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bug)
@@ -63,22 +60,17 @@ struct Dev {
   const uchar4* trainable;      // may be null
   float lr, b1, b2, eps, s_min, s_max;
   // ---- per iteration ----
-  float2* vrel;                 // [V] px, relative to the element translation
+  float4* segA;                 // [V] segment k: start (px, relative to the translation), direction
+  float2* segB;                 // [V] segment k: end point y, 1 / |direction|^2
   float4* tpx;                  // [n] translation in px: (hi.x, hi.y, lo.x, lo.y)
-  float4* bbox;                 // [n] px bbox grown by the coverage margin
+  float4* bbox;                 // [n] outline box relative to the translation, grown by the margin
   int4* rect;                   // [n] tile rectangle (tx0, ty0, tx1, ty1), empty if tx1 < tx0
-  int* cnt;                     // [n] pairs per element
-  int* off;                     // [n+1] exclusive scan of cnt
+  int* tile_cnt;                // [total_tiles] counting-sort counts (zero between iterations)
   int* total_pairs;             // [1]
   int cap;                      // pair capacity
-  uint32_t* keys0;
-  uint32_t* vals0;
-  uint32_t* keys1;
-  uint32_t* vals1;
-  int* elem_of;                 // [cap] emit position -> element
-  uint32_t* sort_hist;          // [kSortBins * sort_blocks]
-  int sort_blocks;
-  uint2* range;                 // [total_tiles] [begin, end) into the sorted pairs
+  int* pair_elem;               // [cap] element of each pair, tile ranges, in emission order
+  int* pair_sorted;             // [cap] the same, each tile's list in increasing element order
+  uint2* range;                 // [total_tiles] [begin, end) into the pair arrays
   float2* saved;                // [cap * tile*tile] (sd px, closest segment as int bits)
   float* covc;                  // [pix] container coverage
   float* img_I;                 // [pix] Ihat = prod(1 - c)
@@ -97,14 +89,10 @@ struct Dev {
   int deterministic;
 };
 
-// The sorted keys / values after the last pass.
-__host__ __device__ inline const uint32_t* sorted_keys(const Dev& d) { return (d.n_sort_passes & 1) ? d.keys1 : d.keys0; }
-__host__ __device__ inline const uint32_t* sorted_vals(const Dev& d) { return (d.n_sort_passes & 1) ? d.vals1 : d.vals0; }
-
 // ---- launchers (each enqueues on `s`, returns the launch error) ----
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
-cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // pair counts -> offsets, total
-cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit, sort, ranges
+cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
+cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit pairs into tile ranges
 cudaError_t launch_container(const Dev& d, cudaStream_t s);
 cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int grid, float* out_bw,
                               float* out_tau);

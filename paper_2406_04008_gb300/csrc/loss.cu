@@ -6,7 +6,7 @@
 // w_k M_C (1 - O) (1 - D_k) over the container.  Its adjoint is
 //   dL_u/dO(q) = sum_k w_k [ -M_C(q)(1 - D_k(q)) - sum_{p in box_k(q)} M_C(p)(1 - O(p)) [B_k(p) < 1] ].
 // Both passes stage a 32 x 32 tile plus a halo of the largest radius in shared memory and form the
-// box sums separably (rows, then columns).
+// box sums separably (rows, then columns) with running windows.
 #include "internal.h"
 
 namespace collage {
@@ -27,23 +27,66 @@ __device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
 
 __host__ __device__ __forceinline__ int dil_radius(int k) { return 2 + 3 * k; }  // (5 + 6k - 1) / 2
 
-// Horizontal box sums of `src` (side S, rows [r_lo, r_hi)) into H (S x kDT), radius r, halo h.
-__device__ __forceinline__ void hsum(const float* src, float* H, int S, int h, int r) {
-  for (int idx = threadIdx.x; idx < S * kDT; idx += blockDim.x) {
-    const int rr = idx / kDT, c = idx % kDT;
+// Box sums by running windows: a thread owns kSeg consecutive outputs of one row (or column) of
+// one kernel, forms the first window directly and slides it (one add, one subtract per output).
+// Restarting every kSeg outputs keeps the float rounding at the level of a direct sum.
+constexpr int kSeg = 8;
+constexpr int kNSeg = kDT / kSeg;
+
+// H[k][rr][c] = sum_{|dc| <= r_k} src(k, rr, c + h + dc) for the rows the vertical pass reads.
+template <class Src>
+__device__ __forceinline__ void hsums(const Src& src, float* H, int S, int h, int K) {
+  const int items = K * S * kNSeg;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int seg = it % kNSeg, rr = (it / kNSeg) % S, k = it / (kNSeg * S);
+    const int r = dil_radius(k);
     if (rr < h - r || rr >= h + kDT + r) continue;
-    const float* row = src + rr * S + c + h;
-    float s = 0.0f;
-    for (int dc = -r; dc <= r; ++dc) s += row[dc];
-    H[idx] = s;
+    const int c0 = seg * kSeg;
+    float sacc = 0.0f;
+    for (int dc = -r; dc <= r; ++dc) sacc += src(k, rr, c0 + h + dc);
+    float* out = H + (k * S + rr) * kDT;
+    out[c0] = sacc;
+    for (int c = c0 + 1; c < c0 + kSeg; ++c) {
+      sacc += src(k, rr, c + h + r) - src(k, rr, c + h - r - 1);
+      out[c] = sacc;
+    }
   }
 }
 
-__device__ __forceinline__ float vsum(const float* H, int h, int r, int rr, int c) {
-  float s = 0.0f;
-  for (int dr = -r; dr <= r; ++dr) s += H[(rr + h + dr) * kDT + c];
-  return s;
+// Bk[k][rr][c] = sum_{|dr| <= r_k} H[k][rr + h + dr][c]: the box sum at output pixel (rr, c).
+__device__ __forceinline__ void vsums(const float* H, float* Bk, int S, int h, int K) {
+  const int items = K * kDT * kNSeg;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int c = it % kDT, seg = (it / kDT) % kNSeg, k = it / (kDT * kNSeg);
+    const int r = dil_radius(k);
+    const float* col = H + k * S * kDT + c;
+    const int r0 = seg * kSeg;
+    float sacc = 0.0f;
+    for (int dr = -r; dr <= r; ++dr) sacc += col[(r0 + h + dr) * kDT];
+    float* out = Bk + k * kDT * kDT + c;
+    out[r0 * kDT] = sacc;
+    for (int rr = r0 + 1; rr < r0 + kSeg; ++rr) {
+      sacc += col[(rr + h + r) * kDT] - col[(rr + h - r - 1) * kDT];
+      out[rr * kDT] = sacc;
+    }
+  }
 }
+
+struct OccSrc {  // occupancy O of the staged region, the same for every kernel
+  const float* sO;
+  int S;
+  __device__ float operator()(int, int rr, int cc) const { return sO[rr * S + cc]; }
+};
+
+struct GSrc {  // G_k = M_C (1 - O) where B_k < 1, else 0
+  const float* sM;
+  const uint8_t* sMask;
+  int S;
+  __device__ float operator()(int k, int rr, int cc) const {
+    const int i = rr * S + cc;
+    return ((sMask[i] >> k) & 1u) ? sM[i] : 0.0f;
+  }
+};
 
 __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
   extern __shared__ float sm[];
@@ -51,7 +94,8 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   const int K = d.L.n_dil, h = dil_radius(K - 1), S = kDT + 2 * h;
   float* sO = sm;
-  float* H = sm + S * S;
+  float* H = sO + S * S;
+  float* Bk = H + K * S * kDT;
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
@@ -63,56 +107,42 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
       sO[idx] = (X >= 0 && Y >= 0 && X < res && Y < res) ? 1.0f - d.img_I[pb + (long long)Y * res + X] : 0.0f;
     }
     __syncthreads();
-    float lu = 0.0f, gdir[kDPPT], mval[kDPPT];
-    unsigned mask[kDPPT];
-#pragma unroll
-    for (int i = 0; i < kDPPT; ++i) {
-      const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
-      const int X = x0 + c, Y = y0 + rr;
-      const bool in = X < res && Y < res;
-      const float O = sO[(rr + h) * S + c + h];
-      const float M = in ? d.covc[pb + (long long)Y * res + X] : 0.0f;
-      mval[i] = M * (1.0f - O);
-      gdir[i] = 0.0f;
-      mask[i] = 0u;
-    }
-    for (int k = 0; k < K; ++k) {
-      const int r = dil_radius(k);
-      hsum(sO, H, S, h, r);
-      __syncthreads();
-      const float w = d.L.dil_w[k];
-#pragma unroll
-      for (int i = 0; i < kDPPT; ++i) {
-        const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
-        if (x0 + c >= res || y0 + rr >= res) continue;
-        const float B = vsum(H, h, r, rr, c);
-        const float D = fminf(1.0f, B);
-        lu += w * mval[i] * (1.0f - D);
-        if (B < 1.0f) mask[i] |= 1u << k;
-        // direct part of the adjoint: d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
-        gdir[i] -= w * (1.0f - D);
-      }
-      __syncthreads();
-    }
+    hsums(OccSrc{sO, S}, H, S, h, K);
+    __syncthreads();
+    vsums(H, Bk, S, h, K);
+    __syncthreads();
+    float lu = 0.0f;
 #pragma unroll
     for (int i = 0; i < kDPPT; ++i) {
       const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
       const int X = x0 + c, Y = y0 + rr;
       if (X >= res || Y >= res) continue;
       const long long pix = pb + (long long)Y * res + X;
+      const float O = sO[(rr + h) * S + c + h];
       const float M = d.covc[pix];
-      d.dil_m[pix] = mval[i];
-      d.dil_mask[pix] = (uint8_t)mask[i];
-      d.gOu[pix] = M * gdir[i];
+      const float mval = M * (1.0f - O);
+      float gdir = 0.0f;
+      unsigned mask = 0u;
+      for (int k = 0; k < K; ++k) {
+        const float B = Bk[k * kDT * kDT + local];
+        const float D = fminf(1.0f, B);
+        const float w = d.L.dil_w[k];
+        lu += w * mval * (1.0f - D);
+        if (B < 1.0f) mask |= 1u << k;
+        gdir -= w * (1.0f - D);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
+      }
+      d.dil_m[pix] = mval;
+      d.dil_mask[pix] = (uint8_t)mask;
+      d.gOu[pix] = M * gdir;
     }
     // fixed-order block sum
     for (int o = 16; o; o >>= 1) lu += __shfl_xor_sync(0xffffffffu, lu, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = lu;
     __syncthreads();
     if (threadIdx.x == 0) {
-      float s = 0.0f;
-      for (int i = 0; i < kDThreads / 32; ++i) s += s_red[i];
-      d.lossU[dt] = s;
+      float t = 0.0f;
+      for (int i = 0; i < kDThreads / 32; ++i) t += s_red[i];
+      d.lossU[dt] = t;
     }
   }
 }
@@ -121,10 +151,10 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
   extern __shared__ float sm[];
   if (*d.status & kStatusOverflow) return;
   const int K = d.L.n_dil, h = dil_radius(K - 1), S = kDT + 2 * h;
-  float* sG = sm;            // G_k for the current k
-  float* H = sm + S * S;
-  float* sM = H + S * kDT;   // M_C (1 - O)
-  uint8_t* sMask = reinterpret_cast<uint8_t*>(sM + S * S);
+  float* sM = sm;
+  float* H = sM + S * S;
+  float* Bk = H + K * S * kDT;
+  uint8_t* sMask = reinterpret_cast<uint8_t*>(Bk + K * kDT * kDT);
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
@@ -138,31 +168,19 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
       sM[idx] = in ? d.dil_m[pix] : 0.0f;
       sMask[idx] = in ? d.dil_mask[pix] : (uint8_t)0;
     }
-    float acc[kDPPT];
-#pragma unroll
-    for (int i = 0; i < kDPPT; ++i) acc[i] = 0.0f;
-    for (int k = 0; k < K; ++k) {
-      const int r = dil_radius(k);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x)
-        sG[idx] = (sMask[idx] >> k) & 1u ? sM[idx] : 0.0f;
-      __syncthreads();
-      hsum(sG, H, S, h, r);
-      __syncthreads();
-      const float w = d.L.dil_w[k];
-#pragma unroll
-      for (int i = 0; i < kDPPT; ++i) {
-        const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
-        acc[i] -= w * vsum(H, h, r, rr, c);
-      }
-    }
+    __syncthreads();
+    hsums(GSrc{sM, sMask, S}, H, S, h, K);
+    __syncthreads();
+    vsums(H, Bk, S, h, K);
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < kDPPT; ++i) {
       const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
       const int X = x0 + c, Y = y0 + rr;
       if (X >= res || Y >= res) continue;
-      const long long pix = pb + (long long)Y * res + X;
-      d.gOu[pix] += acc[i];
+      float acc = 0.0f;
+      for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * Bk[k * kDT * kDT + local];
+      d.gOu[pb + (long long)Y * res + X] += acc;
     }
   }
 }
@@ -224,20 +242,35 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
   }
 }
 
-// Deterministic mode: each element sums its (tile, element) partials in emission order.
+// Deterministic mode: each element sums its (tile, element) partials over its tile rectangle in
+// row-major order; a tile's list is ordered by element id, so the pair is found by bisection.
 __global__ void k_grad_reduce(Dev d) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
-  const int b = d.off[g], n = d.cnt[g];
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int i = 0; i < n; ++i) {
-    const float4 v = d.partial[b + i];
-    r.x += v.x;
-    r.y += v.y;
-    r.z += v.z;
-    r.w += v.w;
+  const int4 rc = d.rect[g];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (rc.z >= rc.x && rc.w >= rc.y) {
+    const int p = d.elem_prob[g];
+    const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
+    for (int ty = rc.y; ty <= rc.w; ++ty)
+      for (int tx = rc.x; tx <= rc.z; ++tx) {
+        const uint2 rg = d.range[tb + ty * ntx + tx];
+        unsigned lo = rg.x, hi = rg.y;  // first entry >= g
+        while (lo < hi) {
+          const unsigned mid = (lo + hi) >> 1;
+          if (d.pair_sorted[mid] < g) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < rg.y && d.pair_sorted[lo] == g) {
+          const float4 v = d.partial[lo];
+          acc.x += v.x;
+          acc.y += v.y;
+          acc.z += v.z;
+          acc.w += v.w;
+        }
+      }
   }
-  d.dq[g] = r;
+  d.dq[g] = acc;
 }
 
 // Adam (bias-corrected, the update torch.optim.Adam performs), then the clamp of s.
@@ -271,8 +304,8 @@ __global__ void k_adam(Dev d) {
 
 static size_t dilate_smem(int K, bool backward) {
   const int h = dil_radius(K - 1), S = kDT + 2 * h;
-  size_t f = (size_t)S * S + (size_t)S * kDT;
-  if (backward) f += (size_t)S * S + ((size_t)S * S + 3) / 4;
+  size_t f = (size_t)S * S + (size_t)K * S * kDT + (size_t)K * kDT * kDT;
+  if (backward) f += ((size_t)S * S + 3) / 4;  // mask bytes
   return f * sizeof(float);
 }
 

@@ -13,7 +13,8 @@
 //
 // The forward pass saves, for every (tile, element) pair and pixel of the tile, the signed
 // distance and the closest segment; the adjoint reads them back instead of repeating the segment
-// loop, so only one pass over the pixel-segment pairs happens per iteration.
+// loop, so only one pass over the pixel-segment pairs happens per iteration.  Pixels farther than
+// the coverage margin from the outline carry sd = +-1e30 (saturated coverage, no gradient).
 #include <cfloat>
 
 #include "internal.h"
@@ -81,21 +82,80 @@ __device__ __forceinline__ float block_sum(float x, float* red) {
   return s;
 }
 
-constexpr int kSegCap = 1024;
+constexpr int kSegCap = 1024;   // container segments staged per chunk
+constexpr int kNearCap = 512;   // near segments staged per chunk of one (tile, element) pair
+constexpr int kListCap = 512;   // tile list entries ordered in shared memory
+constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
+
+// Orders the tile's element list [rg.x, rg.y) by element id into pair_sorted (ids are unique in a
+// tile, so the rank of an id is the number of smaller ids).  Lists up to kListCap are ranked in
+// shared memory and left in s_list; longer ones are ranked from global memory.
+template <int NT>
+__device__ __forceinline__ void order_tile_list(const Dev& d, uint2 rg, int* s_list) {
+  const int m = (int)(rg.y - rg.x);
+  const int* src = d.pair_elem + rg.x;
+  if (m <= kListCap) {
+    constexpr int PER = (kListCap + NT - 1) / NT;
+    int v[PER], r[PER];
+    for (int i = threadIdx.x; i < m; i += NT) s_list[i] = src[i];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      r[k] = 0;
+      v[k] = 0;
+      if (i < m) {
+        v[k] = s_list[i];
+        for (int j = 0; j < m; ++j) r[k] += s_list[j] < v[k] ? 1 : 0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < m) {
+        s_list[r[k]] = v[k];
+        d.pair_sorted[rg.x + r[k]] = v[k];
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < m; i += NT) {
+      const int vi = src[i];
+      int r = 0;
+      for (int j = 0; j < m; ++j) r += src[j] < vi ? 1 : 0;
+      d.pair_sorted[rg.x + r] = vi;
+    }
+  }
+  __syncthreads();
+}
 
 // ------------------------------------------------------------------------------------------------
 // Forward: per tile, per binned element (in element order), per pixel: signed distance, coverage,
 // composites Ihat = prod(1 - c) and prod(1 - tau c^pad); then the per-pixel loss terms.
+//
+// Per (tile, element) the block first splits the outline's segments.  A segment whose box meets
+// the tile's pixel-centre box grown by the coverage margin m = rho + pad (+ stroke half-width) is
+// "near": warp 0 appends it, in index order, to a shared list.  Every other segment lies farther
+// than m from every pixel of the tile; if it spans a pixel row and lies right of the grown box it
+// crosses that row's +x ray right of every pixel, so the other warps add its +-1 to a per-row
+// winding backdrop.  A pixel then runs the distance and crossing tests over the near list only: its
+// winding is backdrop + near crossings, and if no near segment is within m the coverage is
+// saturated (0 or 1, as the full loop would give), else the near minimum is the true distance.
 // ------------------------------------------------------------------------------------------------
 template <int T, int NT>
 __global__ void __launch_bounds__(NT) k_raster_fwd(Dev d, float* out_bw, float* out_tau) {
-  constexpr int NP = T * T, PPT = NP / NT;
-  __shared__ float4 s_seg[kSegCap];
-  __shared__ float2 s_seg2[kSegCap];
-  __shared__ float s_red[NT / 32];
+  constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
+  static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
+  __shared__ float4 s_seg[kNearCap];
+  __shared__ float2 s_seg2[kNearCap];
+  __shared__ int s_idx[kNearCap];
+  __shared__ int s_list[kListCap];
+  __shared__ int s_back[T];
+  __shared__ int s_near;
+  __shared__ float s_red[NW];
   if (*d.status & kStatusOverflow) return;
-  const uint32_t* vals = sorted_vals(d);
-  const float rho = d.L.rho_px, inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
     const int p = find_prob(d.prob_tile_base, d.n_probs, tile);
     const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
@@ -116,73 +176,138 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(Dev d, float* out_bw, float* 
       zc[k] = 0;
     }
     const uint2 rg = d.range[tile];
-    for (uint32_t pr = rg.x; pr < rg.y; ++pr) {
-      const int g = d.elem_of[vals[pr]];
+    const int m_pairs = (int)(rg.y - rg.x);
+    if (m_pairs > 0) order_tile_list<NT>(d, rg, s_list);
+    const float cx0 = (float)(tx * T) + 0.5f, cx1 = (float)(tx * T + T) - 0.5f;
+    const float cy0 = (float)(ty * T) + 0.5f, cy1 = (float)(ty * T + T) - 0.5f;
+    for (int pi = 0; pi < m_pairs; ++pi) {
+      const uint32_t pr = rg.x + (uint32_t)pi;
+      const int g = m_pairs <= kListCap ? s_list[pi] : d.pair_sorted[pr];
       const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
       const bool closed = d.elem_closed[g] != 0;
       const int ns = closed ? nv : nv - 1;
       const float4 tp = d.tpx[g], bb = d.bbox[g];
       const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)res;
-      float dx[PPT], dy[PPT];
+      const float mrg = d.L.rho_px + pad + hwpx;
+      const float mrg2 = mrg * mrg;
+      // tile pixel-centre box in the element frame, grown by the margin (+ rounding slack)
+      const float gx0 = (cx0 - tp.x) - tp.z - mrg - 0.01f, gx1 = (cx1 - tp.x) - tp.z + mrg + 0.01f;
+      const float gy0 = (cy0 - tp.y) - tp.w - mrg - 0.01f, gy1 = (cy1 - tp.y) - tp.w + mrg + 0.01f;
+      float dx[PPT], dy[PPT], best[PPT];
+      int bj[PPT], wn[PPT], idx[PPT];
       bool act[PPT];
-      SegQuery Q[PPT];
       bool any = false;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         dx[k] = (px[k] - tp.x) - tp.z;
         dy[k] = (py[k] - tp.y) - tp.w;
-        act[k] = in[k] && px[k] >= bb.x && px[k] <= bb.z && py[k] >= bb.y && py[k] <= bb.w;
+        act[k] = in[k] && dx[k] >= bb.x && dx[k] <= bb.z && dy[k] >= bb.y && dy[k] <= bb.w;
         any |= act[k];
-        Q[k].best = FLT_MAX;
-        Q[k].idx = 0;
-        Q[k].wn = 0;
+        best[k] = FLT_MAX;
+        idx[k] = 0;
+        bj[k] = -1;
+        wn[k] = 0;
       }
-      for (int c0 = 0; c0 < ns; c0 += kSegCap) {
-        const int cn = min(kSegCap, ns - c0);
-        __syncthreads();
-        for (int j = threadIdx.x; j < cn; j += NT) {
-          const int a_i = c0 + j, b_i = (a_i + 1 == nv) ? 0 : a_i + 1;
-          const float2 a = d.vrel[v0 + a_i], b = d.vrel[v0 + b_i];
-          const float ex = b.x - a.x, ey = b.y - a.y;
-          const float ee = ex * ex + ey * ey;
-          s_seg[j] = make_float4(a.x, a.y, ex, ey);
-          s_seg2[j] = make_float2(b.y, ee > 0.0f ? 1.0f / ee : 0.0f);
-        }
-        __syncthreads();
-        if (any) {
-          if (closed) {
-            for (int j = 0; j < cn; ++j) {
-              const float4 s = s_seg[j];
-              const float2 s2 = s_seg2[j];
-#pragma unroll
-              for (int k = 0; k < PPT; ++k)
-                if (act[k]) seg_update(Q[k], dx[k], dy[k], s, s2, c0 + j, true);
+      // row y of the pixels of tile row r, in the element frame, exactly as each pixel forms dy
+      for (int base = 0;; base += kNearCap) {
+        __syncthreads();  // the previous users of the shared lists are done
+        if (wid == 0) {
+          // ordered compaction of the near segments with positions in [base, base + kNearCap)
+          int cnt = 0;
+          for (int j0 = 0; j0 < ns; j0 += 32) {
+            const int j = j0 + lane;
+            bool nr = false;
+            float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 sb = make_float2(0.f, 0.f);
+            if (j < ns) {
+              sa = d.segA[v0 + j];
+              sb = d.segB[v0 + j];
+              const float bx = sa.x + sa.z;
+              nr = !(fmaxf(sa.x, bx) < gx0 || fminf(sa.x, bx) > gx1 ||
+                     fmaxf(sa.y, sb.x) < gy0 || fminf(sa.y, sb.x) > gy1);
             }
-          } else {
-            for (int j = 0; j < cn; ++j) {
-              const float4 s = s_seg[j];
-              const float2 s2 = s_seg2[j];
-#pragma unroll
-              for (int k = 0; k < PPT; ++k)
-                if (act[k]) seg_update(Q[k], dx[k], dy[k], s, s2, c0 + j, false);
+            const unsigned bal = __ballot_sync(0xffffffffu, nr);
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u)) - base;
+            if (nr && pos >= 0 && pos < kNearCap) {
+              s_seg[pos] = sa;
+              s_seg2[pos] = sb;
+              s_idx[pos] = j;
+            }
+            cnt += __popc(bal);
+          }
+          if (lane == 0) s_near = cnt;
+        } else if (base == 0 && closed) {
+          // winding backdrop of the far segments right of the tile
+          for (int r = threadIdx.x - 32; r < T; r += NT - 32) s_back[r] = 0;
+          __syncwarp();
+          asm volatile("bar.sync 1, %0;" ::"r"(NT - 32));
+          for (int j = threadIdx.x - 32; j < ns; j += NT - 32) {
+            const float4 sa = d.segA[v0 + j];
+            const float2 sb = d.segB[v0 + j];
+            const float bx = sa.x + sa.z;
+            if (fminf(sa.x, bx) <= gx1) continue;  // near, left or overlapping in x: per pixel
+            const bool up = sa.y < sb.x;
+            for (int r = 0; r < T; ++r) {
+              const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
+              const bool a_le = yr >= sa.y, b_le = yr >= sb.x;
+              if (a_le != b_le) atomicAdd(&s_back[r], up ? 1 : -1);
             }
           }
         }
+        __syncthreads();
+        const int total_near = s_near;
+        const int cn = min(kNearCap, total_near - base);
+        if (any && cn > 0) {
+          for (int j = 0; j < cn; ++j) {
+            const float4 s = s_seg[j];
+            const float2 s2 = s_seg2[j];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+              if (!act[k]) continue;
+              const float wx = dx[k] - s.x, wy = dy[k] - s.y;
+              const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
+              const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
+              const float d2 = fmaf(qx, qx, qy * qy);
+              if (d2 < best[k]) {
+                best[k] = d2;
+                bj[k] = j;
+              }
+              if (closed) {
+                const bool a_le = wy >= 0.0f, b_le = dy[k] - s2.x >= 0.0f;
+                const float cr = s.z * wy - s.w * wx;
+                if (a_le && !b_le && cr > 0.0f) wn[k] += 1;
+                if (!a_le && b_le && cr < 0.0f) wn[k] -= 1;
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < PPT; ++k)  // a minimum set in this chunk: its segment index
+            if (act[k] && best[k] != FLT_MAX && bj[k] >= 0) {
+              idx[k] = s_idx[bj[k]];
+              bj[k] = -1;
+            }
+        }
+        if (total_near <= base + kNearCap) break;
       }
       float2* sv = d.saved + (size_t)pr * NP;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        float sd = -1e30f;
+        float sd = -kFar;
         if (act[k]) {
-          const float dist = sqrtf(Q[k].best);
-          sd = closed ? (Q[k].wn != 0 ? dist : -dist) : hwpx - dist;
+          const int w = closed ? wn[k] + s_back[(threadIdx.x + k * NT) / T] : 0;
+          if (best[k] < mrg2) {
+            const float dist = sqrtf(best[k]);
+            sd = closed ? (w != 0 ? dist : -dist) : hwpx - dist;
+          } else {
+            sd = (closed && w != 0) ? kFar : -kFar;
+          }
         }
         const float x = sd * inv_rho;
         const float omc = Sfun(-x), cp = Sfun((sd + pad) * inv_rho);
         if (omc == 0.0f) zc[k] += 1;
         else keep[k] *= omc;
         keept[k] *= 1.0f - tau * cp;
-        sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(Q[k].idx));
+        sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(idx[k]));
       }
     }
     // per-pixel loss terms (Eq. 5, Eq. 6 surrogate, downward force)
@@ -210,7 +335,6 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(Dev d, float* out_bw, float* 
     lo = block_sum<NT>(lo, s_red);
     ld = block_sum<NT>(ld, s_red);
     if (threadIdx.x == 0) d.lossA[tile] = make_float4(lc, lo, ld, 0.0f);
-    (void)rho;
   }
 }
 
@@ -224,7 +348,6 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
   constexpr int NP = T * T, PPT = NP / NT;
   __shared__ float s_red[4][NT / 32];
   if (*d.status & kStatusOverflow) return;
-  const uint32_t* vals = sorted_vals(d);
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
@@ -259,9 +382,8 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
       }
     }
     for (uint32_t pr = rg.x; pr < rg.y; ++pr) {
-      const int emit = (int)vals[pr];
-      const int g = d.elem_of[emit];
-      const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
+      const int g = d.pair_sorted[pr];
+      const int v0 = d.elem_voff[g];
       const bool closed = d.elem_closed[g] != 0;
       const float4 tp = d.tpx[g];
       const float s_inv = 1.0f / d.q[g].w;
@@ -281,9 +403,10 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
         const float gsd = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
         if (gsd == 0.0f) continue;
         const int j = __float_as_int(rec.y);
-        const float2 a = d.vrel[v0 + j], b = d.vrel[v0 + (j + 1 == nv ? 0 : j + 1)];
+        const float4 sa = d.segA[v0 + j];
+        const float2 a = make_float2(sa.x, sa.y);
         const float dx = (px[k] - tp.x) - tp.z, dy = (py[k] - tp.y) - tp.w;
-        const float ex = b.x - a.x, ey = b.y - a.y, ee = ex * ex + ey * ey;
+        const float ex = sa.z, ey = sa.w, ee = ex * ex + ey * ey;
         const float wx = dx - a.x, wy = dy - a.y;
         const float u = ee > 0.0f ? __saturatef((wx * ex + wy * ey) / ee) : 0.0f;
         const float qx = fmaf(u, ex, a.x), qy = fmaf(u, ey, a.y);  // closest point, rel. to t
@@ -335,7 +458,7 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
           r.w += s_red[3][i];
         }
         if (d.deterministic) {
-          d.partial[emit] = r;
+          d.partial[pr] = r;
         } else {
           atomicAdd(&d.dq[g].x, r.x);
           atomicAdd(&d.dq[g].y, r.y);
