@@ -35,7 +35,8 @@ struct collage_s {
   int level = -1;
   std::vector<int> res, ntx, tile_base, dtile_base;
   std::vector<long long> pix_base;
-  int raster_grid = 0;
+  int pair_grid = 0;  // grid of the per-pair raster kernels
+  int tile_grid = 0;  // grid of the per-tile composite
   int sms = 1;
   // device memory
   Dev d{};
@@ -256,6 +257,20 @@ static void flatten(const collage_problem& p, int e, int spc, std::vector<float2
 // --------------------------------------------------------------------------------------------
 // Level setup
 // --------------------------------------------------------------------------------------------
+// Persistent grids: resident blocks per SM times the SM count; plain grids: one block per work
+// item (pairs up to the capacity, every tile).
+static void set_grids(collage_t h) {
+  int pper = 1, tper = 1;
+  raster_blocks_per_sm(h->d.tile, &pper, &tper);
+  if (h->opt.persistent) {
+    h->pair_grid = h->sms * pper;
+    h->tile_grid = std::min(h->d.total_tiles, h->sms * tper);
+  } else {
+    h->pair_grid = std::max(h->d.cap, 1);
+    h->tile_grid = h->d.total_tiles;
+  }
+}
+
 static collage_status ensure_pairs(collage_t h, size_t cap) {
   const size_t tt = (size_t)h->d.tile * h->d.tile;
   if (cap <= h->pair_cap && tt == h->saved_tile) return COLLAGE_OK;
@@ -265,12 +280,16 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   h->pair_cap = 0;
   Dev& d = h->d;
   CK(h, dmalloc(h->pair_bufs, d.pair_elem, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_tile, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_live, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_sorted, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_slot, cap));
   CK(h, dmalloc(h->pair_bufs, d.partial, cap));
   CK(h, dmalloc(h->pair_bufs, d.saved, cap * tt));
   h->pair_cap = cap;
   h->saved_tile = tt;
   d.cap = (int)std::min<size_t>(cap, 0x7fffffff);
+  set_grids(h);
   return COLLAGE_OK;
 }
 
@@ -348,7 +367,7 @@ static collage_status setup_level(collage_t h, int level) {
   const size_t need = (size_t)h->h_ctl[2];
   st = ensure_pairs(h, std::max<size_t>(need + need / 2 + 256, 1024));
   if (st) return st;
-  h->raster_grid = o.persistent ? std::min(d.total_tiles, raster_fwd_max_grid(T)) : d.total_tiles;
+  set_grids(h);
   h->level = level;
   return COLLAGE_OK;
 }
@@ -372,14 +391,14 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   STEP_(launch_scan(d, s));
   STEP_(launch_bin(d, s));
   MARK_(2);
-  STEP_(launch_raster_fwd(d, s, h->raster_grid, out_bw, out_tau));
+  STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau));
   MARK_(3);
   if (dil) {
     STEP_(launch_dilate(d, s, false));
     STEP_(launch_dilate(d, s, true));
   }
   MARK_(4);
-  if (bwd) STEP_(launch_raster_bwd(d, s, h->raster_grid));
+  if (bwd) STEP_(launch_raster_bwd(d, s, h->pair_grid));
   MARK_(5);
   if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
   MARK_(6);
@@ -880,10 +899,10 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   out->total_pixels = h->d.total_pix;
   out->pair_capacity = h->d.cap;
   out->last_pairs = h->h_ctl ? h->h_ctl[2] : 0;
-  // transform, tile scan, emit, raster fwd, (2 dilation), raster bwd, (gradient reduce), loss,
-  // Adam
+  // transform, tile scan, emit, pair distances, composite, (2 dilation), raster bwd, (gradient
+  // reduce), loss, Adam
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 4 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 2;
+  out->kernels_per_iter = 5 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 2;
   return COLLAGE_OK;
 }
 

@@ -58,46 +58,79 @@ __device__ __forceinline__ float2 vertex_px(const float2 v, double c, double sn,
   return make_float2((float)x, (float)y);
 }
 
-// One warp per element: segment records (start, direction, end y, 1/|e|^2), translation in pixels
-// as a float hi/lo pair, outline box grown by the coverage margin, tile rectangle, and the
-// per-tile element counts of the counting sort.
-__global__ void k_transform(Dev d, int zero_grad) {
-  const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (g >= d.n_elems) return;
+// One block per element: segment records (start, direction, end y, 1/|e|^2) of the vertices
+// relative to the translation, translation in pixels as a float hi/lo pair, outline box grown by
+// the coverage margin, tile rectangle, and the per-tile element counts of the counting sort.
+// Lanes own consecutive vertices; a segment's end point is the next lane's start point (shuffled),
+// so each vertex is rotated once in double.
+constexpr int kTfThreads = 128;
+__global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) {
+  __shared__ double s_cs[3];
+  __shared__ float s_box[4][kTfThreads / 32];
+  __shared__ int4 s_rect;
+  const int g = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = d.elem_prob[g];
   const int res = d.prob_res[p];
   const float4 q = d.q[g];
-  double sn, c;
-  sincos((double)q.z, &sn, &c);
-  const double sc = (double)q.w * (double)res;
-  const int v0 = d.elem_voff[g], v1 = d.elem_voff[g + 1], nv = v1 - v0;
+  if (threadIdx.x == 0) {
+    double sn, c;
+    sincos((double)q.z, &sn, &c);
+    s_cs[0] = c;
+    s_cs[1] = sn;
+    s_cs[2] = (double)q.w * (double)res;
+  }
+  __syncthreads();
+  const double c = s_cs[0], sn = s_cs[1], sc = s_cs[2];
+  const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
   const bool closed = d.elem_closed[g] != 0;
   float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
-  for (int k = lane; k < nv; k += 32) {
-    const float2 a = vertex_px(d.vloc[v0 + k], c, sn, sc);
-    xmin = fminf(xmin, a.x);
-    xmax = fmaxf(xmax, a.x);
-    ymin = fminf(ymin, a.y);
-    ymax = fmaxf(ymax, a.y);
-    float4 sa = make_float4(a.x, a.y, 0.f, 0.f);
-    float2 sb = make_float2(a.y, 0.f);
-    if (closed || k + 1 < nv) {
-      const float2 b = vertex_px(d.vloc[v0 + (k + 1 == nv ? 0 : k + 1)], c, sn, sc);
-      const float ex = b.x - a.x, ey = b.y - a.y, ee = ex * ex + ey * ey;
-      sa.z = ex;
-      sa.w = ey;
-      sb = make_float2(b.y, ee > 0.0f ? 1.0f / ee : 0.0f);
+  for (int k0 = wid * 32; k0 < nv; k0 += kTfThreads) {  // warp-uniform trip count
+    const int k = k0 + lane;
+    float2 a = make_float2(0.f, 0.f);
+    if (k < nv) {
+      a = vertex_px(d.vloc[v0 + k], c, sn, sc);
+      xmin = fminf(xmin, a.x);
+      xmax = fmaxf(xmax, a.x);
+      ymin = fminf(ymin, a.y);
+      ymax = fmaxf(ymax, a.y);
     }
-    d.segA[v0 + k] = sa;
-    d.segB[v0 + k] = sb;
+    float2 b;
+    b.x = __shfl_down_sync(0xffffffffu, a.x, 1);
+    b.y = __shfl_down_sync(0xffffffffu, a.y, 1);
+    const int kb = k + 1 == nv ? 0 : k + 1;
+    if (k < nv && (lane == 31 || k + 1 == nv)) b = vertex_px(d.vloc[v0 + kb], c, sn, sc);
+    if (k < nv) {
+      float4 sa = make_float4(a.x, a.y, 0.f, 0.f);
+      float2 sb = make_float2(a.y, 0.f);
+      if (closed || k + 1 < nv) {
+        const float ex = b.x - a.x, ey = b.y - a.y, ee = ex * ex + ey * ey;
+        sa.z = ex;
+        sa.w = ey;
+        sb = make_float2(b.y, ee > 0.0f ? 1.0f / ee : 0.0f);
+      }
+      d.segA[v0 + k] = sa;
+      d.segB[v0 + k] = sb;
+    }
   }
   xmin = warp_min(xmin);
   ymin = warp_min(ymin);
   xmax = warp_max(xmax);
   ymax = warp_max(ymax);
-  int4 r = make_int4(0, 0, -1, -1);
   if (lane == 0) {
+    s_box[0][wid] = xmin;
+    s_box[1][wid] = ymin;
+    s_box[2][wid] = xmax;
+    s_box[3][wid] = ymax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kTfThreads / 32; ++w) {
+      xmin = fminf(xmin, s_box[0][w]);
+      ymin = fminf(ymin, s_box[1][w]);
+      xmax = fmaxf(xmax, s_box[2][w]);
+      ymax = fmaxf(ymax, s_box[3][w]);
+    }
     const double tx = (double)q.x * res, ty = (double)q.y * res;
     const float hx = (float)tx, hy = (float)ty;
     d.tpx[g] = make_float4(hx, hy, (float)(tx - (double)hx), (float)(ty - (double)hy));
@@ -106,56 +139,80 @@ __global__ void k_transform(Dev d, int zero_grad) {
     const float m = d.L.rho_px + d.L.pad_px + hw * (float)res + 0.01f;
     d.bbox[g] = make_float4(xmin - m, ymin - m, xmax + m, ymax + m);
     const bool finite = isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && q.w > 0.0f;
+    int4 r = make_int4(0, 0, -1, -1);
     if (finite) r = bin_rect(q, d.elem_rbin[g], hw, res, d.tile, d.L.rho_px, d.L.pad_px);
     else atomicOr(d.status, kStatusBadParam);
     d.rect[g] = r;
+    s_rect = r;
     if (zero_grad) d.dq[g] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  r.x = __shfl_sync(0xffffffffu, r.x, 0);
-  r.y = __shfl_sync(0xffffffffu, r.y, 0);
-  r.z = __shfl_sync(0xffffffffu, r.z, 0);
-  r.w = __shfl_sync(0xffffffffu, r.w, 0);
+  __syncthreads();
+  const int4 r = s_rect;
   if (r.z < r.x || r.w < r.y) return;
   const int w = r.z - r.x + 1, n = w * (r.w - r.y + 1);
   const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
-  for (int i = lane; i < n; i += 32) atomicAdd(&d.tile_cnt[tb + (r.y + i / w) * ntx + r.x + i % w], 1);
+  for (int i = threadIdx.x; i < n; i += kTfThreads)
+    atomicAdd(&d.tile_cnt[tb + (r.y + i / w) * ntx + r.x + i % w], 1);
 }
 
-// Exclusive scan of the per-tile counts into [begin, end) ranges (one block; a contiguous chunk
-// per thread).  The total is the pair count; above the capacity the overflow bit is latched.
+// Exclusive scan of the per-tile counts into [begin, end) ranges: one block; per round a thread
+// owns 16 consecutive tiles (loaded as four int4), scans them in registers, and the block scans
+// the per-thread totals.  The total is the pair count; above the capacity the overflow bit is
+// latched.
+constexpr int kScanPer = 16;
 __global__ void __launch_bounds__(1024) k_tile_scan(Dev d) {
   __shared__ int wsum[32];
-  const int n = d.total_tiles, t = threadIdx.x;
-  const int per = (n + 1023) / 1024;
-  const int b = min(t * per, n), e = min(b + per, n);
-  int s = 0;
-  for (int i = b; i < e; ++i) s += d.tile_cnt[i];
-  const int lane = t & 31, w = t >> 5;
-  int x = s;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    int ws = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, ws, o);
-      if (lane >= o) ws += y;
+  const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int carry = 0;
+  for (int base = 0; base < n; base += 1024 * kScanPer) {
+    const int b = base + t * kScanPer;
+    int v[kScanPer];
+    if (b + kScanPer <= n) {
+      const int4* src = reinterpret_cast<const int4*>(d.tile_cnt + b);
+#pragma unroll
+      for (int i = 0; i < kScanPer / 4; ++i) {
+        const int4 x = src[i];
+        v[4 * i] = x.x;
+        v[4 * i + 1] = x.y;
+        v[4 * i + 2] = x.z;
+        v[4 * i + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kScanPer; ++i) v[i] = b + i < n ? d.tile_cnt[b + i] : 0;
     }
-    wsum[lane] = ws;  // inclusive
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) s += v[i];
+    int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int ws = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      wsum[lane] = ws;  // inclusive
+    }
+    __syncthreads();
+    int run = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
+    const int round_total = wsum[31];
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+      if (b + i < n) d.range[b + i] = make_uint2((uint32_t)run, (uint32_t)(run + v[i]));
+      run += v[i];
+    }
+    carry += round_total;
+    __syncthreads();  // wsum is reused by the next round
   }
-  __syncthreads();
-  int run = x - s + (w > 0 ? wsum[w - 1] : 0);
-  for (int i = b; i < e; ++i) {
-    const int c = d.tile_cnt[i];
-    d.range[i] = make_uint2((uint32_t)run, (uint32_t)(run + c));
-    run += c;
-  }
-  if (t == 1023) {
-    *d.total_pairs = run;
-    if (run > d.cap) atomicOr(d.status, kStatusOverflow);
+  if (t == 0) {
+    *d.total_pairs = carry;
+    if (carry > d.cap) atomicOr(d.status, kStatusOverflow);
   }
 }
 
@@ -174,13 +231,15 @@ __global__ void k_emit(Dev d) {
     const int t = tb + (r.y + i / w) * ntx + r.x + i % w;
     const int slot = atomicSub(&d.tile_cnt[t], 1) - 1;
     const unsigned pos = d.range[t].x + (unsigned)slot;
-    if (pos < (unsigned)d.cap) d.pair_elem[pos] = g;
+    if (pos < (unsigned)d.cap) {
+      d.pair_elem[pos] = g;
+      d.pair_tile[pos] = t;
+    }
   }
 }
 
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad) {
-  const int threads = 256, warps = threads / 32;
-  k_transform<<<(d.n_elems + warps - 1) / warps, threads, 0, s>>>(d, zero_grad ? 1 : 0);
+  k_transform<<<d.n_elems, kTfThreads, 0, s>>>(d, zero_grad ? 1 : 0);
   return cudaGetLastError();
 }
 

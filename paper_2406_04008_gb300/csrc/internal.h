@@ -68,8 +68,11 @@ struct Dev {
   int* tile_cnt;                // [total_tiles] counting-sort counts (zero between iterations)
   int* total_pairs;             // [1]
   int cap;                      // pair capacity
-  int* pair_elem;               // [cap] element of each pair, tile ranges, in emission order
-  int* pair_sorted;             // [cap] the same, each tile's list in increasing element order
+  int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
+  int* pair_tile;               // [cap] tile of each pair slot
+  uint8_t* pair_live;           // [cap] 1 if some pixel of the pair has non-saturated coverage
+  int* pair_sorted;             // [cap] each tile's elements in increasing element order
+  int* pair_slot;               // [cap] the pair slot of each pair_sorted entry
   uint2* range;                 // [total_tiles] [begin, end) into the pair arrays
   float2* saved;                // [cap * tile*tile] (sd px, closest segment as int bits)
   float* covc;                  // [pix] container coverage
@@ -94,15 +97,17 @@ cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
 cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
 cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit pairs into tile ranges
 cudaError_t launch_container(const Dev& d, cudaStream_t s);
-cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int grid, float* out_bw,
-                              float* out_tau);
+// per-pair signed distances, then the per-tile composite and loss partials
+cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid,
+                              float* out_bw, float* out_tau);
 cudaError_t prepare_dilate(int n_dil);  // sets dynamic shared memory limits (not capturable)
 cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward);
-cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int grid);
+cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid);
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step);
 cudaError_t launch_adam(const Dev& d, cudaStream_t s);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
-int raster_fwd_max_grid(int tile);  // resident blocks for a persistent grid (per SM)
+// resident blocks per SM of the pair kernels and of the per-tile composite (persistent grids)
+void raster_blocks_per_sm(int tile, int* pair_per_sm, int* tile_per_sm);
 
 }  // namespace collage

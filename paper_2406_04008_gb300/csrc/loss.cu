@@ -185,16 +185,21 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
   }
 }
 
-// One block per problem: fixed-order sums of the tile partials (float per thread over a strided
-// subset with independent loads in flight, double across threads), then Eq. 8.
+// One block per problem: fixed-order float sums of the tile partials (strided per thread, then a
+// shuffle tree within and across warps), then Eq. 8.  Float throughout: FP64 arithmetic is slow on
+// this part and 1e-7 relative is ample for a sum of non-negative partials.
 constexpr int kLossThreads = 1024;
+__device__ __forceinline__ float warp_sum_f(float x) {
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
 __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
-  __shared__ double s_red[4][kLossThreads / 32];
+  __shared__ float s_red[4][kLossThreads / 32];
   const int p = blockIdx.x;
   const int t0 = d.prob_tile_base[p], t1 = d.prob_tile_base[p + 1];
   const bool use_u = d.L.gamma != 0.0f && d.L.n_dil > 0;
   float a = 0.f, b = 0.f, c = 0.f, u = 0.f;
-#pragma unroll 8
+#pragma unroll 4
   for (int t = t0 + (int)threadIdx.x; t < t1; t += kLossThreads) {
     const float4 v = d.lossA[t];
     a += v.x;
@@ -203,42 +208,37 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
   }
   if (use_u) {
     const int u0 = d.prob_dtile_base[p], u1 = d.prob_dtile_base[p + 1];
-#pragma unroll 8
+#pragma unroll 4
     for (int t = u0 + (int)threadIdx.x; t < u1; t += kLossThreads) u += d.lossU[t];
   }
-  double A = a, B = b, Cc = c, U = u;
-  for (int o = 16; o; o >>= 1) {
-    A += __shfl_xor_sync(0xffffffffu, A, o);
-    B += __shfl_xor_sync(0xffffffffu, B, o);
-    Cc += __shfl_xor_sync(0xffffffffu, Cc, o);
-    U += __shfl_xor_sync(0xffffffffu, U, o);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    s_red[0][w] = A;
-    s_red[1][w] = B;
-    s_red[2][w] = Cc;
-    s_red[3][w] = U;
+  a = warp_sum_f(a);
+  b = warp_sum_f(b);
+  c = warp_sum_f(c);
+  u = warp_sum_f(u);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_red[0][w] = a;
+    s_red[1][w] = b;
+    s_red[2][w] = c;
+    s_red[3][w] = u;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double SA = 0, SB = 0, SC = 0, SU = 0;
-    for (int i = 0; i < kLossThreads / 32; ++i) {
-      SA += s_red[0][i];
-      SB += s_red[1][i];
-      SC += s_red[2][i];
-      SU += s_red[3][i];
+  if (w == 0) {
+    a = warp_sum_f(s_red[0][lane]);
+    b = warp_sum_f(s_red[1][lane]);
+    c = warp_sum_f(s_red[2][lane]);
+    u = warp_sum_f(s_red[3][lane]);
+    if (lane == 0) {
+      const float np = (float)d.prob_res[p] * (float)d.prob_res[p];
+      const float Lc = a / np, Lo = b / np, Ld = c / np;
+      float* out = d.loss_terms + 5 * p;
+      out[0] = Lc;
+      out[1] = Lo;
+      out[2] = u;
+      out[3] = Ld;
+      out[4] = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * u + d.L.delta * Ld;
+      if (count_step && p == 0 && !(*d.status & kStatusOverflow)) *d.step += 1;
     }
-    const double np = (double)d.prob_res[p] * (double)d.prob_res[p];
-    const double Lc = SA / np, Lo = SB / np, Ld = SC / np;
-    const double L = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * SU + d.L.delta * Ld;
-    float* out = d.loss_terms + 5 * p;
-    out[0] = (float)Lc;
-    out[1] = (float)Lo;
-    out[2] = (float)SU;
-    out[3] = (float)Ld;
-    out[4] = (float)L;
-    if (count_step && p == 0 && !(*d.status & kStatusOverflow)) *d.step += 1;
   }
 }
 
@@ -262,7 +262,7 @@ __global__ void k_grad_reduce(Dev d) {
           else hi = mid;
         }
         if (lo < rg.y && d.pair_sorted[lo] == g) {
-          const float4 v = d.partial[lo];
+          const float4 v = d.partial[d.pair_slot[lo]];
           acc.x += v.x;
           acc.y += v.y;
           acc.z += v.z;

@@ -87,247 +87,259 @@ constexpr int kNearCap = 512;   // near segments staged per chunk of one (tile, 
 constexpr int kListCap = 512;   // tile list entries ordered in shared memory
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
 
-// Orders the tile's element list [rg.x, rg.y) by element id into pair_sorted (ids are unique in a
-// tile, so the rank of an id is the number of smaller ids).  Lists up to kListCap are ranked in
-// shared memory and left in s_list; longer ones are ranked from global memory.
-template <int NT>
-__device__ __forceinline__ void order_tile_list(const Dev& d, uint2 rg, int* s_list) {
-  const int m = (int)(rg.y - rg.x);
-  const int* src = d.pair_elem + rg.x;
-  if (m <= kListCap) {
-    constexpr int PER = (kListCap + NT - 1) / NT;
-    int v[PER], r[PER];
-    for (int i = threadIdx.x; i < m; i += NT) s_list[i] = src[i];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      r[k] = 0;
-      v[k] = 0;
-      if (i < m) {
-        v[k] = s_list[i];
-        for (int j = 0; j < m; ++j) r[k] += s_list[j] < v[k] ? 1 : 0;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < m) {
-        s_list[r[k]] = v[k];
-        d.pair_sorted[rg.x + r[k]] = v[k];
-      }
-    }
-  } else {
-    for (int i = threadIdx.x; i < m; i += NT) {
-      const int vi = src[i];
-      int r = 0;
-      for (int j = 0; j < m; ++j) r += src[j] < vi ? 1 : 0;
-      d.pair_sorted[rg.x + r] = vi;
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& p, int& tx, int& ty,
+                                            int& res) {
+  p = find_prob(d.prob_tile_base, d.n_probs, tile);
+  const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p];
+  res = d.prob_res[p];
+  tx = lt % ntx;
+  ty = lt / ntx;
 }
 
 // ------------------------------------------------------------------------------------------------
-// Forward: per tile, per binned element (in element order), per pixel: signed distance, coverage,
-// composites Ihat = prod(1 - c) and prod(1 - tau c^pad); then the per-pixel loss terms.
+// Signed distances of one (tile, element) pair per block.
 //
-// Per (tile, element) the block first splits the outline's segments.  A segment whose box meets
-// the tile's pixel-centre box grown by the coverage margin m = rho + pad (+ stroke half-width) is
-// "near": warp 0 appends it, in index order, to a shared list.  Every other segment lies farther
-// than m from every pixel of the tile; if it spans a pixel row and lies right of the grown box it
-// crosses that row's +x ray right of every pixel, so the other warps add its +-1 to a per-row
-// winding backdrop.  A pixel then runs the distance and crossing tests over the near list only: its
-// winding is backdrop + near crossings, and if no near segment is within m the coverage is
-// saturated (0 or 1, as the full loop would give), else the near minimum is the true distance.
+// The block first splits the outline's segments.  A segment whose box meets the tile's pixel-centre
+// box grown by the coverage margin m = rho + pad (+ stroke half-width) is "near": warp 0 appends
+// it, in index order, to a shared list.  Every other segment lies farther than m from every pixel
+// of the tile; if it spans a pixel row and lies right of the grown box it crosses that row's +x
+// ray right of every pixel, so the other warps add its +-1 to a per-row winding backdrop.  A pixel
+// then runs the distance and crossing tests over the near list only: its winding is backdrop +
+// near crossings; if no near segment is within m the coverage is saturated (0 or 1, as the full
+// loop would give) and sd = +-1e30, else the near minimum is the true distance.
 // ------------------------------------------------------------------------------------------------
 template <int T, int NT>
-__global__ void __launch_bounds__(NT) k_raster_fwd(Dev d, float* out_bw, float* out_tau) {
+__global__ void __launch_bounds__(NT) k_pair_sd(Dev d) {
   constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
   static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
   __shared__ float4 s_seg[kNearCap];
   __shared__ float2 s_seg2[kNearCap];
   __shared__ int s_idx[kNearCap];
-  __shared__ int s_list[kListCap];
   __shared__ int s_back[T];
   __shared__ int s_near;
-  __shared__ float s_red[NW];
   if (*d.status & kStatusOverflow) return;
-  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
-    const int p = find_prob(d.prob_tile_base, d.n_probs, tile);
-    const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
-    const int tx = lt % ntx, ty = lt / ntx;
-    const long long pixbase = d.prob_pix_base[p];
-    float px[PPT], py[PPT], keep[PPT], keept[PPT];
-    int zc[PPT];
-    bool in[PPT];
+  const int total = *d.total_pairs;
+  for (int slot = blockIdx.x; slot < total; slot += gridDim.x) {
+    const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
+    int p, tx, ty, res;
+    tile_coords(d, tile, T, p, tx, ty, res);
+    const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
+    const bool closed = d.elem_closed[g] != 0;
+    const int ns = closed ? nv : nv - 1;
+    const float4 tp = d.tpx[g], bb = d.bbox[g];
+    const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)res;
+    const float mrg = d.L.rho_px + pad + hwpx;
+    const float mrg2 = mrg * mrg;
+    // tile pixel-centre box in the element frame, grown by the margin (+ rounding slack)
+    const float cx0 = (float)(tx * T) + 0.5f, cx1 = (float)(tx * T + T) - 0.5f;
+    const float cy0 = (float)(ty * T) + 0.5f, cy1 = (float)(ty * T + T) - 0.5f;
+    const float gx0 = (cx0 - tp.x) - tp.z - mrg - 0.01f, gx1 = (cx1 - tp.x) - tp.z + mrg + 0.01f;
+    const float gy0 = (cy0 - tp.y) - tp.w - mrg - 0.01f, gy1 = (cy1 - tp.y) - tp.w + mrg + 0.01f;
+    float dx[PPT], dy[PPT], best[PPT];
+    int bj[PPT], wn[PPT], idx[PPT];
+    bool act[PPT];
+    bool any = false;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int local = threadIdx.x + k * NT;
       const int X = tx * T + local % T, Y = ty * T + local / T;
-      in[k] = X < res && Y < res;
-      px[k] = (float)X + 0.5f;
-      py[k] = (float)Y + 0.5f;
-      keep[k] = 1.0f;
-      keept[k] = 1.0f;
-      zc[k] = 0;
+      dx[k] = ((float)X + 0.5f - tp.x) - tp.z;
+      dy[k] = ((float)Y + 0.5f - tp.y) - tp.w;
+      act[k] = X < res && Y < res && dx[k] >= bb.x && dx[k] <= bb.z && dy[k] >= bb.y && dy[k] <= bb.w;
+      any |= act[k];
+      best[k] = FLT_MAX;
+      idx[k] = 0;
+      bj[k] = -1;
+      wn[k] = 0;
     }
-    const uint2 rg = d.range[tile];
-    const int m_pairs = (int)(rg.y - rg.x);
-    if (m_pairs > 0) order_tile_list<NT>(d, rg, s_list);
-    const float cx0 = (float)(tx * T) + 0.5f, cx1 = (float)(tx * T + T) - 0.5f;
-    const float cy0 = (float)(ty * T) + 0.5f, cy1 = (float)(ty * T + T) - 0.5f;
-    for (int pi = 0; pi < m_pairs; ++pi) {
-      const uint32_t pr = rg.x + (uint32_t)pi;
-      const int g = m_pairs <= kListCap ? s_list[pi] : d.pair_sorted[pr];
-      const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
-      const bool closed = d.elem_closed[g] != 0;
-      const int ns = closed ? nv : nv - 1;
-      const float4 tp = d.tpx[g], bb = d.bbox[g];
-      const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)res;
-      const float mrg = d.L.rho_px + pad + hwpx;
-      const float mrg2 = mrg * mrg;
-      // tile pixel-centre box in the element frame, grown by the margin (+ rounding slack)
-      const float gx0 = (cx0 - tp.x) - tp.z - mrg - 0.01f, gx1 = (cx1 - tp.x) - tp.z + mrg + 0.01f;
-      const float gy0 = (cy0 - tp.y) - tp.w - mrg - 0.01f, gy1 = (cy1 - tp.y) - tp.w + mrg + 0.01f;
-      float dx[PPT], dy[PPT], best[PPT];
-      int bj[PPT], wn[PPT], idx[PPT];
-      bool act[PPT];
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        dx[k] = (px[k] - tp.x) - tp.z;
-        dy[k] = (py[k] - tp.y) - tp.w;
-        act[k] = in[k] && dx[k] >= bb.x && dx[k] <= bb.z && dy[k] >= bb.y && dy[k] <= bb.w;
-        any |= act[k];
-        best[k] = FLT_MAX;
-        idx[k] = 0;
-        bj[k] = -1;
-        wn[k] = 0;
-      }
-      // row y of the pixels of tile row r, in the element frame, exactly as each pixel forms dy
-      for (int base = 0;; base += kNearCap) {
-        __syncthreads();  // the previous users of the shared lists are done
-        if (wid == 0) {
-          // ordered compaction of the near segments with positions in [base, base + kNearCap)
-          int cnt = 0;
-          for (int j0 = 0; j0 < ns; j0 += 32) {
-            const int j = j0 + lane;
-            bool nr = false;
-            float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 sb = make_float2(0.f, 0.f);
-            if (j < ns) {
-              sa = d.segA[v0 + j];
-              sb = d.segB[v0 + j];
-              const float bx = sa.x + sa.z;
-              nr = !(fmaxf(sa.x, bx) < gx0 || fminf(sa.x, bx) > gx1 ||
-                     fmaxf(sa.y, sb.x) < gy0 || fminf(sa.y, sb.x) > gy1);
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, nr);
-            const int pos = cnt + __popc(bal & ((1u << lane) - 1u)) - base;
-            if (nr && pos >= 0 && pos < kNearCap) {
-              s_seg[pos] = sa;
-              s_seg2[pos] = sb;
-              s_idx[pos] = j;
-            }
-            cnt += __popc(bal);
-          }
-          if (lane == 0) s_near = cnt;
-        } else if (base == 0 && closed) {
-          // winding backdrop of the far segments right of the tile
-          for (int r = threadIdx.x - 32; r < T; r += NT - 32) s_back[r] = 0;
-          __syncwarp();
-          asm volatile("bar.sync 1, %0;" ::"r"(NT - 32));
-          for (int j = threadIdx.x - 32; j < ns; j += NT - 32) {
-            const float4 sa = d.segA[v0 + j];
-            const float2 sb = d.segB[v0 + j];
+    for (int base = 0;; base += kNearCap) {
+      __syncthreads();  // the previous users of the shared lists are done
+      if (wid == 0) {
+        // ordered compaction of the near segments with positions in [base, base + kNearCap)
+        int cnt = 0;
+        for (int j0 = 0; j0 < ns; j0 += 32) {
+          const int j = j0 + lane;
+          bool nr = false;
+          float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
+          float2 sb = make_float2(0.f, 0.f);
+          if (j < ns) {
+            sa = d.segA[v0 + j];
+            sb = d.segB[v0 + j];
             const float bx = sa.x + sa.z;
-            if (fminf(sa.x, bx) <= gx1) continue;  // near, left or overlapping in x: per pixel
-            const bool up = sa.y < sb.x;
-            for (int r = 0; r < T; ++r) {
-              const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
-              const bool a_le = yr >= sa.y, b_le = yr >= sb.x;
-              if (a_le != b_le) atomicAdd(&s_back[r], up ? 1 : -1);
+            nr = !(fmaxf(sa.x, bx) < gx0 || fminf(sa.x, bx) > gx1 || fmaxf(sa.y, sb.x) < gy0 ||
+                   fminf(sa.y, sb.x) > gy1);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, nr);
+          const int pos = cnt + __popc(bal & ((1u << lane) - 1u)) - base;
+          if (nr && pos >= 0 && pos < kNearCap) {
+            s_seg[pos] = sa;
+            s_seg2[pos] = sb;
+            s_idx[pos] = j;
+          }
+          cnt += __popc(bal);
+        }
+        if (lane == 0) s_near = cnt;
+      } else if (base == 0 && closed) {
+        // winding backdrop of the far segments right of the tile
+        for (int r = threadIdx.x - 32; r < T; r += NT - 32) s_back[r] = 0;
+        asm volatile("bar.sync 1, %0;" ::"r"(NT - 32));
+        for (int j = threadIdx.x - 32; j < ns; j += NT - 32) {
+          const float4 sa = d.segA[v0 + j];
+          const float2 sb = d.segB[v0 + j];
+          if (fminf(sa.x, sa.x + sa.z) <= gx1) continue;  // near, left or overlapping in x
+          const int up = sa.y < sb.x ? 1 : -1;
+          for (int r = 0; r < T; ++r) {
+            const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;  // as a pixel forms dy
+            if ((yr >= sa.y) != (yr >= sb.x)) atomicAdd(&s_back[r], up);
+          }
+        }
+      }
+      __syncthreads();
+      const int total_near = s_near;
+      const int cn = min(kNearCap, total_near - base);
+      if (any && cn > 0) {
+        for (int j = 0; j < cn; ++j) {
+          const float4 s = s_seg[j];
+          const float2 s2 = s_seg2[j];
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (!act[k]) continue;
+            const float wx = dx[k] - s.x, wy = dy[k] - s.y;
+            const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
+            const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
+            const float d2 = fmaf(qx, qx, qy * qy);
+            if (d2 < best[k]) {
+              best[k] = d2;
+              bj[k] = j;
             }
+            if (closed) {
+              const bool a_le = wy >= 0.0f, b_le = dy[k] - s2.x >= 0.0f;
+              const float cr = s.z * wy - s.w * wx;
+              if (a_le && !b_le && cr > 0.0f) wn[k] += 1;
+              if (!a_le && b_le && cr < 0.0f) wn[k] -= 1;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)  // a minimum set in this chunk: its segment index
+          if (bj[k] >= 0) {
+            idx[k] = s_idx[bj[k]];
+            bj[k] = -1;
+          }
+      }
+      if (total_near <= base + kNearCap) break;
+    }
+    float2* sv = d.saved + (size_t)slot * NP;
+    bool live = false;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      float sd = -kFar;
+      if (act[k]) {
+        const int w = closed ? wn[k] + s_back[(threadIdx.x + k * NT) / T] : 0;
+        if (best[k] < mrg2) {
+          const float dist = sqrtf(best[k]);
+          sd = closed ? (w != 0 ? dist : -dist) : hwpx - dist;
+        } else {
+          sd = (closed && w != 0) ? kFar : -kFar;
+        }
+        live |= fabsf(sd * inv_rho) < 1.0f || fabsf((sd + pad) * inv_rho) < 1.0f;
+      }
+      sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(idx[k]));
+    }
+    live = __syncthreads_or(live);
+    if (threadIdx.x == 0) d.pair_live[slot] = live ? 1 : 0;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Composite per tile: order the tile's pairs by element id (ids are unique in a tile, so an id's
+// rank is the number of smaller ids), then per pixel Ihat = prod(1 - c_i) and prod(1 - tau c_i^pad)
+// over the pairs in that order, and the per-pixel loss terms (Eq. 5, Eq. 6 surrogate, force).
+// ------------------------------------------------------------------------------------------------
+template <int T, int NT>
+__global__ void __launch_bounds__(NT) k_composite(Dev d, float* out_bw, float* out_tau) {
+  constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
+  constexpr int PER = (kListCap + NT - 1) / NT;
+  __shared__ int s_list[kListCap];
+  __shared__ int s_slot[kListCap];
+  __shared__ float s_red[NW];
+  if (*d.status & kStatusOverflow) return;
+  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
+    int p, tx, ty, res;
+    tile_coords(d, tile, T, p, tx, ty, res);
+    const long long pixbase = d.prob_pix_base[p];
+    const uint2 rg = d.range[tile];
+    const int m = (int)(rg.y - rg.x);
+    const bool small = m <= kListCap;
+    __syncthreads();  // the previous tile's readers of the lists are done
+    if (m > 0) {
+      if (small) {
+        int v[PER], r[PER];
+        for (int i = threadIdx.x; i < m; i += NT) s_list[i] = d.pair_elem[rg.x + i];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+          const int i = threadIdx.x + k * NT;
+          r[k] = 0;
+          v[k] = 0;
+          if (i < m) {
+            v[k] = s_list[i];
+            for (int j = 0; j < m; ++j) r[k] += s_list[j] < v[k] ? 1 : 0;
           }
         }
         __syncthreads();
-        const int total_near = s_near;
-        const int cn = min(kNearCap, total_near - base);
-        if (any && cn > 0) {
-          for (int j = 0; j < cn; ++j) {
-            const float4 s = s_seg[j];
-            const float2 s2 = s_seg2[j];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-              if (!act[k]) continue;
-              const float wx = dx[k] - s.x, wy = dy[k] - s.y;
-              const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
-              const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
-              const float d2 = fmaf(qx, qx, qy * qy);
-              if (d2 < best[k]) {
-                best[k] = d2;
-                bj[k] = j;
-              }
-              if (closed) {
-                const bool a_le = wy >= 0.0f, b_le = dy[k] - s2.x >= 0.0f;
-                const float cr = s.z * wy - s.w * wx;
-                if (a_le && !b_le && cr > 0.0f) wn[k] += 1;
-                if (!a_le && b_le && cr < 0.0f) wn[k] -= 1;
-              }
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < PPT; ++k)  // a minimum set in this chunk: its segment index
-            if (act[k] && best[k] != FLT_MAX && bj[k] >= 0) {
-              idx[k] = s_idx[bj[k]];
-              bj[k] = -1;
-            }
-        }
-        if (total_near <= base + kNearCap) break;
-      }
-      float2* sv = d.saved + (size_t)pr * NP;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        float sd = -kFar;
-        if (act[k]) {
-          const int w = closed ? wn[k] + s_back[(threadIdx.x + k * NT) / T] : 0;
-          if (best[k] < mrg2) {
-            const float dist = sqrtf(best[k]);
-            sd = closed ? (w != 0 ? dist : -dist) : hwpx - dist;
-          } else {
-            sd = (closed && w != 0) ? kFar : -kFar;
+        for (int k = 0; k < PER; ++k) {
+          const int i = threadIdx.x + k * NT;
+          if (i < m) {
+            s_list[r[k]] = v[k];
+            s_slot[r[k]] = (int)rg.x + i;
+            d.pair_sorted[rg.x + r[k]] = v[k];
+            d.pair_slot[rg.x + r[k]] = (int)rg.x + i;
           }
         }
-        const float x = sd * inv_rho;
-        const float omc = Sfun(-x), cp = Sfun((sd + pad) * inv_rho);
-        if (omc == 0.0f) zc[k] += 1;
-        else keep[k] *= omc;
-        keept[k] *= 1.0f - tau * cp;
-        sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(idx[k]));
+      } else {
+        for (int i = threadIdx.x; i < m; i += NT) {
+          const int vi = d.pair_elem[rg.x + i];
+          int r = 0;
+          for (int j = 0; j < m; ++j) r += d.pair_elem[rg.x + j] < vi ? 1 : 0;
+          d.pair_sorted[rg.x + r] = vi;
+          d.pair_slot[rg.x + r] = (int)rg.x + i;
+        }
       }
+      __syncthreads();
     }
-    // per-pixel loss terms (Eq. 5, Eq. 6 surrogate, downward force)
     float lc = 0.0f, lo = 0.0f, ld = 0.0f;
-    const float inv_res = 1.0f / (float)res;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      if (!in[k]) continue;
-      const long long pix = pixbase + (long long)(py[k] - 0.5f) * res + (long long)(px[k] - 0.5f);
-      const float ihat = zc[k] ? 0.0f : keep[k];
+      const int local = threadIdx.x + k * NT;
+      const int X = tx * T + local % T, Y = ty * T + local / T;
+      if (X >= res || Y >= res) continue;
+      float keep = 1.0f, keept = 1.0f;
+      int zc = 0;
+      for (int i = 0; i < m; ++i) {
+        const int slot = small ? s_slot[i] : d.pair_slot[rg.x + i];
+        const float sd = d.saved[(size_t)slot * NP + local].x;
+        const float x = sd * inv_rho;
+        const float omc = Sfun(-x), cp = Sfun((sd + pad) * inv_rho);
+        if (omc == 0.0f) zc += 1;
+        else keep *= omc;
+        keept *= 1.0f - tau * cp;
+      }
+      const long long pix = pixbase + (long long)Y * res + X;
+      const float ihat = zc ? 0.0f : keep;
       const float cov = d.covc[pix];
-      const float ic = 1.0f - cov;
       const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
-      const float df = ihat - ic;
+      const float df = ihat - (1.0f - cov);
       lc += W * df * df;
-      const float A = 1.0f - keept[k];
+      const float A = 1.0f - keept;
       lo += A > tau ? A - tau : 0.0f;
-      ld += (1.0f - ihat) * (1.0f - py[k] * inv_res);
+      ld += (1.0f - ihat) * (1.0f - ((float)Y + 0.5f) / (float)res);
       d.img_I[pix] = ihat;
-      d.img_Pt[pix] = keept[k];
+      d.img_Pt[pix] = keept;
       if (out_bw) out_bw[pix] = ihat;
       if (out_tau) out_tau[pix] = A;
     }
@@ -339,9 +351,9 @@ __global__ void __launch_bounds__(NT) k_raster_fwd(Dev d, float* out_bw, float* 
 }
 
 // ------------------------------------------------------------------------------------------------
-// Adjoint: dL/dIhat and dL/dA_tau per pixel, then per (tile, element) the chain
+// Adjoint, one (tile, element) pair per block: dL/dIhat and dL/dA_tau per pixel, then the chain
 // dL/dc -> dc/dsd -> dsd/d(closest segment) -> d/d(tx, ty, theta, s) of Eq. 2, reduced over the
-// tile's pixels in a fixed order and added to the element's gradient.
+// tile's pixels in a fixed order and added to the element's gradient (or stored per pair).
 // ------------------------------------------------------------------------------------------------
 template <int T, int NT>
 __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
@@ -350,123 +362,111 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
-    const uint2 rg = d.range[tile];
-    if (rg.x == rg.y) continue;
-    const int p = find_prob(d.prob_tile_base, d.n_probs, tile);
-    const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
-    const int tx = lt % ntx, ty = lt / ntx;
+  const int total = *d.total_pairs;
+  for (int slot = blockIdx.x; slot < total; slot += gridDim.x) {
+    if (!d.pair_live[slot]) {
+      if (d.deterministic && threadIdx.x == 0) d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
+    int p, tx, ty, res;
+    tile_coords(d, tile, T, p, tx, ty, res);
     const long long pixbase = d.prob_pix_base[p];
     const float inv_np = 1.0f / ((float)res * (float)res);
-    float px[PPT], py[PPT], ihat[PPT], pt[PPT], gI[PPT], gA[PPT];
-    bool in[PPT];
+    const int v0 = d.elem_voff[g];
+    const bool closed = d.elem_closed[g] != 0;
+    const float4 tp = d.tpx[g];
+    const float s_inv = 1.0f / d.q[g].w;
+    const float2* sv = d.saved + (size_t)slot * NP;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int local = threadIdx.x + k * NT;
       const int X = tx * T + local % T, Y = ty * T + local / T;
-      in[k] = X < res && Y < res;
-      px[k] = (float)X + 0.5f;
-      py[k] = (float)Y + 0.5f;
-      ihat[k] = pt[k] = gI[k] = gA[k] = 0.0f;
-      if (in[k]) {
-        const long long pix = pixbase + (long long)Y * res + X;
-        ihat[k] = d.img_I[pix];
-        pt[k] = d.img_Pt[pix];
-        const float cov = d.covc[pix];
-        const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
-        const float gou = d.L.gamma != 0.0f ? d.gOu[pix] : 0.0f;
-        // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
-        gI[k] = d.L.alpha * inv_np * 2.0f * W * (ihat[k] - (1.0f - cov)) - d.L.gamma * gou -
-                d.L.delta * inv_np * (1.0f - py[k] / (float)res);
-        gA[k] = (1.0f - pt[k]) > tau ? d.L.beta * inv_np : 0.0f;
+      if (X >= res || Y >= res) continue;
+      const float2 rec = sv[local];
+      const float sd = rec.x;
+      const float x = sd * inv_rho, xp = (sd + pad) * inv_rho;
+      if (!(fabsf(x) < 1.0f || fabsf(xp) < 1.0f)) continue;
+      const long long pix = pixbase + (long long)Y * res + X;
+      const float ihat = d.img_I[pix], pt = d.img_Pt[pix], cov = d.covc[pix];
+      const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
+      const float gou = d.L.gamma != 0.0f ? d.gOu[pix] : 0.0f;
+      const float py = (float)Y + 0.5f;
+      // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
+      const float gI = d.L.alpha * inv_np * 2.0f * W * (ihat - (1.0f - cov)) - d.L.gamma * gou -
+                       d.L.delta * inv_np * (1.0f - py / (float)res);
+      const float gA = (1.0f - pt) > tau ? d.L.beta * inv_np : 0.0f;
+      const float omc = Sfun(-x), cp = Sfun(xp);
+      // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)
+      const float gc = omc > 0.0f ? -gI * ihat / omc : 0.0f;
+      // dA/dc^pad_i = tau prod_{j != i}(1 - tau c^pad_j)
+      const float gcp = gA * tau * pt / (1.0f - tau * cp);
+      const float gsd = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
+      if (gsd == 0.0f) continue;
+      const int j = __float_as_int(rec.y);
+      const float4 sa = d.segA[v0 + j];
+      const float dx = ((float)X + 0.5f - tp.x) - tp.z, dy = (py - tp.y) - tp.w;
+      const float ex = sa.z, ey = sa.w, ee = ex * ex + ey * ey;
+      const float wx = dx - sa.x, wy = dy - sa.y;
+      const float u = ee > 0.0f ? __saturatef((wx * ex + wy * ey) / ee) : 0.0f;
+      const float qx = fmaf(u, ex, sa.x), qy = fmaf(u, ey, sa.y);  // closest point, rel. to t
+      // unit normal from the closest point towards the pixel: for a closest point inside the
+      // segment it is the segment's perpendicular on the pixel's side (well conditioned even
+      // when the pixel is almost on the outline); at an end point it is the direction to the pixel
+      float nx, ny;
+      if (u > 0.0f && u < 1.0f) {
+        const float inv_len = rsqrtf(ee);
+        const float side = ex * wy - ey * wx >= 0.0f ? inv_len : -inv_len;
+        nx = -ey * side;
+        ny = ex * side;
+      } else {
+        const float rx = dx - qx, ry = dy - qy;
+        const float dist = sqrtf(rx * rx + ry * ry);
+        if (!(dist > 0.0f)) continue;
+        nx = rx / dist;
+        ny = ry / dist;
       }
+      // sd = sig * dist (closed: sig = +-1 by the winding; open: sd = hw - dist, sig = -1)
+      const float sig = closed ? (sd > 0.0f ? 1.0f : -1.0f) : -1.0f;
+      const float gs = -sig * gsd;
+      a0 += gs * nx * (float)res;              // d(dist)/dt = -n, t in unit coords
+      a1 += gs * ny * (float)res;
+      a2 += gs * (ny * qx - nx * qy);          // d(dist)/dtheta = -n . J q
+      a3 += gs * (nx * qx + ny * qy) * s_inv;  // d(dist)/ds = -n . q / s
     }
-    for (uint32_t pr = rg.x; pr < rg.y; ++pr) {
-      const int g = d.pair_sorted[pr];
-      const int v0 = d.elem_voff[g];
-      const bool closed = d.elem_closed[g] != 0;
-      const float4 tp = d.tpx[g];
-      const float s_inv = 1.0f / d.q[g].w;
-      const float2* sv = d.saved + (size_t)pr * NP;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    // fixed-order block reduction of the four sums
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const float2 rec = sv[threadIdx.x + k * NT];
-        const float sd = rec.x;
-        const float x = sd * inv_rho, xp = (sd + pad) * inv_rho;
-        if (!in[k] || !(fabsf(x) < 1.0f || fabsf(xp) < 1.0f)) continue;
-        const float omc = Sfun(-x), cp = Sfun(xp);
-        // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)
-        const float gc = omc > 0.0f ? -gI[k] * ihat[k] / omc : 0.0f;
-        // dA/dc^pad_i = tau prod_{j != i}(1 - tau c^pad_j)
-        const float gcp = gA[k] * tau * pt[k] / (1.0f - tau * cp);
-        const float gsd = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
-        if (gsd == 0.0f) continue;
-        const int j = __float_as_int(rec.y);
-        const float4 sa = d.segA[v0 + j];
-        const float2 a = make_float2(sa.x, sa.y);
-        const float dx = (px[k] - tp.x) - tp.z, dy = (py[k] - tp.y) - tp.w;
-        const float ex = sa.z, ey = sa.w, ee = ex * ex + ey * ey;
-        const float wx = dx - a.x, wy = dy - a.y;
-        const float u = ee > 0.0f ? __saturatef((wx * ex + wy * ey) / ee) : 0.0f;
-        const float qx = fmaf(u, ex, a.x), qy = fmaf(u, ey, a.y);  // closest point, rel. to t
-        // unit normal from the closest point towards the pixel: for a closest point inside the
-        // segment it is the segment's perpendicular on the pixel's side (well conditioned even
-        // when the pixel is almost on the outline); at an end point it is the direction to the pixel
-        float nx, ny;
-        if (u > 0.0f && u < 1.0f) {
-          const float inv_len = rsqrtf(ee);
-          const float side = ex * wy - ey * wx >= 0.0f ? inv_len : -inv_len;
-          nx = -ey * side;
-          ny = ex * side;
-        } else {
-          const float rx = dx - qx, ry = dy - qy;
-          const float dist = sqrtf(rx * rx + ry * ry);
-          if (!(dist > 0.0f)) continue;
-          nx = rx / dist;
-          ny = ry / dist;
-        }
-        // sd = sig * dist (closed: sig = +-1 by the winding; open: sd = hw - dist, sig = -1)
-        const float sig = closed ? (sd > 0.0f ? 1.0f : -1.0f) : -1.0f;
-        const float gs = -sig * gsd;
-        a0 += gs * nx * (float)res;                 // d(dist)/dt = -n, t in unit coords
-        a1 += gs * ny * (float)res;
-        a2 += gs * (ny * qx - nx * qy);             // d(dist)/dtheta = -n . J q
-        a3 += gs * (nx * qx + ny * qy) * s_inv;     // d(dist)/ds = -n . q / s
+    for (int o = 16; o; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+    }
+    __syncthreads();  // the previous pair's reader of s_red is done
+    if (lane == 0) {
+      s_red[0][wid] = a0;
+      s_red[1][wid] = a1;
+      s_red[2][wid] = a2;
+      s_red[3][wid] = a3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < NT / 32; ++i) {
+        r.x += s_red[0][i];
+        r.y += s_red[1][i];
+        r.z += s_red[2][i];
+        r.w += s_red[3][i];
       }
-      // fixed-order block reduction of the four sums
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+      if (d.deterministic) {
+        d.partial[slot] = r;
+      } else {
+        atomicAdd(&d.dq[g].x, r.x);
+        atomicAdd(&d.dq[g].y, r.y);
+        atomicAdd(&d.dq[g].z, r.z);
+        atomicAdd(&d.dq[g].w, r.w);
       }
-      if (lane == 0) {
-        s_red[0][wid] = a0;
-        s_red[1][wid] = a1;
-        s_red[2][wid] = a2;
-        s_red[3][wid] = a3;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int i = 0; i < NT / 32; ++i) {
-          r.x += s_red[0][i];
-          r.y += s_red[1][i];
-          r.z += s_red[2][i];
-          r.w += s_red[3][i];
-        }
-        if (d.deterministic) {
-          d.partial[pr] = r;
-        } else {
-          atomicAdd(&d.dq[g].x, r.x);
-          atomicAdd(&d.dq[g].y, r.y);
-          atomicAdd(&d.dq[g].z, r.z);
-          atomicAdd(&d.dq[g].w, r.w);
-        }
-      }
-      __syncthreads();
     }
   }
 }
@@ -543,7 +543,7 @@ struct TileCfg<8> {
 };
 template <>
 struct TileCfg<16> {
-  static constexpr int NT = 128;
+  static constexpr int NT = 256;
 };
 template <>
 struct TileCfg<32> {
@@ -551,77 +551,61 @@ struct TileCfg<32> {
 };
 
 template <int T>
-static int default_grid(const Dev& d, int grid) {
-  return grid > 0 ? grid : d.total_tiles;
-}
-
-cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int grid, float* out_bw, float* out_tau) {
-  switch (d.tile) {
-    case 8:
-      k_raster_fwd<8, TileCfg<8>::NT><<<default_grid<8>(d, grid), TileCfg<8>::NT, 0, s>>>(d, out_bw, out_tau);
-      break;
-    case 16:
-      k_raster_fwd<16, TileCfg<16>::NT><<<default_grid<16>(d, grid), TileCfg<16>::NT, 0, s>>>(d, out_bw, out_tau);
-      break;
-    case 32:
-      k_raster_fwd<32, TileCfg<32>::NT><<<default_grid<32>(d, grid), TileCfg<32>::NT, 0, s>>>(d, out_bw, out_tau);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+static cudaError_t fwd_t(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid, float* bw,
+                         float* tau) {
+  constexpr int NT = TileCfg<T>::NT;
+  k_pair_sd<T, NT><<<pair_grid, NT, 0, s>>>(d);
+  k_composite<T, NT><<<tile_grid, NT, 0, s>>>(d, bw, tau);
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int grid) {
+cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid,
+                              float* out_bw, float* out_tau) {
   switch (d.tile) {
-    case 8:
-      k_raster_bwd<8, TileCfg<8>::NT><<<default_grid<8>(d, grid), TileCfg<8>::NT, 0, s>>>(d);
-      break;
-    case 16:
-      k_raster_bwd<16, TileCfg<16>::NT><<<default_grid<16>(d, grid), TileCfg<16>::NT, 0, s>>>(d);
-      break;
-    case 32:
-      k_raster_bwd<32, TileCfg<32>::NT><<<default_grid<32>(d, grid), TileCfg<32>::NT, 0, s>>>(d);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case 8: return fwd_t<8>(d, s, pair_grid, tile_grid, out_bw, out_tau);
+    case 16: return fwd_t<16>(d, s, pair_grid, tile_grid, out_bw, out_tau);
+    case 32: return fwd_t<32>(d, s, pair_grid, tile_grid, out_bw, out_tau);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid) {
+  switch (d.tile) {
+    case 8: k_raster_bwd<8, TileCfg<8>::NT><<<pair_grid, TileCfg<8>::NT, 0, s>>>(d); break;
+    case 16: k_raster_bwd<16, TileCfg<16>::NT><<<pair_grid, TileCfg<16>::NT, 0, s>>>(d); break;
+    case 32: k_raster_bwd<32, TileCfg<32>::NT><<<pair_grid, TileCfg<32>::NT, 0, s>>>(d); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_container(const Dev& d, cudaStream_t s) {
   switch (d.tile) {
-    case 8:
-      k_container<8, TileCfg<8>::NT><<<d.total_tiles, TileCfg<8>::NT, 0, s>>>(d);
-      break;
-    case 16:
-      k_container<16, TileCfg<16>::NT><<<d.total_tiles, TileCfg<16>::NT, 0, s>>>(d);
-      break;
-    case 32:
-      k_container<32, TileCfg<32>::NT><<<d.total_tiles, TileCfg<32>::NT, 0, s>>>(d);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case 8: k_container<8, TileCfg<8>::NT><<<d.total_tiles, TileCfg<8>::NT, 0, s>>>(d); break;
+    case 16: k_container<16, TileCfg<16>::NT><<<d.total_tiles, TileCfg<16>::NT, 0, s>>>(d); break;
+    case 32: k_container<32, TileCfg<32>::NT><<<d.total_tiles, TileCfg<32>::NT, 0, s>>>(d); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-int raster_fwd_max_grid(int tile) {
-  int dev = 0, sms = 0, per = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+template <int T>
+static void per_sm_t(int* pair_per_sm, int* tile_per_sm) {
+  constexpr int NT = TileCfg<T>::NT;
+  int a = 1, b = 1, c = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pair_sd<T, NT>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T, NT>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_composite<T, NT>, NT, 0);
+  *pair_per_sm = a < b ? (a > 0 ? a : 1) : (b > 0 ? b : 1);
+  *tile_per_sm = c > 0 ? c : 1;
+}
+
+void raster_blocks_per_sm(int tile, int* pair_per_sm, int* tile_per_sm) {
   switch (tile) {
-    case 8:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_raster_fwd<8, 64>, 64, 0);
-      break;
-    case 16:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_raster_fwd<16, 128>, 128, 0);
-      break;
-    default:
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_raster_fwd<32, 256>, 256, 0);
-      break;
+    case 8: per_sm_t<8>(pair_per_sm, tile_per_sm); break;
+    case 16: per_sm_t<16>(pair_per_sm, tile_per_sm); break;
+    default: per_sm_t<32>(pair_per_sm, tile_per_sm); break;
   }
-  return sms * (per > 0 ? per : 1);
 }
 
 }  // namespace collage
