@@ -162,15 +162,16 @@ collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_e
 
 /* Device time per stage, averaged over n_iters eager iterations, into h_ms[COLLAGE_N_STAGES]
  * (see COLLAGE_STAGE_*); the kernels run on `stream`, timed with events on that stream. */
-#define COLLAGE_N_STAGES 8
-#define COLLAGE_STAGE_TRANSFORM 0 /* transform, bbox, tile counts */
-#define COLLAGE_STAGE_BIN 1       /* scan, emit, key sort, tile ranges */
-#define COLLAGE_STAGE_RASTER_FWD 2
-#define COLLAGE_STAGE_DILATE 3    /* distribution term forward and backward */
-#define COLLAGE_STAGE_RASTER_BWD 4
-#define COLLAGE_STAGE_REDUCE 5    /* deterministic gradient reduction */
-#define COLLAGE_STAGE_LOSS 6      /* loss assembly */
-#define COLLAGE_STAGE_ADAM 7
+#define COLLAGE_N_STAGES 9
+#define COLLAGE_STAGE_TRANSFORM 0 /* transform, segment records, tile counts */
+#define COLLAGE_STAGE_BIN 1       /* tile-count scan and pair emission */
+#define COLLAGE_STAGE_RASTER_FWD 2 /* signed distances per (tile, element) pair */
+#define COLLAGE_STAGE_COMPOSITE 3 /* per-tile products and loss partials */
+#define COLLAGE_STAGE_DILATE 4    /* distribution term forward and backward */
+#define COLLAGE_STAGE_RASTER_BWD 5
+#define COLLAGE_STAGE_REDUCE 6    /* deterministic gradient reduction */
+#define COLLAGE_STAGE_LOSS 7      /* loss assembly */
+#define COLLAGE_STAGE_ADAM 8
 collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float* h_ms);
 
 /* Times each raster tile size on the current level and keeps the fastest (the autotuner);

@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcollage.so")
 
 COLLAGE_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "OVERFLOW", -5: "TIMEOUT", -6: "STATE"}
-N_STAGES = 8
-STAGES = ["transform", "bin", "raster_fwd", "dilate", "raster_bwd", "reduce", "loss", "adam"]
+N_STAGES = 9
+STAGES = ["transform", "bin", "raster_fwd", "composite", "dilate", "raster_bwd", "reduce", "loss",
+          "adam"]
 
 _ip = C.POINTER(C.c_int)
 _fp = C.POINTER(C.c_float)

@@ -339,6 +339,7 @@ static collage_status setup_level(collage_t h, int level) {
     CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
     CK(h, dmalloc(h->level_bufs, d.lossA, nt));
     CK(h, dmalloc(h->level_bufs, d.lossU, nd));
+    CK(h, dmalloc(h->level_bufs, d.dtile_flags, nd));
     h->pix_cap = np;
     h->tile_cap = nt;
     h->dtile_cap = nd;
@@ -352,6 +353,7 @@ static collage_status setup_level(collage_t h, int level) {
   cudaStream_t s = h->cap_stream;
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));  // clear latched status
   CK(h, launch_container(d, s));
+  CK(h, launch_dtile_flags(d, s));
   // size the pair buffers from the current params: count with an unbounded capacity
   CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
   Dev probe = d;
@@ -391,21 +393,23 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   STEP_(launch_scan(d, s));
   STEP_(launch_bin(d, s));
   MARK_(2);
-  STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau));
+  STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 1));
   MARK_(3);
+  STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 2));
+  MARK_(4);
   if (dil) {
     STEP_(launch_dilate(d, s, false));
     STEP_(launch_dilate(d, s, true));
   }
-  MARK_(4);
-  if (bwd) STEP_(launch_raster_bwd(d, s, h->pair_grid));
   MARK_(5);
-  if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
+  if (bwd) STEP_(launch_raster_bwd(d, s, h->pair_grid));
   MARK_(6);
-  if (bwd) STEP_(launch_loss(d, s, mode == kStep));
+  if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
   MARK_(7);
-  if (mode == kStep) STEP_(launch_adam(d, s));
+  if (bwd) STEP_(launch_loss(d, s, mode == kStep));
   MARK_(8);
+  if (mode == kStep) STEP_(launch_adam(d, s));
+  MARK_(9);
 #undef STEP_
 #undef MARK_
   return cudaSuccess;
@@ -817,7 +821,7 @@ extern "C" collage_status collage_get_bins(collage_t h, void* stream, int* d_til
 extern "C" collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float* h_ms) {
   if (!h || !h_ms || n_iters < 1) return fail(h, COLLAGE_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
-  constexpr int NE = 9;
+  constexpr int NE = COLLAGE_N_STAGES + 1;
   cudaEvent_t ev[NE];
   for (int i = 0; i < NE; ++i) CK(h, cudaEventCreate(&ev[i]));
   double acc[NE - 1] = {0};
@@ -841,7 +845,7 @@ extern "C" collage_status collage_stage_times(collage_t h, void* stream, int n_i
   }
   for (int i = 0; i < NE; ++i) cudaEventDestroy(ev[i]);
   if (st) return st;
-  // events: 0 transform 1 bin 2 raster_fwd 3 dilate 4 raster_bwd 5 reduce 6 loss 7 adam 8
+  // events bracket the stages in COLLAGE_STAGE_* order
   for (int i = 0; i < COLLAGE_N_STAGES; ++i) h_ms[i] = (float)(acc[i] / n_iters);
   bool over = false;
   return check_and_grow(h, s, &over);

@@ -83,6 +83,7 @@ struct Dev {
   uint8_t* dil_mask;            // [pix] bit k: B_k < 1
   float4* lossA;                // [total_tiles] (sum W(I-Ic)^2, sum relu(A-tau), sum O(1-y), 0)
   float* lossU;                 // [total_dtiles] weighted uniform-loss partial
+  uint8_t* dtile_flags;         // [total_dtiles] container coverage on the tile / its halo (or null)
   float4* dq;                   // [n] gradient
   float4* partial;              // [cap] deterministic gradient partials, at emit position
   float* loss_terms;            // [P*5]
@@ -97,11 +98,12 @@ cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
 cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
 cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit pairs into tile ranges
 cudaError_t launch_container(const Dev& d, cudaStream_t s);
-// per-pair signed distances, then the per-tile composite and loss partials
+// part 1: per-pair signed distances; part 2: per-tile composite and loss partials; 3: both
 cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid,
-                              float* out_bw, float* out_tau);
+                              float* out_bw, float* out_tau, int part = 3);
 cudaError_t prepare_dilate(int n_dil);  // sets dynamic shared memory limits (not capturable)
 cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward);
+cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s);  // once per level, after the container
 cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid);
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step);

@@ -12,7 +12,7 @@
 namespace collage {
 
 constexpr int kDT = 32;       // dilation tile side
-constexpr int kDThreads = 256;
+constexpr int kDThreads = 512;
 constexpr int kDPPT = kDT * kDT / kDThreads;
 
 __device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
@@ -29,45 +29,56 @@ __host__ __device__ __forceinline__ int dil_radius(int k) { return 2 + 3 * k; } 
 
 // Box sums by running windows: a thread owns kSeg consecutive outputs of one row (or column) of
 // one kernel, forms the first window directly and slides it (one add, one subtract per output).
-// Restarting every kSeg outputs keeps the float rounding at the level of a direct sum.
+// Restarting every kSeg outputs keeps the float rounding at the level of a direct sum.  The
+// kernels are instantiated per number of dilations K so that every window loop unrolls.
 constexpr int kSeg = 8;
 constexpr int kNSeg = kDT / kSeg;
+constexpr int kFlagOwn = 1;   // container coverage is nonzero somewhere on the tile
+constexpr int kFlagHalo = 2;  // ... or somewhere within the halo of the largest kernel
+
+template <int K>
+struct DilGeom {
+  static constexpr int h = 2 + 3 * (K - 1);  // radius of the widest kernel
+  static constexpr int S = kDT + 2 * h;      // staged side
+};
 
 // H[k][rr][c] = sum_{|dc| <= r_k} src(k, rr, c + h + dc) for the rows the vertical pass reads.
-template <class Src>
-__device__ __forceinline__ void hsums(const Src& src, float* H, int S, int h, int K) {
-  const int items = K * S * kNSeg;
+template <int K, int k, class Src>
+__device__ __forceinline__ void hsums_k(const Src& src, float* H) {
+  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h, r = 2 + 3 * k;
+  constexpr int rows = kDT + 2 * r, items = rows * kNSeg;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int seg = it % kNSeg, rr = (it / kNSeg) % S, k = it / (kNSeg * S);
-    const int r = dil_radius(k);
-    if (rr < h - r || rr >= h + kDT + r) continue;
+    const int seg = it % kNSeg, rr = h - r + it / kNSeg;
     const int c0 = seg * kSeg;
     float sacc = 0.0f;
+#pragma unroll
     for (int dc = -r; dc <= r; ++dc) sacc += src(k, rr, c0 + h + dc);
-    float* out = H + (k * S + rr) * kDT;
-    out[c0] = sacc;
-    for (int c = c0 + 1; c < c0 + kSeg; ++c) {
-      sacc += src(k, rr, c + h + r) - src(k, rr, c + h - r - 1);
+    float* out = H + (k * S + rr) * kDT + c0;
+    out[0] = sacc;
+#pragma unroll
+    for (int c = 1; c < kSeg; ++c) {
+      sacc += src(k, rr, c0 + c + h + r) - src(k, rr, c0 + c + h - r - 1);
       out[c] = sacc;
     }
   }
 }
 
 // Bk[k][rr][c] = sum_{|dr| <= r_k} H[k][rr + h + dr][c]: the box sum at output pixel (rr, c).
-__device__ __forceinline__ void vsums(const float* H, float* Bk, int S, int h, int K) {
-  const int items = K * kDT * kNSeg;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it % kDT, seg = (it / kDT) % kNSeg, k = it / (kDT * kNSeg);
-    const int r = dil_radius(k);
+template <int K, int k>
+__device__ __forceinline__ void vsums_k(const float* H, float* Bk) {
+  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h, r = 2 + 3 * k;
+  for (int it = threadIdx.x; it < kDT * kNSeg; it += blockDim.x) {
+    const int c = it % kDT, r0 = (it / kDT) * kSeg;
     const float* col = H + k * S * kDT + c;
-    const int r0 = seg * kSeg;
     float sacc = 0.0f;
+#pragma unroll
     for (int dr = -r; dr <= r; ++dr) sacc += col[(r0 + h + dr) * kDT];
     float* out = Bk + k * kDT * kDT + c;
     out[r0 * kDT] = sacc;
-    for (int rr = r0 + 1; rr < r0 + kSeg; ++rr) {
-      sacc += col[(rr + h + r) * kDT] - col[(rr + h - r - 1) * kDT];
-      out[rr * kDT] = sacc;
+#pragma unroll
+    for (int i = 1; i < kSeg; ++i) {
+      sacc += col[(r0 + i + h + r) * kDT] - col[(r0 + i + h - r - 1) * kDT];
+      out[(r0 + i) * kDT] = sacc;
     }
   }
 }
@@ -88,11 +99,33 @@ struct GSrc {  // G_k = M_C (1 - O) where B_k < 1, else 0
   }
 };
 
+template <int K, int k = 0>
+__device__ __forceinline__ void hsums_all(const OccSrc& o, const GSrc& g, bool occ, float* H) {
+  if constexpr (k < K) {
+    if (occ) hsums_k<K, k>(o, H);
+    else hsums_k<K, k>(g, H);
+    hsums_all<K, k + 1>(o, g, occ, H);
+  }
+}
+
+template <int K, int k = 0>
+__device__ __forceinline__ void vsums_all(const float* H, float* Bk) {
+  if constexpr (k < K) {
+    vsums_k<K, k>(H, Bk);
+    vsums_all<K, k + 1>(H, Bk);
+  }
+}
+
+__device__ __forceinline__ int dil_flags(const Dev& d, int dt) {
+  return d.dtile_flags ? (int)d.dtile_flags[dt] : (kFlagOwn | kFlagHalo);
+}
+
+template <int K>
 __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
+  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h;
   extern __shared__ float sm[];
   __shared__ float s_red[kDThreads / 32];
   if (*d.status & kStatusOverflow) return;
-  const int K = d.L.n_dil, h = dil_radius(K - 1), S = kDT + 2 * h;
   float* sO = sm;
   float* H = sO + S * S;
   float* Bk = H + K * S * kDT;
@@ -101,15 +134,28 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
+    if (!(dil_flags(d, dt) & kFlagOwn)) {
+      // no container coverage on this tile: M_C (1 - O) = 0, dL_u/dO = 0, no loss
+      for (int local = threadIdx.x; local < kDT * kDT; local += kDThreads) {
+        const int X = x0 + local % kDT, Y = y0 + local / kDT;
+        if (X >= res || Y >= res) continue;
+        const long long pix = pb + (long long)Y * res + X;
+        d.dil_m[pix] = 0.0f;
+        d.dil_mask[pix] = 0;
+        d.gOu[pix] = 0.0f;
+      }
+      if (threadIdx.x == 0) d.lossU[dt] = 0.0f;
+      continue;
+    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
       sO[idx] = (X >= 0 && Y >= 0 && X < res && Y < res) ? 1.0f - d.img_I[pb + (long long)Y * res + X] : 0.0f;
     }
     __syncthreads();
-    hsums(OccSrc{sO, S}, H, S, h, K);
+    hsums_all<K>(OccSrc{sO, S}, GSrc{nullptr, nullptr, S}, true, H);
     __syncthreads();
-    vsums(H, Bk, S, h, K);
+    vsums_all<K>(H, Bk);
     __syncthreads();
     float lu = 0.0f;
 #pragma unroll
@@ -123,6 +169,7 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
       const float mval = M * (1.0f - O);
       float gdir = 0.0f;
       unsigned mask = 0u;
+#pragma unroll
       for (int k = 0; k < K; ++k) {
         const float B = Bk[k * kDT * kDT + local];
         const float D = fminf(1.0f, B);
@@ -147,15 +194,17 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
   }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
+  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h;
   extern __shared__ float sm[];
   if (*d.status & kStatusOverflow) return;
-  const int K = d.L.n_dil, h = dil_radius(K - 1), S = kDT + 2 * h;
   float* sM = sm;
   float* H = sM + S * S;
   float* Bk = H + K * S * kDT;
   uint8_t* sMask = reinterpret_cast<uint8_t*>(Bk + K * kDT * kDT);
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
+    if (!(dil_flags(d, dt) & kFlagHalo)) continue;  // G = 0 over the tile and its halo
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
@@ -169,9 +218,9 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
       sMask[idx] = in ? d.dil_mask[pix] : (uint8_t)0;
     }
     __syncthreads();
-    hsums(GSrc{sM, sMask, S}, H, S, h, K);
+    hsums_all<K>(OccSrc{nullptr, S}, GSrc{sM, sMask, S}, false, H);
     __syncthreads();
-    vsums(H, Bk, S, h, K);
+    vsums_all<K>(H, Bk);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kDPPT; ++i) {
@@ -179,9 +228,40 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
       const int X = x0 + c, Y = y0 + rr;
       if (X >= res || Y >= res) continue;
       float acc = 0.0f;
+#pragma unroll
       for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * Bk[k * kDT * kDT + local];
       d.gOu[pb + (long long)Y * res + X] += acc;
     }
+  }
+}
+
+// Per dilation tile, once per level: whether the container coverage is nonzero on the tile, and
+// whether it is nonzero within the halo of the widest kernel.
+__global__ void k_dtile_flags(Dev d, int h) {
+  __shared__ int s_own, s_halo;
+  for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
+    const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
+    const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
+    const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
+    const long long pb = d.prob_pix_base[p];
+    if (threadIdx.x == 0) s_own = s_halo = 0;
+    __syncthreads();
+    const int S = kDT + 2 * h;
+    int own = 0, halo = 0;
+    for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+      const int rr = idx / S, cc = idx % S;
+      const int Y = y0 + rr - h, X = x0 + cc - h;
+      if (X < 0 || Y < 0 || X >= res || Y >= res) continue;
+      if (d.covc[pb + (long long)Y * res + X] > 0.0f) {
+        halo = 1;
+        if (rr >= h && rr < h + kDT && cc >= h && cc < h + kDT) own = 1;
+      }
+    }
+    if (own) atomicOr(&s_own, 1);
+    if (halo) atomicOr(&s_halo, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) d.dtile_flags[dt] = (uint8_t)((s_own ? kFlagOwn : 0) | (s_halo ? kFlagHalo : 0));
+    __syncthreads();
   }
 }
 
@@ -309,20 +389,60 @@ static size_t dilate_smem(int K, bool backward) {
   return f * sizeof(float);
 }
 
-cudaError_t prepare_dilate(int n_dil) {
-  if (n_dil <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_dilate_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)dilate_smem(n_dil, true));
+template <int K>
+static cudaError_t prepare_k() {
+  cudaError_t e = cudaFuncSetAttribute(k_dilate_bwd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)dilate_smem(K, true));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_dilate_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)dilate_smem(n_dil, false));
+  return cudaFuncSetAttribute(k_dilate_fwd<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dilate_smem(K, false));
+}
+
+cudaError_t prepare_dilate(int n_dil) {
+  switch (n_dil) {
+    case 1: return prepare_k<1>();
+    case 2: return prepare_k<2>();
+    case 3: return prepare_k<3>();
+    case 4: return prepare_k<4>();
+    case 5: return prepare_k<5>();
+    case 6: return prepare_k<6>();
+    case 7: return prepare_k<7>();
+    case 8: {  // the largest: also raise every smaller instantiation (callers may mix sizes)
+      for (int k = 1; k < 8; ++k) {
+        cudaError_t e = prepare_dilate(k);
+        if (e != cudaSuccess) return e;
+      }
+      return prepare_k<8>();
+    }
+    default: return cudaSuccess;
+  }
+}
+
+template <int K>
+static void launch_k(const Dev& d, cudaStream_t s, bool backward) {
+  const size_t sm = dilate_smem(K, backward);
+  if (backward) k_dilate_bwd<K><<<d.total_dtiles, kDThreads, sm, s>>>(d);
+  else k_dilate_fwd<K><<<d.total_dtiles, kDThreads, sm, s>>>(d);
 }
 
 cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward) {
-  if (d.L.n_dil <= 0) return cudaSuccess;
-  const size_t sm = dilate_smem(d.L.n_dil, backward);
-  if (backward) k_dilate_bwd<<<d.total_dtiles, kDThreads, sm, s>>>(d);
-  else k_dilate_fwd<<<d.total_dtiles, kDThreads, sm, s>>>(d);
+  switch (d.L.n_dil) {
+    case 1: launch_k<1>(d, s, backward); break;
+    case 2: launch_k<2>(d, s, backward); break;
+    case 3: launch_k<3>(d, s, backward); break;
+    case 4: launch_k<4>(d, s, backward); break;
+    case 5: launch_k<5>(d, s, backward); break;
+    case 6: launch_k<6>(d, s, backward); break;
+    case 7: launch_k<7>(d, s, backward); break;
+    case 8: launch_k<8>(d, s, backward); break;
+    default: return cudaSuccess;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s) {
+  if (d.L.n_dil <= 0 || !d.dtile_flags) return cudaSuccess;
+  k_dtile_flags<<<d.total_dtiles, 256, 0, s>>>(d, dil_radius(d.L.n_dil - 1));
   return cudaGetLastError();
 }
 

@@ -70,20 +70,8 @@ __device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, floa
   }
 }
 
-template <int NT>
-__device__ __forceinline__ float block_sum(float x, float* red) {
-  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = x;
-  __syncthreads();
-  float s = 0.0f;
-  for (int i = 0; i < NT / 32; ++i) s += red[i];  // fixed order
-  return s;
-}
-
 constexpr int kSegCap = 1024;   // container segments staged per chunk
-constexpr int kNearCap = 512;   // near segments staged per chunk of one (tile, element) pair
+constexpr int kNearCap = 256;   // near segments staged per chunk of one (tile, element) pair
 constexpr int kListCap = 512;   // tile list entries ordered in shared memory
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
 
@@ -109,7 +97,7 @@ __device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& 
 // loop would give) and sd = +-1e30, else the near minimum is the true distance.
 // ------------------------------------------------------------------------------------------------
 template <int T, int NT>
-__global__ void __launch_bounds__(NT) k_pair_sd(Dev d) {
+__global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d) {
   constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
   static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
   __shared__ float4 s_seg[kNearCap];
@@ -264,7 +252,7 @@ __global__ void __launch_bounds__(NT) k_composite(Dev d, float* out_bw, float* o
   constexpr int PER = (kListCap + NT - 1) / NT;
   __shared__ int s_list[kListCap];
   __shared__ int s_slot[kListCap];
-  __shared__ float s_red[NW];
+  __shared__ float s_red[3][NW];
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
@@ -343,10 +331,27 @@ __global__ void __launch_bounds__(NT) k_composite(Dev d, float* out_bw, float* o
       if (out_bw) out_bw[pix] = ihat;
       if (out_tau) out_tau[pix] = A;
     }
-    lc = block_sum<NT>(lc, s_red);
-    lo = block_sum<NT>(lo, s_red);
-    ld = block_sum<NT>(ld, s_red);
-    if (threadIdx.x == 0) d.lossA[tile] = make_float4(lc, lo, ld, 0.0f);
+    // fixed-order block sums of the three partials
+    for (int o = 16; o; o >>= 1) {
+      lc += __shfl_xor_sync(0xffffffffu, lc, o);
+      lo += __shfl_xor_sync(0xffffffffu, lo, o);
+      ld += __shfl_xor_sync(0xffffffffu, ld, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_red[0][threadIdx.x >> 5] = lc;
+      s_red[1][threadIdx.x >> 5] = lo;
+      s_red[2][threadIdx.x >> 5] = ld;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < NW; ++i) {
+        r.x += s_red[0][i];
+        r.y += s_red[1][i];
+        r.z += s_red[2][i];
+      }
+      d.lossA[tile] = r;
+    }
   }
 }
 
@@ -547,24 +552,24 @@ struct TileCfg<16> {
 };
 template <>
 struct TileCfg<32> {
-  static constexpr int NT = 256;
+  static constexpr int NT = 512;
 };
 
 template <int T>
 static cudaError_t fwd_t(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid, float* bw,
-                         float* tau) {
+                         float* tau, int part) {
   constexpr int NT = TileCfg<T>::NT;
-  k_pair_sd<T, NT><<<pair_grid, NT, 0, s>>>(d);
-  k_composite<T, NT><<<tile_grid, NT, 0, s>>>(d, bw, tau);
+  if (part & 1) k_pair_sd<T, NT><<<pair_grid, NT, 0, s>>>(d);
+  if (part & 2) k_composite<T, NT><<<tile_grid, NT, 0, s>>>(d, bw, tau);
   return cudaGetLastError();
 }
 
 cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid,
-                              float* out_bw, float* out_tau) {
+                              float* out_bw, float* out_tau, int part) {
   switch (d.tile) {
-    case 8: return fwd_t<8>(d, s, pair_grid, tile_grid, out_bw, out_tau);
-    case 16: return fwd_t<16>(d, s, pair_grid, tile_grid, out_bw, out_tau);
-    case 32: return fwd_t<32>(d, s, pair_grid, tile_grid, out_bw, out_tau);
+    case 8: return fwd_t<8>(d, s, pair_grid, tile_grid, out_bw, out_tau, part);
+    case 16: return fwd_t<16>(d, s, pair_grid, tile_grid, out_bw, out_tau, part);
+    case 32: return fwd_t<32>(d, s, pair_grid, tile_grid, out_bw, out_tau, part);
     default: return cudaErrorInvalidValue;
   }
 }
