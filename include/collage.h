@@ -129,7 +129,10 @@ collage_status collage_loss_backward(collage_t h, void* stream, float* d_loss_te
 /* n_iters >= 0 iterations of forward + backward + Adam (Eq. 4 with Adam) at the current level,
  * replaying a captured CUDA graph when use_graphs is set.  Synchronises the stream at the end to
  * check the device status; a bin overflow regrows the buffers and resumes, so exactly n_iters
- * successful iterations run. */
+ * successful iterations run.  Each iteration's Adam step is applied at the start of the next
+ * iteration (inside its transform kernel); every call that reads or replaces the params
+ * (get_params, get_state, set_params, step_host) applies a pending step first, so callers always
+ * observe the updated params. */
 collage_status collage_step(collage_t h, void* stream, int n_iters);
 
 /* Runs every level of the schedule from the current one: set_level + level_iters[l] steps. */
@@ -163,7 +166,7 @@ collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_e
 /* Device time per stage, averaged over n_iters eager iterations, into h_ms[COLLAGE_N_STAGES]
  * (see COLLAGE_STAGE_*); the kernels run on `stream`, timed with events on that stream. */
 #define COLLAGE_N_STAGES 9
-#define COLLAGE_STAGE_TRANSFORM 0 /* transform, segment records, tile counts */
+#define COLLAGE_STAGE_TRANSFORM 0 /* previous Adam step, transform, segment records, tile counts */
 #define COLLAGE_STAGE_BIN 1       /* tile-count scan and pair emission */
 #define COLLAGE_STAGE_RASTER_FWD 2 /* signed distances per (tile, element) pair */
 #define COLLAGE_STAGE_COMPOSITE 3 /* per-tile products and loss partials */
@@ -171,7 +174,7 @@ collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_e
 #define COLLAGE_STAGE_RASTER_BWD 5
 #define COLLAGE_STAGE_REDUCE 6    /* deterministic gradient reduction */
 #define COLLAGE_STAGE_LOSS 7      /* loss assembly */
-#define COLLAGE_STAGE_ADAM 8
+#define COLLAGE_STAGE_ADAM 8      /* (empty: the Adam step is applied by the next transform) */
 collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float* h_ms);
 
 /* Times each raster tile size on the current level and keeps the fastest (the autotuner);

@@ -406,9 +406,10 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   MARK_(6);
   if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
   MARK_(7);
+  // in step mode the loss assembly marks this iteration's Adam step pending; the next transform
+  // (or a flush before params are read) applies it
   if (bwd) STEP_(launch_loss(d, s, mode == kStep));
   MARK_(8);
-  if (mode == kStep) STEP_(launch_adam(d, s));
   MARK_(9);
 #undef STEP_
 #undef MARK_
@@ -630,6 +631,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.status = h->ctl;
   d.step = h->ctl + 1;
   d.total_pairs = h->ctl + 2;
+  d.pending = h->ctl + 3;
   CKC(dmalloc(h->owned, h->d_prob_res, h->P));
   CKC(dmalloc(h->owned, h->d_prob_ntx, h->P));
   CKC(dmalloc(h->owned, h->d_prob_tile_base, h->P + 1));
@@ -729,12 +731,16 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
                                             float* h_loss_out) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  if (h_params_in)
+  if (h_params_in) {
+    CK(h, launch_adam_flush(h->d, s));  // the step belongs to the old params
     CK(h, cudaMemcpyAsync(h->d.q, h_params_in, sizeof(float4) * h->N, cudaMemcpyHostToDevice, s));
+  }
   collage_status st = collage_step(h, stream, n_iters);
   if (st) return st;
-  if (h_params_out)
+  if (h_params_out) {
+    CK(h, launch_adam_flush(h->d, s));
     CK(h, cudaMemcpyAsync(h_params_out, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToHost, s));
+  }
   if (h_loss_out)
     CK(h, cudaMemcpyAsync(h_loss_out, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
@@ -750,12 +756,14 @@ extern "C" collage_status collage_get_loss(collage_t h, void* stream, float* d_l
 
 extern "C" collage_status collage_get_params(collage_t h, void* stream, float* d_params) {
   if (!h || !d_params) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, launch_adam_flush(h->d, (cudaStream_t)stream));
   CK(h, cudaMemcpyAsync(d_params, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return COLLAGE_OK;
 }
 
 extern "C" collage_status collage_set_params(collage_t h, void* stream, const float* d_params) {
   if (!h || !d_params) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, launch_adam_flush(h->d, (cudaStream_t)stream));  // the step belongs to the old params
   CK(h, cudaMemcpyAsync(h->d.q, d_params, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return COLLAGE_OK;
 }
@@ -765,6 +773,7 @@ extern "C" collage_status collage_get_state(collage_t h, void* stream, float* d_
   if (!h || !d_state) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = sizeof(float4) * h->N;
+  CK(h, launch_adam_flush(h->d, s));
   CK(h, cudaMemcpyAsync(d_state, h->d.q, n, cudaMemcpyDeviceToDevice, s));
   CK(h, cudaMemcpyAsync((char*)d_state + n, h->d.m, n, cudaMemcpyDeviceToDevice, s));
   CK(h, cudaMemcpyAsync((char*)d_state + 2 * n, h->d.v, n, cudaMemcpyDeviceToDevice, s));
@@ -790,6 +799,7 @@ extern "C" collage_status collage_set_state(collage_t h, void* stream, const flo
   CK(h, cudaMemcpyAsync(h->d.v, (const char*)d_state + 2 * n, n, cudaMemcpyDeviceToDevice, s));
   h->h_ctl[1] = h_step;
   CK(h, cudaMemcpyAsync(h->d.step, &h->h_ctl[1], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(h, cudaMemsetAsync(h->d.pending, 0, sizeof(int), s));  // the state replaces everything
   CK(h, cudaStreamSynchronize(s));
   return COLLAGE_OK;
 }
@@ -903,10 +913,10 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   out->total_pixels = h->d.total_pix;
   out->pair_capacity = h->d.cap;
   out->last_pairs = h->h_ctl ? h->h_ctl[2] : 0;
-  // transform, tile scan, emit, pair distances, composite, (2 dilation), raster bwd, (gradient
-  // reduce), loss, Adam
+  // transform (with the previous Adam step), tile scan, emit, pair distances, composite,
+  // (2 dilation), raster bwd, (gradient reduce), loss
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 5 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 2;
+  out->kernels_per_iter = 5 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 1;
   return COLLAGE_OK;
 }
 

@@ -49,39 +49,60 @@ __device__ int4 bin_rect(float4 q, float rbin, float hw, int res, int T, float r
   return r;
 }
 
-// Vertex of an element relative to its translation, in pixels: R(theta) (s v) * res, formed in
-// double and rounded once.  A segment's end point and the next segment's start point come from the
-// same call, so they are bitwise equal (the winding test relies on it).
-__device__ __forceinline__ float2 vertex_px(const float2 v, double c, double sn, double sc) {
-  const double x = sc * (c * (double)v.x - sn * (double)v.y);
-  const double y = sc * (sn * (double)v.x + c * (double)v.y);
-  return make_float2((float)x, (float)y);
+// Vertex of an element relative to its translation, in pixels: (s res R(theta)) v.  The matrix is
+// formed in double once per element and split into float hi + lo parts; the per-vertex product uses
+// error-free transformations in float (FMA two-product and Knuth's two-sum, as in Ogita, Rump &
+// Oishi 2005), so the result is within about one float ulp of the exact value without FP64 work
+// per vertex (FP64 throughput is low on this part).  Explicit round-to-nearest intrinsics keep the
+// compiler from contracting the error terms away.  A segment's end point and the next segment's
+// start point come from the same call, so they are bitwise equal (the winding test relies on it).
+struct RotFF {
+  float m[4][2];  // row-major 2x2, (hi, lo)
+};
+
+__device__ __forceinline__ float dot2_ff(const float (&a)[2], const float (&b)[2], float vx, float vy) {
+  const float p1 = __fmul_rn(a[0], vx), e1 = __fmaf_rn(a[0], vx, -p1);
+  const float p2 = __fmul_rn(b[0], vy), e2 = __fmaf_rn(b[0], vy, -p2);
+  const float sum = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(sum, p1);
+  const float es = __fadd_rn(__fsub_rn(p1, __fsub_rn(sum, bb)), __fsub_rn(p2, bb));
+  const float tail = __fmaf_rn(a[1], vx, __fmaf_rn(b[1], vy, __fadd_rn(__fadd_rn(e1, e2), es)));
+  return __fadd_rn(sum, tail);
 }
 
-// One block per element: segment records (start, direction, end y, 1/|e|^2) of the vertices
+__device__ __forceinline__ float2 vertex_px(const float2 v, const RotFF& M) {
+  return make_float2(dot2_ff(M.m[0], M.m[1], v.x, v.y), dot2_ff(M.m[2], M.m[3], v.x, v.y));
+}
+
+// One block per element: the pending Adam step of the previous iteration, then segment records
+// (start, direction, end y, 1/|e|^2) of the vertices
 // relative to the translation, translation in pixels as a float hi/lo pair, outline box grown by
 // the coverage margin, tile rectangle, and the per-tile element counts of the counting sort.
 // Lanes own consecutive vertices; a segment's end point is the next lane's start point (shuffled),
-// so each vertex is rotated once in double.
+// so each vertex is transformed once.
 constexpr int kTfThreads = 128;
 __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) {
-  __shared__ double s_cs[3];
+  __shared__ RotFF s_rot;
   __shared__ float s_box[4][kTfThreads / 32];
   __shared__ int4 s_rect;
   const int g = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = d.elem_prob[g];
   const int res = d.prob_res[p];
+  if (threadIdx.x == 0 && *d.pending) adam_update(d, g, *d.step, d.dq[g]);  // previous step
+  __syncthreads();
   const float4 q = d.q[g];
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 4) {
     double sn, c;
     sincos((double)q.z, &sn, &c);
-    s_cs[0] = c;
-    s_cs[1] = sn;
-    s_cs[2] = (double)q.w * (double)res;
+    const double sc = (double)q.w * (double)res;
+    const double m = threadIdx.x == 0 ? sc * c : threadIdx.x == 1 ? -sc * sn : threadIdx.x == 2 ? sc * sn : sc * c;
+    const float hi = (float)m;
+    s_rot.m[threadIdx.x][0] = hi;
+    s_rot.m[threadIdx.x][1] = (float)(m - (double)hi);
   }
   __syncthreads();
-  const double c = s_cs[0], sn = s_cs[1], sc = s_cs[2];
+  const RotFF rot = s_rot;
   const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
   const bool closed = d.elem_closed[g] != 0;
   float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
@@ -89,7 +110,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     const int k = k0 + lane;
     float2 a = make_float2(0.f, 0.f);
     if (k < nv) {
-      a = vertex_px(d.vloc[v0 + k], c, sn, sc);
+      a = vertex_px(d.vloc[v0 + k], rot);
       xmin = fminf(xmin, a.x);
       xmax = fmaxf(xmax, a.x);
       ymin = fminf(ymin, a.y);
@@ -99,7 +120,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     b.x = __shfl_down_sync(0xffffffffu, a.x, 1);
     b.y = __shfl_down_sync(0xffffffffu, a.y, 1);
     const int kb = k + 1 == nv ? 0 : k + 1;
-    if (k < nv && (lane == 31 || k + 1 == nv)) b = vertex_px(d.vloc[v0 + kb], c, sn, sc);
+    if (k < nv && (lane == 31 || k + 1 == nv)) b = vertex_px(d.vloc[v0 + kb], rot);
     if (k < nv) {
       float4 sa = make_float4(a.x, a.y, 0.f, 0.f);
       float2 sb = make_float2(a.y, 0.f);
@@ -155,35 +176,26 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     atomicAdd(&d.tile_cnt[tb + (r.y + i / w) * ntx + r.x + i % w], 1);
 }
 
-// Exclusive scan of the per-tile counts into [begin, end) ranges: one block; per round a thread
-// owns 16 consecutive tiles (loaded as four int4), scans them in registers, and the block scans
-// the per-thread totals.  The total is the pair count; above the capacity the overflow bit is
-// latched.
-constexpr int kScanPer = 16;
-__global__ void __launch_bounds__(1024) k_tile_scan(Dev d) {
+// Exclusive scan of the per-tile counts into [begin, end) ranges: one block, rounds of 8192 tiles
+// staged through shared memory so that global loads and stores are coalesced; each thread scans 8
+// consecutive counts, the block scans the per-thread totals.  The total is the pair count; above
+// the capacity the overflow bit is latched.
+constexpr int kScanThreads = 1024, kScanPer = 8, kScanRound = kScanThreads * kScanPer;
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
+  __shared__ int buf[kScanRound + 1];
   __shared__ int wsum[32];
   const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
   int carry = 0;
-  for (int base = 0; base < n; base += 1024 * kScanPer) {
-    const int b = base + t * kScanPer;
+  for (int base = 0; base < n; base += kScanRound) {
+    for (int i = t; i < kScanRound; i += kScanThreads) buf[i] = base + i < n ? d.tile_cnt[base + i] : 0;
+    __syncthreads();
     int v[kScanPer];
-    if (b + kScanPer <= n) {
-      const int4* src = reinterpret_cast<const int4*>(d.tile_cnt + b);
-#pragma unroll
-      for (int i = 0; i < kScanPer / 4; ++i) {
-        const int4 x = src[i];
-        v[4 * i] = x.x;
-        v[4 * i + 1] = x.y;
-        v[4 * i + 2] = x.z;
-        v[4 * i + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < kScanPer; ++i) v[i] = b + i < n ? d.tile_cnt[b + i] : 0;
-    }
     int s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) s += v[i];
+    for (int i = 0; i < kScanPer; ++i) {
+      v[i] = buf[t * kScanPer + i];
+      s += v[i];
+    }
     int x = s;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -201,18 +213,23 @@ __global__ void __launch_bounds__(1024) k_tile_scan(Dev d) {
     }
     __syncthreads();
     int run = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
-    const int round_total = wsum[31];
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-      if (b + i < n) d.range[b + i] = make_uint2((uint32_t)run, (uint32_t)(run + v[i]));
+    for (int i = 0; i < kScanPer; ++i) {  // exclusive starts; buf[kScanRound] = end of the round
+      buf[t * kScanPer + i] = run;
       run += v[i];
     }
+    if (t == kScanThreads - 1) buf[kScanRound] = run;
+    const int round_total = wsum[31];
+    __syncthreads();
+    for (int i = t; i < kScanRound && base + i < n; i += kScanThreads)
+      d.range[base + i] = make_uint2((uint32_t)buf[i], (uint32_t)buf[i + 1]);
     carry += round_total;
-    __syncthreads();  // wsum is reused by the next round
+    __syncthreads();  // buf and wsum are reused by the next round
   }
   if (t == 0) {
     *d.total_pairs = carry;
     if (carry > d.cap) atomicOr(d.status, kStatusOverflow);
+    *d.pending = 0;  // every transform block has applied the pending Adam step
   }
 }
 
@@ -244,7 +261,7 @@ cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad) {
 }
 
 cudaError_t launch_scan(const Dev& d, cudaStream_t s) {
-  k_tile_scan<<<1, 1024, 0, s>>>(d);
+  k_tile_scan<<<1, kScanThreads, 0, s>>>(d);
   return cudaGetLastError();
 }
 

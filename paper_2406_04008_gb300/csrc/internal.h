@@ -88,10 +88,40 @@ struct Dev {
   float4* partial;              // [cap] deterministic gradient partials, at emit position
   float* loss_terms;            // [P*5]
   int* status;                  // [1]
-  int* step;                    // [1] Adam step count
+  int* step;                    // [1] Adam step count (the loss assembly advances it)
+  int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
   LossParams L;
   int deterministic;
 };
+
+// Adam (bias-corrected, the update torch.optim.Adam performs; it stands in for the plain descent
+// step of Eq. 4) of element g at step t >= 1 with gradient gr, then the clamp of s.
+// An iteration's step is applied lazily: the loss assembly marks it pending, and the next
+// iteration's transform kernel (one block per element, which reads the params first anyway)
+// applies it before forming the geometry; API calls that read or replace params flush it.
+__device__ __forceinline__ void adam_update(const Dev& d, int g, int t, float4 gr) {
+  const float bc1 = 1.0f - powf(d.b1, (float)t), bc2 = 1.0f - powf(d.b2, (float)t);
+  const float step_size = d.lr / bc1, bc2s = sqrtf(bc2);
+  float4 q = d.q[g], m = d.m[g], v = d.v[g];
+  const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
+  float* qp = &q.x;
+  float* mp = &m.x;
+  float* vp = &v.x;
+  const float gg[4] = {gr.x, gr.y, gr.z, gr.w};
+  const unsigned char tt[4] = {tr.x, tr.y, tr.z, tr.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!tt[k]) continue;
+    mp[k] = d.b1 * mp[k] + (1.0f - d.b1) * gg[k];
+    vp[k] = d.b2 * vp[k] + (1.0f - d.b2) * gg[k] * gg[k];
+    const float denom = sqrtf(vp[k]) / bc2s + d.eps;
+    qp[k] -= step_size * mp[k] / denom;
+  }
+  q.w = fminf(fmaxf(q.w, d.s_min), d.s_max);
+  d.q[g] = q;
+  d.m[g] = m;
+  d.v[g] = v;
+}
 
 // ---- launchers (each enqueues on `s`, returns the launch error) ----
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
@@ -106,8 +136,9 @@ cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward);
 cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s);  // once per level, after the container
 cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid);
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s);
+// applies a pending Adam step to all elements and clears the flag (before params are read)
+cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step);
-cudaError_t launch_adam(const Dev& d, cudaStream_t s);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
 // resident blocks per SM of the pair kernels and of the per-tile composite (persistent grids)
 void raster_blocks_per_sm(int tile, int* pair_per_sm, int* tile_per_sm);

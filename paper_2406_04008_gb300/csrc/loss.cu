@@ -1,5 +1,5 @@
-// Even-distribution term (Eq. 7), loss assembly (Eq. 8), deterministic gradient reduction and the
-// Adam update that stands in for the descent step of Eq. 4.
+// Even-distribution term (Eq. 7), loss assembly (Eq. 8), the deterministic gradient reduction and
+// the flush of a pending Adam step.
 //
 // Eq. 7 as implemented: K box kernels of widths 5 + 6k pixels (k = 0..K-1) dilate the occupancy
 // O = 1 - Ihat; D_k = min(1, B_k) with B_k the zero-padded box sum; the term sums
@@ -317,13 +317,16 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
       out[2] = u;
       out[3] = Ld;
       out[4] = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * u + d.L.delta * Ld;
-      if (count_step && p == 0 && !(*d.status & kStatusOverflow)) *d.step += 1;
+      if (count_step && p == 0 && !(*d.status & (kStatusOverflow | kStatusBadParam))) {
+        *d.step += 1;  // this iteration's Adam step is now pending (applied by the next transform)
+        *d.pending = 1;
+      }
     }
   }
 }
 
 // Deterministic mode: each element sums its (tile, element) partials over its tile rectangle in
-// row-major order; a tile's list is ordered by element id, so the pair is found by bisection.
+// row-major order (a tile's list is ordered by element id, so the pair is found by bisection).
 __global__ void k_grad_reduce(Dev d) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
@@ -353,33 +356,11 @@ __global__ void k_grad_reduce(Dev d) {
   d.dq[g] = acc;
 }
 
-// Adam (bias-corrected, the update torch.optim.Adam performs), then the clamp of s.
-__global__ void k_adam(Dev d) {
+// Applies a pending Adam step to every element (see adam_update); the caller then clears the flag.
+__global__ void k_adam_flush(Dev d) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
-  const int t = *d.step;
-  const float bc1 = 1.0f - powf(d.b1, (float)t), bc2 = 1.0f - powf(d.b2, (float)t);
-  const float step_size = d.lr / bc1, bc2s = sqrtf(bc2);
-  float4 q = d.q[g], m = d.m[g], v = d.v[g];
-  const float4 gr = d.dq[g];
-  const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
-  float* qp = &q.x;
-  float* mp = &m.x;
-  float* vp = &v.x;
-  const float gg[4] = {gr.x, gr.y, gr.z, gr.w};
-  const unsigned char tt[4] = {tr.x, tr.y, tr.z, tr.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (!tt[k]) continue;
-    mp[k] = d.b1 * mp[k] + (1.0f - d.b1) * gg[k];
-    vp[k] = d.b2 * vp[k] + (1.0f - d.b2) * gg[k] * gg[k];
-    const float denom = sqrtf(vp[k]) / bc2s + d.eps;
-    qp[k] -= step_size * mp[k] / denom;
-  }
-  q.w = fminf(fmaxf(q.w, d.s_min), d.s_max);
-  d.q[g] = q;
-  d.m[g] = m;
-  d.v[g] = v;
+  if (g >= d.n_elems || !*d.pending) return;
+  adam_update(d, g, *d.step, d.dq[g]);
 }
 
 static size_t dilate_smem(int K, bool backward) {
@@ -456,9 +437,11 @@ cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(const Dev& d, cudaStream_t s) {
-  k_adam<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d);
-  return cudaGetLastError();
+cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s) {
+  k_adam_flush<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(d.pending, 0, sizeof(int), s);
 }
 
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out) {
