@@ -40,7 +40,7 @@ FLOP_PER_PAIR = 14
 # ncu capture of the raster forward kernel (dram__bytes_read.sum + dram__bytes_write.sum per
 # launch) and the hash of raster.cu it was taken with; the figure is reported only while the
 # source is unchanged.
-NCU_TRAFFIC = {"raster_src_sha1": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"raster_src_sha1": "cbb3bcbc5b2f9c7e6d1b2ea27342690226f592b8", "bytes_per_launch": 2259200}
 
 
 def _peaks():
@@ -49,6 +49,16 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def _measured_fp32_peak(torch):
+    """FP32 FMA rate of this GPU in TFLOP/s, from the library's FMA-chain kernel."""
+    import ctypes as C
+    from paper_2406_04008_gb300 import _lib
+    out = C.c_float()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _lib.check(_lib.load().collage_fp32_peak(stream, C.byref(out)))
+    return float(out.value)
 
 
 def _raster_src_sha1():
@@ -72,10 +82,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()  # the timed region starts once samples flow
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.lines.clear()
         except OSError:
             self.proc = None
         return self
@@ -126,19 +140,25 @@ def _opts(**kw):
 
 
 def _time_steps(col, steps, flush, torch):
-    """Per-step device time with CUDA events on the launching stream, L2 flushed between steps."""
+    """Per-step device time with CUDA events on the launching stream, L2 flushed between steps.
+    Steps are enqueued without a host round trip (collage_step_async); the status word is checked
+    once after the loop, and a run that met a bin overflow (iterations skipped) is an error."""
     stream = torch.cuda.current_stream()
-    times = []
+    _, step0, _ = col.get_state()
+    ev = []
     for _ in range(steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        col.step(1)
+        col.step_async(1)
         b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b) / 1e3)
-    return times
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    col.sync()
+    _, step1, _ = col.get_state()
+    assert step1 - step0 == steps, "iterations were skipped inside the timed region"
+    return [a.elapsed_time(b) / 1e3 for a, b in ev]
 
 
 def run_reference(args):
@@ -222,6 +242,43 @@ def cpu_baseline(max_seconds=20.0):
                       f"workload, OpenMP over pixel rows"}, pairs
 
 
+def cpu_per_config():
+    """Seconds per FP64 oracle iteration (forward, gradient, Adam) at each workload's finest level,
+    on all host cores, plus the 1024^2 workload on one core.  One iteration each (three for the
+    16-disk case); for the 64-collage batch, 8 of its collages (the seconds are for those 8)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2406_04008_gb300 import workloads as W
+
+    def per_iter(prob, grid, opts, iters=1):
+        sc = O.Scene(prob)
+        o = O.options(**opts)
+        q = prob["params0"].astype(np.float64)
+        m, v = np.zeros_like(q), np.zeros_like(q)
+        t0 = time.perf_counter()
+        for i in range(iters):
+            g = sc.eval(q, grid, o)["grad_a"]
+            q, m, v = O.adam(q, m, v, g, i + 1)
+        return (time.perf_counter() - t0) / iters
+
+    out = {"unit": "s/iteration", "cores": os.cpu_count()}
+    out["disks16_128"] = per_iter(W.config_problem(1), 128, dict(gamma=0.0), 3)
+    out["blobs200_star_512"] = per_iter(W.config_problem(2), 512, {})
+    t0 = time.perf_counter()
+    for i in range(8):
+        p = W.config_problem(4, i)
+        per_iter(p, p["grid"], {})
+    out["batch64_first8"] = time.perf_counter() - t0
+    out["open5000_rect_2048"] = per_iter(W.config_problem(5), 2048, dict(pad_px=1.0, delta=1e3))
+    prev = O.set_threads(1)
+    try:
+        out["mixed1000_annulus_1024_1core"] = per_iter(_workload(), 1024, dict(pad_px=2.0))
+    finally:
+        O.set_threads(prev)
+    return out
+
+
 def batch_vs_plain(steps, flush, torch):
     """64 independent collages (n ~ U[20, 800], grids 256/512/1024, stars and annuli): one batched,
     graph-captured, persistent, autotuned handle against 64 plain handles stepped one after
@@ -249,11 +306,12 @@ def batch_vs_plain(steps, flush, torch):
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for c in plain:
-            c.step(1)
+            c.step_async(1)
         b.record(stream)
         b.synchronize()
         pt += a.elapsed_time(b) / 1e3
     for c in plain:
+        c.sync()
         c.close()
     return {"workload": "batch64: 64 collages, %d elements in all, grids 256/512/1024" % n_elems,
             "batched": steps / bt, "plain_sequential": steps / pt, "speedup": pt / bt,
@@ -296,7 +354,7 @@ def schedule_time(torch):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -410,11 +468,13 @@ def main():
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    fp32_nominal = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    fp32_peak = _measured_fp32_peak(torch)
     cpu = None
     pairs = None
     if not args.no_cpu_baseline and world == 1:
         cpu, pairs = cpu_baseline()
+        cpu["per_workload"] = cpu_per_config()
     roof = None
     if pairs is not None:
         t_fwd = stages["raster_fwd"] / 1e3
@@ -423,7 +483,9 @@ def main():
             if NCU_TRAFFIC["raster_src_sha1"] == _raster_src_sha1() else None
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_pair_sd",
-                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "peak_source": "measured: FP32 FMA-chain kernel (collage_fp32_peak), burst",
+                "peak_nominal": fp32_nominal,
+                "peak_nominal_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "work": f"{pairs:.4g} pixel-segment pairs x {FLOP_PER_PAIR} flop",
                 "launch_ms": stages["raster_fwd"]}
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,

@@ -83,9 +83,13 @@ typedef struct {
   float s_min, s_max;                   /* scale clamp after each step (default 0.05, 20) */
   int deterministic;                    /* 1: gradients reduced in a fixed order (bitwise
                                            reproducible); 0: warp-reduced float atomics */
-  int tile;                             /* raster tile side 8, 16 or 32; 0 = autotune */
+  int tile;                             /* raster tile side 8 or 16; 0 = autotune */
   int persistent;                       /* 1: grid-stride launches sized to the SM count */
   int use_graphs;                       /* 1: collage_step replays a captured CUDA graph */
+  int overlap_launches;                 /* 1: each kernel of an iteration is launched with
+                                           programmatic stream serialisation, so its launch and
+                                           block scheduling overlap the previous kernel's tail;
+                                           results are bitwise the same either way */
 } collage_options;
 
 /* Per-level sizes, for callers that allocate image buffers. */
@@ -106,7 +110,7 @@ void collage_default_options(collage_options* opt);
  * each, allocates device memory, and selects level 0.  The current CUDA device is used.
  * Returns INVALID_ARG (with the offending field in collage_last_error(NULL)) for: n_probs < 1,
  * n_elems < 1, unknown kind, too few points, NaN/Inf or s <= 0 params, rings with < 3 points,
- * grid not divisible as the level schedule requires, tile not in {0, 8, 16, 32}. */
+ * grid not divisible as the level schedule requires, tile not in {0, 8, 16}. */
 collage_status collage_create(const collage_problem* probs, int n_probs,
                               const collage_options* opt, collage_t* out);
 
@@ -134,6 +138,14 @@ collage_status collage_loss_backward(collage_t h, void* stream, float* d_loss_te
  * (get_params, get_state, set_params, step_host) applies a pending step first, so callers always
  * observe the updated params. */
 collage_status collage_step(collage_t h, void* stream, int n_iters);
+
+/* Enqueues n_iters >= 0 iterations exactly as collage_step does and returns without waiting for
+ * the stream.  A bin overflow met on the device latches the status word and turns the remaining
+ * enqueued iterations into no-ops (the step counter of collage_get_state counts only the ones
+ * that ran); collage_sync then regrows the buffers and returns COLLAGE_ERR_OVERFLOW so that the
+ * caller can enqueue the missing iterations again.  No host round trip per call: this is the
+ * form for timing the device work of one iteration and for overlapping it with host work. */
+collage_status collage_step_async(collage_t h, void* stream, int n_iters);
 
 /* Runs every level of the schedule from the current one: set_level + level_iters[l] steps. */
 collage_status collage_run_schedule(collage_t h, void* stream);
@@ -204,6 +216,12 @@ collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
 collage_status collage_uniform_term_noalloc(void* stream, int res, int n_dilations,
                                             const float* h_dil_weight, const float* d_ihat,
                                             const float* d_cov, float* d_loss, float* d_grad_occ);
+
+/* Measurement helper, no counterpart in the paper: the FP32 FMA rate of the current device in
+ * TFLOP/s (eight independent FMA chains per thread at full occupancy, best of three timed launches
+ * after a warm-up), the ceiling of the ALU-bound distance kernel.  Writes *h_tflops (host memory);
+ * INVALID_ARG for NULL, CUDA on a launch or event failure.  Synchronises `stream`. */
+collage_status collage_fp32_peak(void* stream, float* h_tflops);
 
 collage_status collage_get_info(collage_t h, collage_info* out);
 /* Waits for the stream and returns any latched device error. */

@@ -750,3 +750,9 @@ double ora_pair_work(const ora_scene* sc, const double* params, int R, const ora
   free_world(&g);
   return work;
 }
+
+int ora_set_threads(int n) {
+  const int prev = omp_get_max_threads();
+  omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+  return prev;
+}

@@ -90,6 +90,10 @@ float ora_bin_radius(const ora_scene* sc, int e);
  * grown by rho + pad (+ stroke half-width)) x (segments of the element). */
 double ora_pair_work(const ora_scene* sc, const double* params, int res, const ora_opts* o);
 
+/* Threads the OpenMP loops use from now on (n < 1: all the host's cores); returns the previous
+ * setting.  For timing the oracle on one core. */
+int ora_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,8 @@ def _load():
     lib.ora_bin_radius.argtypes = [vp, C.c_int]
     lib.ora_pair_work.restype = C.c_double
     lib.ora_pair_work.argtypes = [vp, _dp, C.c_int, opt]
+    lib.ora_set_threads.restype = C.c_int
+    lib.ora_set_threads.argtypes = [C.c_int]
     _lib = lib
     return lib
 
@@ -190,6 +192,11 @@ class Scene:
 
     def pair_work(self, params, res, opts):
         return self.lib.ora_pair_work(self.h, _d(params), res, C.byref(opts))
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (n < 1: all cores); returns the previous setting."""
+    return _load().ora_set_threads(n)
 
 
 def _d(params):

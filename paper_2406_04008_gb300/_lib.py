@@ -40,7 +40,8 @@ class collage_options(C.Structure):
                 ("n_levels", C.c_int), ("level_res", C.c_int * 8), ("level_iters", C.c_int * 8),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("s_min", C.c_float), ("s_max", C.c_float), ("deterministic", C.c_int),
-                ("tile", C.c_int), ("persistent", C.c_int), ("use_graphs", C.c_int)]
+                ("tile", C.c_int), ("persistent", C.c_int), ("use_graphs", C.c_int),
+                ("overlap_launches", C.c_int)]
 
 
 class collage_info(C.Structure):
@@ -58,7 +59,9 @@ SIGNATURES = {
     "collage_set_level": (C.c_int, [_vp, C.c_int]),
     "collage_render": (C.c_int, [_vp, _vp, _vp, _vp]),
     "collage_loss_backward": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "collage_fp32_peak": (C.c_int, [_vp, C.c_void_p]),
     "collage_step": (C.c_int, [_vp, _vp, C.c_int]),
+    "collage_step_async": (C.c_int, [_vp, _vp, C.c_int]),
     "collage_run_schedule": (C.c_int, [_vp, _vp]),
     "collage_step_host": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
     "collage_get_loss": (C.c_int, [_vp, _vp, _vp]),

@@ -79,6 +79,10 @@ class Collage:
     def step(self, n_iters: int = 1):
         self._check(self.lib.collage_step(self.h, _stream(), n_iters))
 
+    def step_async(self, n_iters: int = 1):
+        """Enqueue n_iters iterations without waiting; sync() reports a latched overflow."""
+        self._check(self.lib.collage_step_async(self.h, _stream(), n_iters))
+
     def run_schedule(self):
         self._check(self.lib.collage_run_schedule(self.h, _stream()))
 

@@ -35,7 +35,8 @@ struct collage_s {
   int level = -1;
   std::vector<int> res, ntx, tile_base, dtile_base;
   std::vector<long long> pix_base;
-  int pair_grid = 0;  // grid of the per-pair raster kernels
+  int pair_grid = 0;  // grid of the per-pair distance kernel
+  int bwd_grid = 0;   // grid of the per-pair adjoint
   int tile_grid = 0;  // grid of the per-tile composite
   int sms = 1;
   // device memory
@@ -47,7 +48,7 @@ struct collage_s {
   int* d_prob_tile_base = nullptr;
   int* d_prob_dtile_base = nullptr;
   long long* d_prob_pix_base = nullptr;
-  int* ctl = nullptr;        // device: status, step, total_pairs, pad
+  int* ctl = nullptr;        // device: status, step, total_pairs, pending, 4 work counters
   int* h_ctl = nullptr;      // pinned mirror
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -150,6 +151,7 @@ extern "C" void collage_default_options(collage_options* o) {
   o->tile = 16;
   o->persistent = 1;
   o->use_graphs = 1;
+  o->overlap_launches = 1;
 }
 
 static std::string check_options(const collage_options& o) {
@@ -158,7 +160,7 @@ static std::string check_options(const collage_options& o) {
     if (o.level_res[l] < 1) return "level_res[" + std::to_string(l) + "] must be >= 1";
     if (o.level_iters[l] < 0) return "level_iters[" + std::to_string(l) + "] must be >= 0";
   }
-  if (!(o.tile == 0 || o.tile == 8 || o.tile == 16 || o.tile == 32)) return "tile must be 0, 8, 16 or 32";
+  if (!(o.tile == 0 || o.tile == 8 || o.tile == 16)) return "tile must be 0, 8 or 16";
   if (o.n_dilations < 0 || o.n_dilations > 8) return "n_dilations must be in 0..8";
   const float f[] = {o.alpha, o.beta, o.gamma, o.delta_down, o.w_in, o.w_out, o.lr, o.eps};
   for (float x : f)
@@ -260,14 +262,17 @@ static void flatten(const collage_problem& p, int e, int spc, std::vector<float2
 // Persistent grids: resident blocks per SM times the SM count; plain grids: one block per work
 // item (pairs up to the capacity, every tile).
 static void set_grids(collage_t h) {
-  int pper = 1, tper = 1;
-  raster_blocks_per_sm(h->d.tile, &pper, &tper);
+  RasterOcc o{};
+  raster_occupancy(h->d.tile, &o);
   if (h->opt.persistent) {
-    h->pair_grid = h->sms * pper;
-    h->tile_grid = std::min(h->d.total_tiles, h->sms * tper);
+    h->pair_grid = h->sms * o.fwd_per_sm;
+    h->bwd_grid = h->sms * o.bwd_per_sm;
+    h->tile_grid = std::min((h->d.total_tiles + o.tiles_per_block - 1) / o.tiles_per_block,
+                            h->sms * o.tile_per_sm);
   } else {
     h->pair_grid = std::max(h->d.cap, 1);
-    h->tile_grid = h->d.total_tiles;
+    h->bwd_grid = std::max((h->d.cap + o.bwd_pairs_per_block - 1) / o.bwd_pairs_per_block, 1);
+    h->tile_grid = (h->d.total_tiles + o.tiles_per_block - 1) / o.tiles_per_block;
   }
 }
 
@@ -281,7 +286,9 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   Dev& d = h->d;
   CK(h, dmalloc(h->pair_bufs, d.pair_elem, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_tile, cap));
-  CK(h, dmalloc(h->pair_bufs, d.pair_live, cap));
+  CK(h, dmalloc(h->pair_bufs, d.live_list, cap));
+  CK(h, dmalloc(h->pair_bufs, d.near_list, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_cls, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_sorted, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_slot, cap));
   CK(h, dmalloc(h->pair_bufs, d.partial, cap));
@@ -402,7 +409,7 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
     STEP_(launch_dilate(d, s, true));
   }
   MARK_(5);
-  if (bwd) STEP_(launch_raster_bwd(d, s, h->pair_grid));
+  if (bwd) STEP_(launch_raster_bwd(d, s, h->bwd_grid));
   MARK_(6);
   if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
   MARK_(7);
@@ -553,6 +560,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.n_probs = h->P;
   d.tile = h->opt.tile;
   d.deterministic = o.deterministic ? 1 : 0;
+  d.pdl = o.overlap_launches ? 1 : 0;
   d.lr = o.lr;
   d.b1 = o.beta1;
   d.b2 = o.beta2;
@@ -626,12 +634,13 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   CKC(cudaMemset(d.dq, 0, sizeof(float4) * h->N));
   CKC(dmalloc(h->owned, d.loss_terms, 5 * h->P));
   CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
-  CKC(dmalloc(h->owned, h->ctl, 4));
-  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 4));
+  CKC(dmalloc(h->owned, h->ctl, 8));
+  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 8));
   d.status = h->ctl;
   d.step = h->ctl + 1;
   d.total_pairs = h->ctl + 2;
   d.pending = h->ctl + 3;
+  d.work = h->ctl + 4;
   CKC(dmalloc(h->owned, h->d_prob_res, h->P));
   CKC(dmalloc(h->owned, h->d_prob_ntx, h->P));
   CKC(dmalloc(h->owned, h->d_prob_tile_base, h->P + 1));
@@ -685,32 +694,43 @@ extern "C" collage_status collage_loss_backward(collage_t h, void* stream, float
   return COLLAGE_OK;
 }
 
+// Enqueues n iterations in step mode: graph replays or eager launches.
+static collage_status enqueue_steps(collage_t h, cudaStream_t s, int n) {
+  if (h->opt.use_graphs) {
+    collage_status st = ensure_graph(h);
+    if (st) return st;
+    for (int i = 0; i < n; ++i) CK(h, cudaGraphLaunch(h->graph, s));
+  } else {
+    for (int i = 0; i < n; ++i) CK(h, enqueue_iter(h, s, kStep, nullptr, nullptr));
+  }
+  return COLLAGE_OK;
+}
+
 extern "C" collage_status collage_step(collage_t h, void* stream, int n_iters) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
   if (n_iters < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "n_iters must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   int remaining = n_iters;
+  collage_status st = remaining > 0 ? read_ctl(h, s) : COLLAGE_OK;
+  if (st) return st;
   for (int attempt = 0; remaining > 0 && attempt < 8; ++attempt) {
-    collage_status st = read_ctl(h, s);
-    if (st) return st;
     const int step0 = h->h_ctl[1];
-    if (h->opt.use_graphs) {
-      st = ensure_graph(h);
-      if (st) return st;
-      for (int i = 0; i < remaining; ++i) CK(h, cudaGraphLaunch(h->graph, s));
-    } else {
-      for (int i = 0; i < remaining; ++i) CK(h, enqueue_iter(h, s, kStep, nullptr, nullptr));
-    }
-    bool over = false;
-    st = check_and_grow(h, s, &over);
+    st = enqueue_steps(h, s, remaining);
     if (st) return st;
-    st = read_ctl(h, s);
+    bool over = false;
+    st = check_and_grow(h, s, &over);  // reads the status and the step counter
     if (st) return st;
     remaining -= h->h_ctl[1] - step0;
     if (!over && remaining > 0) return fail(h, COLLAGE_ERR_STATE, "iterations went missing");
   }
   if (remaining > 0) return fail(h, COLLAGE_ERR_OVERFLOW, "bin capacity kept overflowing");
   return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_step_async(collage_t h, void* stream, int n_iters) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  if (n_iters < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "n_iters must be >= 0");
+  return enqueue_steps(h, (cudaStream_t)stream, n_iters);
 }
 
 extern "C" collage_status collage_run_schedule(collage_t h, void* stream) {
@@ -864,7 +884,7 @@ extern "C" collage_status collage_stage_times(collage_t h, void* stream, int n_i
 extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int tiles[3] = {8, 16, 32};
+  const int tiles[2] = {8, 16};
   float best = 1e30f;
   int best_tile = h->d.tile;
   cudaEvent_t a, b;

@@ -82,6 +82,7 @@ __device__ __forceinline__ float2 vertex_px(const float2 v, const RotFF& M) {
 // so each vertex is transformed once.
 constexpr int kTfThreads = 128;
 __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) {
+  pdl_enter();
   __shared__ RotFF s_rot;
   __shared__ float s_box[4][kTfThreads / 32];
   __shared__ int4 s_rect;
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
 // the capacity the overflow bit is latched.
 constexpr int kScanThreads = 1024, kScanPer = 8, kScanRound = kScanThreads * kScanPer;
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
+  pdl_enter();
   __shared__ int buf[kScanRound + 1];
   __shared__ int wsum[32];
   const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -230,45 +232,132 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
     *d.total_pairs = carry;
     if (carry > d.cap) atomicOr(d.status, kStatusOverflow);
     *d.pending = 0;  // every transform block has applied the pending Adam step
+    for (int i = 0; i < 4; ++i) d.work[i] = 0;
   }
 }
 
-// Emission: each (tile, element) pair takes a slot of its tile's range by counting the tile back
-// down (so the counts are zero again for the next iteration, also after an overflow).
-__global__ void k_emit(Dev d) {
-  const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+// Emission, one block per element.  Classification of the element's tiles first, in work
+// proportional to its segments rather than segments x tiles:
+//  - near: every segment marks the tiles whose pixel-centre box, grown by the coverage margin,
+//    its own box meets (computed with 0.05 px of slack, so the mark is a superset of the
+//    distance kernel's near test: a tile it leaves unmarked has no segment within the margin);
+//  - inside / outside for the other tiles: the winding number at a tile's first pixel, from the
+//    crossings of that pixel row with the segments (half-open test).  A crossing at x counts for
+//    the tiles whose first pixel lies left of x; it is added to the last such tile of the row and
+//    a suffix sum along the row spreads it.  For a tile that is not near, every crossing is
+//    farther than the margin from its pixel, so the comparison is well conditioned.
+// Then one thread per tile: the (tile, element) pair takes a slot of its tile's range by counting
+// the tile back down (so the counts are zero again for the next iteration, also after an
+// overflow), and near pairs are appended to the distance kernel's list (one atomic per warp).
+constexpr int kEmitThreads = 128, kEmitChunkRows = 32, kEmitMaxW = 64;
+__global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
+  pdl_enter();
+  __shared__ uint8_t s_near[kEmitChunkRows * kEmitMaxW];
+  __shared__ int s_wind[kEmitChunkRows * kEmitMaxW];
+  const int g = blockIdx.x;
   const int lane = threadIdx.x & 31;
-  if (g >= d.n_elems) return;
   const int4 r = d.rect[g];
   if (r.z < r.x || r.w < r.y) return;
-  const int w = r.z - r.x + 1, n = w * (r.w - r.y + 1);
+  const int w = r.z - r.x + 1, hgt = r.w - r.y + 1;
   const int p = d.elem_prob[g];
-  const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
-  for (int i = lane; i < n; i += 32) {
-    const int t = tb + (r.y + i / w) * ntx + r.x + i % w;
-    const int slot = atomicSub(&d.tile_cnt[t], 1) - 1;
-    const unsigned pos = d.range[t].x + (unsigned)slot;
-    if (pos < (unsigned)d.cap) {
-      d.pair_elem[pos] = g;
-      d.pair_tile[pos] = t;
+  const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p], T = d.tile;
+  const bool ovf = (*d.status & kStatusOverflow) != 0;  // slots are void: only count back down
+  const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
+  const bool closed = d.elem_closed[g] != 0;
+  const int ns = ovf ? 0 : (closed ? nv : nv - 1);
+  const float4 tp = d.tpx[g];
+  const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)d.prob_res[p];
+  const float mrg = d.L.rho_px + d.L.pad_px + hwpx;
+  const float fT = (float)T, tpx = tp.x + tp.z, tpy = tp.y + tp.w;
+  // rectangles wider than kEmitMaxW tiles are classified in column strips
+  for (int cx0 = 0; cx0 < w; cx0 += kEmitMaxW) {
+    const int cw = min(kEmitMaxW, w - cx0);
+    for (int cy0 = 0; cy0 < hgt; cy0 += kEmitChunkRows) {
+      const int ch = min(kEmitChunkRows, hgt - cy0), cn = cw * ch;
+      const int tx_lo = r.x + cx0, ty_lo = r.y + cy0;  // chunk origin in tiles
+      __syncthreads();  // the previous chunk's readers are done
+      for (int i = threadIdx.x; i < cn; i += kEmitThreads) {
+        s_near[i] = 0;
+        s_wind[i] = 0;
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < ns; j += kEmitThreads) {
+        const float4 sa = d.segA[v0 + j];
+        const float2 sb = d.segB[v0 + j];
+        const float bx = sa.x + sa.z;
+        // near: tiles whose grown pixel-centre box meets the segment's box (in pixels)
+        const float x0 = fminf(sa.x, bx) + tpx, x1 = fmaxf(sa.x, bx) + tpx;
+        const float y0 = fminf(sa.y, sb.x) + tpy, y1 = fmaxf(sa.y, sb.x) + tpy;
+        const float m = mrg + 0.06f;
+        const int ax = max((int)floorf((x0 - m - (fT - 0.5f)) / fT) + 1, tx_lo);
+        const int bxt = min((int)floorf((x1 + m - 0.5f) / fT), tx_lo + cw - 1);
+        const int ay = max((int)floorf((y0 - m - (fT - 0.5f)) / fT) + 1, ty_lo);
+        const int byt = min((int)floorf((y1 + m - 0.5f) / fT), ty_lo + ch - 1);
+        for (int ty = ay; ty <= byt; ++ty)
+          for (int tx = ax; tx <= bxt; ++tx) s_near[(ty - ty_lo) * cw + (tx - tx_lo)] = 1;
+        // crossings of the tiles' first pixel rows
+        if (closed) {
+          for (int ty = ty_lo; ty < ty_lo + ch; ++ty) {
+            const float py = ((float)(ty * T) + 0.5f - tp.y) - tp.w;
+            const bool a_le = py - sa.y >= 0.0f, b_le = py - sb.x >= 0.0f;
+            if (a_le == b_le) continue;
+            const float xc = sa.x + sa.z * ((py - sa.y) / sa.w);  // element frame
+            // last tile whose first pixel lies left of xc
+            int tx = (int)floorf((xc + tpx - 0.5f) / fT);
+            if (tx < tx_lo) continue;
+            tx = min(tx, tx_lo + cw - 1);
+            atomicAdd(&s_wind[(ty - ty_lo) * cw + (tx - tx_lo)], a_le ? 1 : -1);
+          }
+        }
+      }
+      __syncthreads();
+      if (closed && !ovf)  // suffix sums along each row (crossings right of the strip included)
+        for (int row = threadIdx.x; row < ch; row += kEmitThreads) {
+          int acc = 0;
+          for (int c = cw - 1; c >= 0; --c) {
+            acc += s_wind[row * cw + c];
+            s_wind[row * cw + c] = acc;
+          }
+        }
+      __syncthreads();
+      for (int i0 = 0; i0 < cn; i0 += kEmitThreads) {  // warp-uniform trip count
+        const int i = i0 + threadIdx.x;
+        int pos = -1;
+        uint8_t cls = kPairOut;
+        if (i < cn) {
+          const int t = tb + (ty_lo + i / cw) * ntx + tx_lo + i % cw;
+          const int slot = atomicSub(&d.tile_cnt[t], 1) - 1;
+          const unsigned u = d.range[t].x + (unsigned)slot;
+          if (!ovf && u < (unsigned)d.cap) {
+            pos = (int)u;
+            cls = s_near[i] ? kPairNear : (closed && s_wind[i] != 0 ? kPairIn : kPairOut);
+            d.pair_elem[pos] = g;
+            d.pair_tile[pos] = t;
+            d.pair_cls[pos] = cls;
+            if (cls != kPairNear && d.deterministic) d.partial[pos] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+        const bool near = pos >= 0 && cls == kPairNear;
+        const unsigned bal = __ballot_sync(0xffffffffu, near);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&d.work[2], __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (near) d.near_list[base + __popc(bal & ((1u << lane) - 1u))] = pos;
+      }
     }
   }
 }
 
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad) {
-  k_transform<<<d.n_elems, kTfThreads, 0, s>>>(d, zero_grad ? 1 : 0);
-  return cudaGetLastError();
+  return klaunch(d.pdl, k_transform, d.n_elems, kTfThreads, 0, s, d, zero_grad ? 1 : 0);
 }
 
 cudaError_t launch_scan(const Dev& d, cudaStream_t s) {
-  k_tile_scan<<<1, kScanThreads, 0, s>>>(d);
-  return cudaGetLastError();
+  return klaunch(d.pdl, k_tile_scan, 1, kScanThreads, 0, s, d);
 }
 
 cudaError_t launch_bin(const Dev& d, cudaStream_t s) {
-  const int warps = 8;
-  k_emit<<<(d.n_elems + warps - 1) / warps, warps * 32, 0, s>>>(d);
-  return cudaGetLastError();
+  return klaunch(d.pdl, k_emit, d.n_elems, kEmitThreads, 0, s, d);
 }
 
 }  // namespace collage

@@ -22,6 +22,14 @@ constexpr int kStatusOverflow = 1;      // device status bits
 constexpr int kStatusBadParam = 2;
 constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bug)
 
+// Class of a (tile, element) pair.  A pair is near when some segment of the outline lies within
+// the coverage margin (rho + pad + stroke half-width) of some pixel centre of the tile; otherwise
+// the coverage and the padded coverage are the same saturated value (0 or 1) on every pixel of
+// the tile and the pair carries no gradient.
+constexpr uint8_t kPairOut = 0;   // not near, outside the outline: c = c^pad = 0
+constexpr uint8_t kPairIn = 1;    // not near, inside: c = c^pad = 1
+constexpr uint8_t kPairNear = 2;  // per-pixel signed distances (the distance kernel)
+
 struct LossParams {
   float alpha, beta, gamma, delta;
   float tau, w_in, w_out;
@@ -70,14 +78,17 @@ struct Dev {
   int cap;                      // pair capacity
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
   int* pair_tile;               // [cap] tile of each pair slot
-  uint8_t* pair_live;           // [cap] 1 if some pixel of the pair has non-saturated coverage
+  uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
+  int* near_list;               // [cap] slots of the near pairs (the distance kernel's work list)
+  int* live_list;               // [cap] slots of the pairs with some non-saturated pixel
+                                //   (the adjoint's work list; order depends on atomics)
   int* pair_sorted;             // [cap] each tile's elements in increasing element order
   int* pair_slot;               // [cap] the pair slot of each pair_sorted entry
   uint2* range;                 // [total_tiles] [begin, end) into the pair arrays
   float2* saved;                // [cap * tile*tile] (sd px, closest segment as int bits)
   float* covc;                  // [pix] container coverage
   float* img_I;                 // [pix] Ihat = prod(1 - c)
-  float* img_Pt;                // [pix] prod(1 - tau c^pad)
+  float* img_Pt;                // [pix] +-prod(1 - tau c^pad), negative where A_tau > tau
   float* gOu;                   // [pix] dL_u/dO
   float* dil_m;                 // [pix] M_C (1 - O), masked per kernel by dil_mask
   uint8_t* dil_mask;            // [pix] bit k: B_k < 1
@@ -90,8 +101,12 @@ struct Dev {
   int* status;                  // [1]
   int* step;                    // [1] Adam step count (the loss assembly advances it)
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
+  int* work;                    // [4] per-iteration counters, zeroed by the tile scan:
+                                //   [0] near pairs taken by the distance kernel's blocks,
+                                //   [1] entries of live_list, [2] entries of near_list, [3] spare
   LossParams L;
   int deterministic;
+  int pdl;                      // launch the iteration's kernels with programmatic serialisation
 };
 
 // Adam (bias-corrected, the update torch.optim.Adam performs; it stands in for the plain descent
@@ -123,6 +138,34 @@ __device__ __forceinline__ void adam_update(const Dev& d, int g, int t, float4 g
   d.v[g] = v;
 }
 
+// ---- programmatic dependent launch ----
+// With Dev::pdl set, the kernels of an iteration are launched with programmatic stream
+// serialisation: a kernel may be scheduled while its predecessor on the stream still runs.  Every
+// such kernel starts with pdl_enter(): griddepcontrol.wait returns once the predecessor grid has
+// completed and its memory operations are visible (before any global access or early return, so
+// completion stays transitive along the chain), then launch_dependents lets the successor be
+// scheduled.  Launched without the attribute, both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t klaunch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---- launchers (each enqueues on `s`, returns the launch error) ----
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
 cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
@@ -140,7 +183,11 @@ cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s);
 cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
-// resident blocks per SM of the pair kernels and of the per-tile composite (persistent grids)
-void raster_blocks_per_sm(int tile, int* pair_per_sm, int* tile_per_sm);
+// Resident blocks per SM of the raster kernels, the pairs one adjoint block and the tiles one
+// composite block take at once (the forward distance kernel takes one pair per block).
+struct RasterOcc {
+  int fwd_per_sm, bwd_per_sm, tile_per_sm, bwd_pairs_per_block, tiles_per_block;
+};
+void raster_occupancy(int tile, RasterOcc* o);
 
 }  // namespace collage

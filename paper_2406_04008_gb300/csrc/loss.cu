@@ -6,7 +6,7 @@
 // w_k M_C (1 - O) (1 - D_k) over the container.  Its adjoint is
 //   dL_u/dO(q) = sum_k w_k [ -M_C(q)(1 - D_k(q)) - sum_{p in box_k(q)} M_C(p)(1 - O(p)) [B_k(p) < 1] ].
 // Both passes stage a 32 x 32 tile plus a halo of the largest radius in shared memory and form the
-// box sums separably (rows, then columns) with running windows.
+// box sums separably (rows, then columns) with running windows, in fixed point.
 #include "internal.h"
 
 namespace collage {
@@ -25,95 +25,128 @@ __device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
   return lo;
 }
 
-__host__ __device__ __forceinline__ int dil_radius(int k) { return 2 + 3 * k; }  // (5 + 6k - 1) / 2
-
-// Box sums by running windows: a thread owns kSeg consecutive outputs of one row (or column) of
-// one kernel, forms the first window directly and slides it (one add, one subtract per output).
-// Restarting every kSeg outputs keeps the float rounding at the level of a direct sum.  The
-// kernels are instantiated per number of dilations K so that every window loop unrolls.
-constexpr int kSeg = 8;
+// Box sums in fixed point: a value v in [0, 1] is held as round(v 2^Q) in a 32-bit unsigned
+// integer, with Q the largest precision for which (w^2 + w) 2^Q < 2^32, w the widest kernel.
+// Integer sums are exact in any order (unsigned wrap-around cancels between the add and the
+// subtract of a running window, and every box sum is below 2^32), so a thread slides one window
+// along kSeg outputs of a row (or column) of one kernel with one add and one subtract per output
+// and no rounding drift.  The kernels are instantiated per number of dilations K so that every
+// window loop unrolls.
+//
+// Shared-memory layout, chosen so that the 32 lanes of a warp touch 32 distinct banks: the staged
+// region has an odd row stride; the horizontal sums H of kernel k keep only the 32 + 2 r_k rows its
+// vertical pass reads, with a row stride of 33; consecutive lanes take consecutive rows in the
+// horizontal pass and consecutive columns in the vertical one.
+constexpr int kSeg = 16;
 constexpr int kNSeg = kDT / kSeg;
+constexpr int kHP = kDT + 1;  // row stride of H
 constexpr int kFlagOwn = 1;   // container coverage is nonzero somewhere on the tile
 constexpr int kFlagHalo = 2;  // ... or somewhere within the halo of the largest kernel
 
+__host__ __device__ constexpr int dil_r(int k) { return 2 + 3 * k; }  // (5 + 6k - 1) / 2
+__host__ __device__ constexpr int hrows(int k) { return kDT + 2 * dil_r(k); }
+__host__ __device__ constexpr int hbase(int k) { return k == 0 ? 0 : hbase(k - 1) + hrows(k - 1); }
+__host__ __device__ constexpr int qbits(int w) {
+  int q = 0;
+  while (q < 30 && ((unsigned long long)(w * w + w) << (q + 1)) < (1ull << 32)) ++q;
+  return q;
+}
+
 template <int K>
 struct DilGeom {
-  static constexpr int h = 2 + 3 * (K - 1);  // radius of the widest kernel
-  static constexpr int S = kDT + 2 * h;      // staged side
+  static constexpr int h = dil_r(K - 1);  // radius of the widest kernel
+  static constexpr int S = kDT + 2 * h;   // staged side
+  static constexpr int SP = S | 1;        // staged row stride (odd)
+  static constexpr int HR = hbase(K);     // rows of H over all kernels
+  static constexpr int Q = qbits(2 * h + 1);
 };
 
-// H[k][rr][c] = sum_{|dc| <= r_k} src(k, rr, c + h + dc) for the rows the vertical pass reads.
+template <int K>
+__device__ __forceinline__ uint32_t to_fixed(float v) {
+  return __float2uint_rn(v * (float)(1u << DilGeom<K>::Q));
+}
+
+// One horizontal running-window item of kernel k: outputs c0..c0+kSeg-1 of staged row
+// rr = h - r + li, H[k][li][c] = sum_{|dc| <= r_k} src(k, rr, c + h + dc).
 template <int K, int k, class Src>
-__device__ __forceinline__ void hsums_k(const Src& src, float* H) {
-  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h, r = 2 + 3 * k;
-  constexpr int rows = kDT + 2 * r, items = rows * kNSeg;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int seg = it % kNSeg, rr = h - r + it / kNSeg;
-    const int c0 = seg * kSeg;
-    float sacc = 0.0f;
+__device__ __forceinline__ void hsum_one(const Src& src, uint32_t* H, int it) {
+  constexpr int h = DilGeom<K>::h, r = dil_r(k), rows = hrows(k);
+  const int li = it % rows, seg = it / rows, rr = h - r + li;
+  const int c0 = seg * kSeg;
+  uint32_t acc = 0u;
 #pragma unroll
-    for (int dc = -r; dc <= r; ++dc) sacc += src(k, rr, c0 + h + dc);
-    float* out = H + (k * S + rr) * kDT + c0;
-    out[0] = sacc;
+  for (int dc = -r; dc <= r; ++dc) acc += src(k, rr, c0 + h + dc);
+  uint32_t* out = H + (hbase(k) + li) * kHP + c0;
+  out[0] = acc;
 #pragma unroll
-    for (int c = 1; c < kSeg; ++c) {
-      sacc += src(k, rr, c0 + c + h + r) - src(k, rr, c0 + c + h - r - 1);
-      out[c] = sacc;
-    }
+  for (int c = 1; c < kSeg; ++c) {
+    acc += src(k, rr, c0 + c + h + r) - src(k, rr, c0 + c + h - r - 1);
+    out[c] = acc;
   }
 }
 
-// Bk[k][rr][c] = sum_{|dr| <= r_k} H[k][rr + h + dr][c]: the box sum at output pixel (rr, c).
+// One vertical running-window item of kernel k: rows r0..r0+kSeg-1 of output column c,
+// Bk[k][o][c] = sum_{|dr| <= r_k} H[k][o + r_k + dr][c].
 template <int K, int k>
-__device__ __forceinline__ void vsums_k(const float* H, float* Bk) {
-  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h, r = 2 + 3 * k;
-  for (int it = threadIdx.x; it < kDT * kNSeg; it += blockDim.x) {
-    const int c = it % kDT, r0 = (it / kDT) * kSeg;
-    const float* col = H + k * S * kDT + c;
-    float sacc = 0.0f;
+__device__ __forceinline__ void vsum_one(const uint32_t* H, uint32_t* Bk, int it) {
+  constexpr int r = dil_r(k);
+  const int c = it % kDT, r0 = (it / kDT) * kSeg;
+  const uint32_t* col = H + hbase(k) * kHP + c;
+  uint32_t acc = 0u;
 #pragma unroll
-    for (int dr = -r; dr <= r; ++dr) sacc += col[(r0 + h + dr) * kDT];
-    float* out = Bk + k * kDT * kDT + c;
-    out[r0 * kDT] = sacc;
+  for (int j = 0; j <= 2 * r; ++j) acc += col[(r0 + j) * kHP];
+  uint32_t* out = Bk + k * kDT * kDT + c;
+  out[r0 * kDT] = acc;
 #pragma unroll
-    for (int i = 1; i < kSeg; ++i) {
-      sacc += col[(r0 + i + h + r) * kDT] - col[(r0 + i + h - r - 1) * kDT];
-      out[(r0 + i) * kDT] = sacc;
-    }
+  for (int i = 1; i < kSeg; ++i) {
+    acc += col[(r0 + i + 2 * r) * kHP] - col[(r0 + i - 1) * kHP];
+    out[(r0 + i) * kDT] = acc;
+  }
+}
+
+// Item `it` of the flattened list of all kernels' horizontal items: every thread of the block
+// gets work, whatever the kernel sizes.
+template <int K, int k = 0, class Src>
+__device__ __forceinline__ void hsum_item(const Src& src, uint32_t* H, int it) {
+  if constexpr (k < K) {
+    constexpr int items_k = hrows(k) * kNSeg;
+    if (it < items_k) hsum_one<K, k>(src, H, it);
+    else hsum_item<K, k + 1>(src, H, it - items_k);
+  }
+}
+
+template <int K, int k = 0>
+__device__ __forceinline__ void vsum_item(const uint32_t* H, uint32_t* Bk, int it) {
+  if constexpr (k < K) {
+    if (it < kDT * kNSeg) vsum_one<K, k>(H, Bk, it);
+    else vsum_item<K, k + 1>(H, Bk, it - kDT * kNSeg);
   }
 }
 
 struct OccSrc {  // occupancy O of the staged region, the same for every kernel
-  const float* sO;
-  int S;
-  __device__ float operator()(int, int rr, int cc) const { return sO[rr * S + cc]; }
+  const uint32_t* sO;
+  int SP;
+  __device__ uint32_t operator()(int, int rr, int cc) const { return sO[rr * SP + cc]; }
 };
 
 struct GSrc {  // G_k = M_C (1 - O) where B_k < 1, else 0
-  const float* sM;
+  const uint32_t* sM;
   const uint8_t* sMask;
-  int S;
-  __device__ float operator()(int k, int rr, int cc) const {
-    const int i = rr * S + cc;
-    return ((sMask[i] >> k) & 1u) ? sM[i] : 0.0f;
+  int SP;
+  __device__ uint32_t operator()(int k, int rr, int cc) const {
+    const int i = rr * SP + cc;
+    return ((sMask[i] >> k) & 1u) ? sM[i] : 0u;
   }
 };
 
-template <int K, int k = 0>
-__device__ __forceinline__ void hsums_all(const OccSrc& o, const GSrc& g, bool occ, float* H) {
-  if constexpr (k < K) {
-    if (occ) hsums_k<K, k>(o, H);
-    else hsums_k<K, k>(g, H);
-    hsums_all<K, k + 1>(o, g, occ, H);
-  }
+template <int K, class Src>
+__device__ __forceinline__ void hsums_all(const Src& src, uint32_t* H) {
+  for (int it = threadIdx.x; it < DilGeom<K>::HR * kNSeg; it += blockDim.x) hsum_item<K>(src, H, it);
 }
 
-template <int K, int k = 0>
-__device__ __forceinline__ void vsums_all(const float* H, float* Bk) {
-  if constexpr (k < K) {
-    vsums_k<K, k>(H, Bk);
-    vsums_all<K, k + 1>(H, Bk);
-  }
+template <int K>
+__device__ __forceinline__ void vsums_all(const uint32_t* H, uint32_t* Bk) {
+  for (int it = threadIdx.x; it < K * kDT * kNSeg; it += blockDim.x) vsum_item<K>(H, Bk, it);
 }
 
 __device__ __forceinline__ int dil_flags(const Dev& d, int dt) {
@@ -122,13 +155,15 @@ __device__ __forceinline__ int dil_flags(const Dev& d, int dt) {
 
 template <int K>
 __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
-  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h;
-  extern __shared__ float sm[];
+  pdl_enter();
+  constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
+  constexpr float inv_q = 1.0f / (float)(1u << Q);
+  extern __shared__ uint32_t sm[];
   __shared__ float s_red[kDThreads / 32];
   if (*d.status & kStatusOverflow) return;
-  float* sO = sm;
-  float* H = sO + S * S;
-  float* Bk = H + K * S * kDT;
+  uint32_t* sO = sm;
+  uint32_t* H = sO + S * SP;
+  uint32_t* Bk = H + DilGeom<K>::HR * kHP;
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
@@ -150,10 +185,11 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
-      sO[idx] = (X >= 0 && Y >= 0 && X < res && Y < res) ? 1.0f - d.img_I[pb + (long long)Y * res + X] : 0.0f;
+      sO[(idx / S) * SP + idx % S] =
+          (X >= 0 && Y >= 0 && X < res && Y < res) ? to_fixed<K>(1.0f - d.img_I[pb + (long long)Y * res + X]) : 0u;
     }
     __syncthreads();
-    hsums_all<K>(OccSrc{sO, S}, GSrc{nullptr, nullptr, S}, true, H);
+    hsums_all<K>(OccSrc{sO, SP}, H);
     __syncthreads();
     vsums_all<K>(H, Bk);
     __syncthreads();
@@ -164,18 +200,18 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
       const int X = x0 + c, Y = y0 + rr;
       if (X >= res || Y >= res) continue;
       const long long pix = pb + (long long)Y * res + X;
-      const float O = sO[(rr + h) * S + c + h];
+      const float O = 1.0f - d.img_I[pix];
       const float M = d.covc[pix];
       const float mval = M * (1.0f - O);
       float gdir = 0.0f;
       unsigned mask = 0u;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float B = Bk[k * kDT * kDT + local];
-        const float D = fminf(1.0f, B);
+        const uint32_t Bq = Bk[k * kDT * kDT + local];
+        const float D = fminf(1.0f, (float)Bq * inv_q);
         const float w = d.L.dil_w[k];
         lu += w * mval * (1.0f - D);
-        if (B < 1.0f) mask |= 1u << k;
+        if (Bq < (1u << Q)) mask |= 1u << k;  // B_k < 1, decided on the exact fixed-point sum
         gdir -= w * (1.0f - D);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
       }
       d.dil_m[pix] = mval;
@@ -196,12 +232,14 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
 
 template <int K>
 __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
-  constexpr int S = DilGeom<K>::S, h = DilGeom<K>::h;
-  extern __shared__ float sm[];
+  pdl_enter();
+  constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
+  constexpr float inv_q = 1.0f / (float)(1u << Q);
+  extern __shared__ uint32_t sm[];
   if (*d.status & kStatusOverflow) return;
-  float* sM = sm;
-  float* H = sM + S * S;
-  float* Bk = H + K * S * kDT;
+  uint32_t* sM = sm;
+  uint32_t* H = sM + S * SP;
+  uint32_t* Bk = H + DilGeom<K>::HR * kHP;
   uint8_t* sMask = reinterpret_cast<uint8_t*>(Bk + K * kDT * kDT);
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     if (!(dil_flags(d, dt) & kFlagHalo)) continue;  // G = 0 over the tile and its halo
@@ -214,11 +252,12 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
       const bool in = X >= 0 && Y >= 0 && X < res && Y < res;
       const long long pix = pb + (long long)Y * res + X;
-      sM[idx] = in ? d.dil_m[pix] : 0.0f;
-      sMask[idx] = in ? d.dil_mask[pix] : (uint8_t)0;
+      const int si = (idx / S) * SP + idx % S;
+      sM[si] = in ? to_fixed<K>(d.dil_m[pix]) : 0u;
+      sMask[si] = in ? d.dil_mask[pix] : (uint8_t)0;
     }
     __syncthreads();
-    hsums_all<K>(OccSrc{nullptr, S}, GSrc{sM, sMask, S}, false, H);
+    hsums_all<K>(GSrc{sM, sMask, SP}, H);
     __syncthreads();
     vsums_all<K>(H, Bk);
     __syncthreads();
@@ -229,7 +268,7 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
       if (X >= res || Y >= res) continue;
       float acc = 0.0f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * Bk[k * kDT * kDT + local];
+      for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * ((float)Bk[k * kDT * kDT + local] * inv_q);
       d.gOu[pb + (long long)Y * res + X] += acc;
     }
   }
@@ -274,6 +313,7 @@ __device__ __forceinline__ float warp_sum_f(float x) {
   return x;
 }
 __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
+  pdl_enter();
   __shared__ float s_red[4][kLossThreads / 32];
   const int p = blockIdx.x;
   const int t0 = d.prob_tile_base[p], t1 = d.prob_tile_base[p + 1];
@@ -328,6 +368,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
 // Deterministic mode: each element sums its (tile, element) partials over its tile rectangle in
 // row-major order (a tile's list is ordered by element id, so the pair is found by bisection).
 __global__ void k_grad_reduce(Dev d) {
+  pdl_enter();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
   const int4 rc = d.rect[g];
@@ -364,10 +405,10 @@ __global__ void k_adam_flush(Dev d) {
 }
 
 static size_t dilate_smem(int K, bool backward) {
-  const int h = dil_radius(K - 1), S = kDT + 2 * h;
-  size_t f = (size_t)S * S + (size_t)K * S * kDT + (size_t)K * kDT * kDT;
-  if (backward) f += ((size_t)S * S + 3) / 4;  // mask bytes
-  return f * sizeof(float);
+  const int S = kDT + 2 * dil_r(K - 1), SP = S | 1;
+  size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP + (size_t)K * kDT * kDT;
+  if (backward) f += ((size_t)S * SP + 3) / 4;  // mask bytes
+  return f * sizeof(uint32_t);
 }
 
 template <int K>
@@ -400,41 +441,38 @@ cudaError_t prepare_dilate(int n_dil) {
 }
 
 template <int K>
-static void launch_k(const Dev& d, cudaStream_t s, bool backward) {
+static cudaError_t launch_k(const Dev& d, cudaStream_t s, bool backward) {
   const size_t sm = dilate_smem(K, backward);
-  if (backward) k_dilate_bwd<K><<<d.total_dtiles, kDThreads, sm, s>>>(d);
-  else k_dilate_fwd<K><<<d.total_dtiles, kDThreads, sm, s>>>(d);
+  if (backward) return klaunch(d.pdl, k_dilate_bwd<K>, d.total_dtiles, kDThreads, sm, s, d);
+  return klaunch(d.pdl, k_dilate_fwd<K>, d.total_dtiles, kDThreads, sm, s, d);
 }
 
 cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward) {
   switch (d.L.n_dil) {
-    case 1: launch_k<1>(d, s, backward); break;
-    case 2: launch_k<2>(d, s, backward); break;
-    case 3: launch_k<3>(d, s, backward); break;
-    case 4: launch_k<4>(d, s, backward); break;
-    case 5: launch_k<5>(d, s, backward); break;
-    case 6: launch_k<6>(d, s, backward); break;
-    case 7: launch_k<7>(d, s, backward); break;
-    case 8: launch_k<8>(d, s, backward); break;
+    case 1: return launch_k<1>(d, s, backward);
+    case 2: return launch_k<2>(d, s, backward);
+    case 3: return launch_k<3>(d, s, backward);
+    case 4: return launch_k<4>(d, s, backward);
+    case 5: return launch_k<5>(d, s, backward);
+    case 6: return launch_k<6>(d, s, backward);
+    case 7: return launch_k<7>(d, s, backward);
+    case 8: return launch_k<8>(d, s, backward);
     default: return cudaSuccess;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s) {
   if (d.L.n_dil <= 0 || !d.dtile_flags) return cudaSuccess;
-  k_dtile_flags<<<d.total_dtiles, 256, 0, s>>>(d, dil_radius(d.L.n_dil - 1));
+  k_dtile_flags<<<d.total_dtiles, 256, 0, s>>>(d, dil_r(d.L.n_dil - 1));
   return cudaGetLastError();
 }
 
 cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step) {
-  k_loss<<<d.n_probs, kLossThreads, 0, s>>>(d, count_step ? 1 : 0);
-  return cudaGetLastError();
+  return klaunch(d.pdl, k_loss, d.n_probs, kLossThreads, 0, s, d, count_step ? 1 : 0);
 }
 
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s) {
-  k_grad_reduce<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d);
-  return cudaGetLastError();
+  return klaunch(d.pdl, k_grad_reduce, (d.n_elems + 255) / 256, 256, 0, s, d);
 }
 
 cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s) {

@@ -71,8 +71,8 @@ __device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, floa
 }
 
 constexpr int kSegCap = 1024;   // container segments staged per chunk
-constexpr int kNearCap = 256;   // near segments staged per chunk of one (tile, element) pair
-constexpr int kListCap = 512;   // tile list entries ordered in shared memory
+constexpr int kNearCap = 64;    // near segments staged per chunk of one (tile, element) pair
+constexpr int kPairWarps = 4;   // pairs per block of the per-pair adjoint (one per warp)
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
 
 __device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& p, int& tx, int& ty,
@@ -85,7 +85,8 @@ __device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& 
 }
 
 // ------------------------------------------------------------------------------------------------
-// Signed distances of one (tile, element) pair per block.
+// Signed distances of one near (tile, element) pair per block (the emission lists the near pairs;
+// the others have saturated coverage on the whole tile and need no per-pixel work).
 //
 // The block first splits the outline's segments.  A segment whose box meets the tile's pixel-centre
 // box grown by the coverage margin m = rho + pad (+ stroke half-width) is "near": warp 0 appends
@@ -98,18 +99,26 @@ __device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& 
 // ------------------------------------------------------------------------------------------------
 template <int T, int NT>
 __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d) {
+  pdl_enter();
   constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
   static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
   __shared__ float4 s_seg[kNearCap];
   __shared__ float2 s_seg2[kNearCap];
   __shared__ int s_idx[kNearCap];
+  __shared__ float2 s_xt[kNearCap * T];  // per (near segment, row): crossing x and direction
   __shared__ int s_back[T];
   __shared__ int s_near;
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int total = *d.total_pairs;
-  for (int slot = blockIdx.x; slot < total; slot += gridDim.x) {
+  const int n_near = d.work[2];
+  // the near pairs: a block's first is its block index in the list, the others are taken from a
+  // shared counter as blocks finish (pair costs vary by two orders of magnitude); s_next is
+  // double-buffered so that thread 0's next write never meets a read of the previous value
+  __shared__ int s_next[2];
+  for (int i = blockIdx.x, it = 0; i < n_near; ++it) {
+    if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
+    const int slot = d.near_list[i];
     const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
@@ -173,10 +182,15 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
         // winding backdrop of the far segments right of the tile
         for (int r = threadIdx.x - 32; r < T; r += NT - 32) s_back[r] = 0;
         asm volatile("bar.sync 1, %0;" ::"r"(NT - 32));
+        // the rows' dy as the pixels form them: non-decreasing in the row, so a segment whose y
+        // range misses [first row, last row] crosses no row's ray
+        const float yr0 = ((float)(ty * T) + 0.5f - tp.y) - tp.w;
+        const float yr1 = ((float)(ty * T + T - 1) + 0.5f - tp.y) - tp.w;
         for (int j = threadIdx.x - 32; j < ns; j += NT - 32) {
           const float4 sa = d.segA[v0 + j];
           const float2 sb = d.segB[v0 + j];
           if (fminf(sa.x, sa.x + sa.z) <= gx1) continue;  // near, left or overlapping in x
+          if (fmaxf(sa.y, sb.x) <= yr0 || fminf(sa.y, sb.x) > yr1) continue;
           const int up = sa.y < sb.x ? 1 : -1;
           for (int r = 0; r < T; ++r) {
             const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;  // as a pixel forms dy
@@ -187,15 +201,35 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
       __syncthreads();
       const int total_near = s_near;
       const int cn = min(kNearCap, total_near - base);
+      if (closed && cn > 0) {
+        // crossings of the pixel rows with the near segments.  Row r crosses segment j when its
+        // end points lie on different sides of the row (the half-open test, on the same dy the
+        // pixels form); the crossing counts for a pixel left of the crossing x, +1 upward and -1
+        // downward.  (This is the sign of cross(e, p - a) read as a comparison of x: the two can
+        // differ only for a pixel within rounding of the segment, where sd ~ 0 and c ~ 1/2 on
+        // either side.)
+        for (int e = threadIdx.x; e < cn * T; e += NT) {
+          const int j = e / T, r = e % T;
+          const float4 sa = s_seg[j];
+          const float bxy = s_seg2[j].x;
+          const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
+          const bool a_le = yr - sa.y >= 0.0f, b_le = yr - bxy >= 0.0f;
+          float2 xt = make_float2(-FLT_MAX, __int_as_float(0));
+          if (a_le != b_le) xt = make_float2(sa.x + sa.z * ((yr - sa.y) / sa.w), __int_as_float(a_le ? 1 : -1));
+          s_xt[e] = xt;
+        }
+        __syncthreads();
+      }
       if (any && cn > 0) {
+#pragma unroll 2
         for (int j = 0; j < cn; ++j) {
           const float4 s = s_seg[j];
-          const float2 s2 = s_seg2[j];
+          const float ie = s_seg2[j].y;
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
             if (!act[k]) continue;
             const float wx = dx[k] - s.x, wy = dy[k] - s.y;
-            const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
+            const float t = __saturatef((wx * s.z + wy * s.w) * ie);
             const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
             const float d2 = fmaf(qx, qx, qy * qy);
             if (d2 < best[k]) {
@@ -203,10 +237,8 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
               bj[k] = j;
             }
             if (closed) {
-              const bool a_le = wy >= 0.0f, b_le = dy[k] - s2.x >= 0.0f;
-              const float cr = s.z * wy - s.w * wx;
-              if (a_le && !b_le && cr > 0.0f) wn[k] += 1;
-              if (!a_le && b_le && cr < 0.0f) wn[k] -= 1;
+              const float2 xt = s_xt[j * T + (threadIdx.x + k * NT) / T];
+              if (dx[k] < xt.x) wn[k] += __float_as_int(xt.y);
             }
           }
         }
@@ -237,142 +269,141 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
       sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(idx[k]));
     }
     live = __syncthreads_or(live);
-    if (threadIdx.x == 0) d.pair_live[slot] = live ? 1 : 0;
+    if (threadIdx.x == 0) {
+      if (live) d.live_list[atomicAdd(&d.work[1], 1)] = slot;
+      else if (d.deterministic) d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    i = s_next[it & 1];
   }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Composite per tile: order the tile's pairs by element id (ids are unique in a tile, so an id's
-// rank is the number of smaller ids), then per pixel Ihat = prod(1 - c_i) and prod(1 - tau c_i^pad)
-// over the pairs in that order, and the per-pixel loss terms (Eq. 5, Eq. 6 surrogate, force).
+// Composite, one tile per warp: order the tile's pairs by element id (ids are unique in a tile, so
+// an id's rank is the number of smaller ids; for up to 32 pairs the lanes hold the ids and rank
+// them by shuffles), then per pixel Ihat = prod(1 - c_i) and prod(1 - tau c_i^pad) over the pairs
+// in that order, and the per-pixel loss terms (Eq. 5, Eq. 6 surrogate, force), summed over the
+// tile by a fixed shuffle tree.  No block-wide barrier: each warp owns its tile.
 // ------------------------------------------------------------------------------------------------
-template <int T, int NT>
-__global__ void __launch_bounds__(NT) k_composite(Dev d, float* out_bw, float* out_tau) {
-  constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
-  constexpr int PER = (kListCap + NT - 1) / NT;
-  __shared__ int s_list[kListCap];
-  __shared__ int s_slot[kListCap];
-  __shared__ float s_red[3][NW];
+constexpr int kCompWarps = 4;
+template <int T>
+__global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out_bw, float* out_tau) {
+  pdl_enter();
+  constexpr int NP = T * T, PPL = NP / 32;
+  __shared__ int s_slot[kCompWarps][32];
+  __shared__ uint8_t s_cls[kCompWarps][32];
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
-  for (int tile = blockIdx.x; tile < d.total_tiles; tile += gridDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int* w_slot = s_slot[wid];
+  uint8_t* w_cls = s_cls[wid];
+  for (int tile = blockIdx.x * kCompWarps + wid; tile < d.total_tiles; tile += gridDim.x * kCompWarps) {
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
     const long long pixbase = d.prob_pix_base[p];
     const uint2 rg = d.range[tile];
     const int m = (int)(rg.y - rg.x);
-    const bool small = m <= kListCap;
-    __syncthreads();  // the previous tile's readers of the lists are done
-    if (m > 0) {
-      if (small) {
-        int v[PER], r[PER];
-        for (int i = threadIdx.x; i < m; i += NT) s_list[i] = d.pair_elem[rg.x + i];
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-          const int i = threadIdx.x + k * NT;
-          r[k] = 0;
-          v[k] = 0;
-          if (i < m) {
-            v[k] = s_list[i];
-            for (int j = 0; j < m; ++j) r[k] += s_list[j] < v[k] ? 1 : 0;
-          }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-          const int i = threadIdx.x + k * NT;
-          if (i < m) {
-            s_list[r[k]] = v[k];
-            s_slot[r[k]] = (int)rg.x + i;
-            d.pair_sorted[rg.x + r[k]] = v[k];
-            d.pair_slot[rg.x + r[k]] = (int)rg.x + i;
-          }
-        }
-      } else {
-        for (int i = threadIdx.x; i < m; i += NT) {
-          const int vi = d.pair_elem[rg.x + i];
-          int r = 0;
-          for (int j = 0; j < m; ++j) r += d.pair_elem[rg.x + j] < vi ? 1 : 0;
-          d.pair_sorted[rg.x + r] = vi;
-          d.pair_slot[rg.x + r] = (int)rg.x + i;
-        }
+    const bool small = m <= 32;
+    __syncwarp();  // the previous tile's readers of this warp's lists are done
+    if (small) {
+      const int v = lane < m ? d.pair_elem[rg.x + lane] : 0;
+      int r = 0;
+      for (int j = 0; j < m; ++j) r += __shfl_sync(0xffffffffu, v, j) < v ? 1 : 0;
+      if (lane < m) {
+        w_slot[r] = (int)rg.x + lane;
+        w_cls[r] = d.pair_cls[rg.x + lane];
+        d.pair_sorted[rg.x + r] = v;
+        d.pair_slot[rg.x + r] = (int)rg.x + lane;
       }
-      __syncthreads();
+    } else {
+      for (int i = lane; i < m; i += 32) {
+        const int vi = d.pair_elem[rg.x + i];
+        int r = 0;
+        for (int j = 0; j < m; ++j) r += d.pair_elem[rg.x + j] < vi ? 1 : 0;
+        d.pair_sorted[rg.x + r] = vi;
+        d.pair_slot[rg.x + r] = (int)rg.x + i;
+      }
+    }
+    __syncwarp();  // the ordered list is visible to the whole warp
+    // products over the pairs in element order; the pair loop is outermost so that a lane's loads
+    // of its PPL pixels are independent and in flight together
+    float keep[PPL], keept[PPL];
+    int zc[PPL], nfull[PPL];
+    bool partial[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      keep[k] = 1.0f;
+      keept[k] = 1.0f;
+      zc[k] = 0;
+      nfull[k] = 0;
+      partial[k] = false;
+    }
+    for (int i = 0; i < m; ++i) {
+      const int slot = small ? w_slot[i] : d.pair_slot[rg.x + i];
+      const uint8_t cls = small ? w_cls[i] : d.pair_cls[slot];
+      if (cls == kPairOut) continue;  // c = c^pad = 0: factors of 1
+      float sd[PPL];
+#pragma unroll
+      for (int k = 0; k < PPL; ++k)  // an inside pair has c = c^pad = 1: sd = +1e30 gives that
+        sd[k] = cls == kPairIn ? kFar : d.saved[(size_t)slot * NP + lane + 32 * k].x;
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        const float x = sd[k] * inv_rho;
+        const float omc = Sfun(-x), cp = Sfun((sd[k] + pad) * inv_rho);
+        if (omc == 0.0f) zc[k] += 1;
+        else keep[k] *= omc;
+        keept[k] *= 1.0f - tau * cp;
+        nfull[k] += cp == 1.0f;
+        partial[k] |= cp > 0.0f && cp < 1.0f;
+      }
     }
     float lc = 0.0f, lo = 0.0f, ld = 0.0f;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int local = threadIdx.x + k * NT;
+    for (int k = 0; k < PPL; ++k) {
+      const int local = lane + 32 * k;
       const int X = tx * T + local % T, Y = ty * T + local / T;
       if (X >= res || Y >= res) continue;
-      float keep = 1.0f, keept = 1.0f;
-      int zc = 0;
-      for (int i = 0; i < m; ++i) {
-        const int slot = small ? s_slot[i] : d.pair_slot[rg.x + i];
-        const float sd = d.saved[(size_t)slot * NP + local].x;
-        const float x = sd * inv_rho;
-        const float omc = Sfun(-x), cp = Sfun((sd + pad) * inv_rho);
-        if (omc == 0.0f) zc += 1;
-        else keep *= omc;
-        keept *= 1.0f - tau * cp;
-      }
       const long long pix = pixbase + (long long)Y * res + X;
-      const float ihat = zc ? 0.0f : keep;
+      const float ihat = zc[k] ? 0.0f : keep[k];
       const float cov = d.covc[pix];
       const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
       const float df = ihat - (1.0f - cov);
       lc += W * df * df;
-      const float A = 1.0f - keept;
-      lo += A > tau ? A - tau : 0.0f;
+      const float A = 1.0f - keept[k];
+      // the kink of max(0, A - tau): one fully covering element gives A = tau exactly and any
+      // other element with c^pad > 0 lifts A above it, by less than float can resolve when that
+      // c^pad is tiny; so the side of the kink is taken from the counts in that case (exact)
+      const bool over = nfull[k] >= 2 || (nfull[k] == 1 ? partial[k] : A > tau);
+      lo += over ? fmaxf(A - tau, 0.0f) : 0.0f;
       ld += (1.0f - ihat) * (1.0f - ((float)Y + 0.5f) / (float)res);
       d.img_I[pix] = ihat;
-      d.img_Pt[pix] = keept;
+      d.img_Pt[pix] = over ? -keept[k] : keept[k];  // the sign carries the side of the kink
       if (out_bw) out_bw[pix] = ihat;
       if (out_tau) out_tau[pix] = A;
     }
-    // fixed-order block sums of the three partials
-    for (int o = 16; o; o >>= 1) {
+    for (int o = 16; o; o >>= 1) {  // fixed-order sums of the three partials
       lc += __shfl_xor_sync(0xffffffffu, lc, o);
       lo += __shfl_xor_sync(0xffffffffu, lo, o);
       ld += __shfl_xor_sync(0xffffffffu, ld, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-      s_red[0][threadIdx.x >> 5] = lc;
-      s_red[1][threadIdx.x >> 5] = lo;
-      s_red[2][threadIdx.x >> 5] = ld;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int i = 0; i < NW; ++i) {
-        r.x += s_red[0][i];
-        r.y += s_red[1][i];
-        r.z += s_red[2][i];
-      }
-      d.lossA[tile] = r;
-    }
+    if (lane == 0) d.lossA[tile] = make_float4(lc, lo, ld, 0.0f);
   }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Adjoint, one (tile, element) pair per block: dL/dIhat and dL/dA_tau per pixel, then the chain
+// Adjoint, one (tile, element) pair per warp: dL/dIhat and dL/dA_tau per pixel, then the chain
 // dL/dc -> dc/dsd -> dsd/d(closest segment) -> d/d(tx, ty, theta, s) of Eq. 2, reduced over the
-// tile's pixels in a fixed order and added to the element's gradient (or stored per pair).
+// tile's pixels by a fixed shuffle tree and added to the element's gradient (or stored per pair).
 // ------------------------------------------------------------------------------------------------
-template <int T, int NT>
-__global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
-  constexpr int NP = T * T, PPT = NP / NT;
-  __shared__ float s_red[4][NT / 32];
+template <int T>
+__global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d) {
+  pdl_enter();
+  constexpr int NP = T * T, PPL = NP / 32;
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int total = *d.total_pairs;
-  for (int slot = blockIdx.x; slot < total; slot += gridDim.x) {
-    if (!d.pair_live[slot]) {
-      if (d.deterministic && threadIdx.x == 0) d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
+  const int n_live = d.work[1];  // pairs without a gradient-carrying pixel are not listed
+  for (int i = blockIdx.x * kPairWarps + wid; i < n_live; i += gridDim.x * kPairWarps) {
+    const int slot = d.live_list[i];
     const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
@@ -385,8 +416,8 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
     const float2* sv = d.saved + (size_t)slot * NP;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int local = threadIdx.x + k * NT;
+    for (int k = 0; k < PPL; ++k) {
+      const int local = lane + 32 * k;
       const int X = tx * T + local % T, Y = ty * T + local / T;
       if (X >= res || Y >= res) continue;
       const float2 rec = sv[local];
@@ -394,14 +425,15 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
       const float x = sd * inv_rho, xp = (sd + pad) * inv_rho;
       if (!(fabsf(x) < 1.0f || fabsf(xp) < 1.0f)) continue;
       const long long pix = pixbase + (long long)Y * res + X;
-      const float ihat = d.img_I[pix], pt = d.img_Pt[pix], cov = d.covc[pix];
+      const float ihat = d.img_I[pix], pt_s = d.img_Pt[pix], cov = d.covc[pix];
+      const float pt = fabsf(pt_s);  // negative: the pixel is on the rising side of the Eq. 6 kink
       const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
       const float gou = d.L.gamma != 0.0f ? d.gOu[pix] : 0.0f;
       const float py = (float)Y + 0.5f;
       // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
       const float gI = d.L.alpha * inv_np * 2.0f * W * (ihat - (1.0f - cov)) - d.L.gamma * gou -
                        d.L.delta * inv_np * (1.0f - py / (float)res);
-      const float gA = (1.0f - pt) > tau ? d.L.beta * inv_np : 0.0f;
+      const float gA = pt_s < 0.0f ? d.L.beta * inv_np : 0.0f;
       const float omc = Sfun(-x), cp = Sfun(xp);
       // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)
       const float gc = omc > 0.0f ? -gI * ihat / omc : 0.0f;
@@ -440,7 +472,6 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
       a2 += gs * (ny * qx - nx * qy);          // d(dist)/dtheta = -n . J q
       a3 += gs * (nx * qx + ny * qy) * s_inv;  // d(dist)/ds = -n . q / s
     }
-    // fixed-order block reduction of the four sums
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
@@ -448,29 +479,14 @@ __global__ void __launch_bounds__(NT) k_raster_bwd(Dev d) {
       a2 += __shfl_xor_sync(0xffffffffu, a2, o);
       a3 += __shfl_xor_sync(0xffffffffu, a3, o);
     }
-    __syncthreads();  // the previous pair's reader of s_red is done
     if (lane == 0) {
-      s_red[0][wid] = a0;
-      s_red[1][wid] = a1;
-      s_red[2][wid] = a2;
-      s_red[3][wid] = a3;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int i = 0; i < NT / 32; ++i) {
-        r.x += s_red[0][i];
-        r.y += s_red[1][i];
-        r.z += s_red[2][i];
-        r.w += s_red[3][i];
-      }
       if (d.deterministic) {
-        d.partial[slot] = r;
+        d.partial[slot] = make_float4(a0, a1, a2, a3);
       } else {
-        atomicAdd(&d.dq[g].x, r.x);
-        atomicAdd(&d.dq[g].y, r.y);
-        atomicAdd(&d.dq[g].z, r.z);
-        atomicAdd(&d.dq[g].w, r.w);
+        atomicAdd(&d.dq[g].x, a0);
+        atomicAdd(&d.dq[g].y, a1);
+        atomicAdd(&d.dq[g].z, a2);
+        atomicAdd(&d.dq[g].w, a3);
       }
     }
   }
@@ -550,18 +566,16 @@ template <>
 struct TileCfg<16> {
   static constexpr int NT = 256;
 };
-template <>
-struct TileCfg<32> {
-  static constexpr int NT = 512;
-};
 
 template <int T>
 static cudaError_t fwd_t(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid, float* bw,
                          float* tau, int part) {
   constexpr int NT = TileCfg<T>::NT;
-  if (part & 1) k_pair_sd<T, NT><<<pair_grid, NT, 0, s>>>(d);
-  if (part & 2) k_composite<T, NT><<<tile_grid, NT, 0, s>>>(d, bw, tau);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (part & 1) e = klaunch(d.pdl, k_pair_sd<T, NT>, pair_grid, NT, 0, s, d);
+  if (e == cudaSuccess && (part & 2))
+    e = klaunch(d.pdl, k_composite<T>, tile_grid, kCompWarps * 32, 0, s, d, bw, tau);
+  return e;
 }
 
 cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid,
@@ -569,48 +583,44 @@ cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int t
   switch (d.tile) {
     case 8: return fwd_t<8>(d, s, pair_grid, tile_grid, out_bw, out_tau, part);
     case 16: return fwd_t<16>(d, s, pair_grid, tile_grid, out_bw, out_tau, part);
-    case 32: return fwd_t<32>(d, s, pair_grid, tile_grid, out_bw, out_tau, part);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid) {
   switch (d.tile) {
-    case 8: k_raster_bwd<8, TileCfg<8>::NT><<<pair_grid, TileCfg<8>::NT, 0, s>>>(d); break;
-    case 16: k_raster_bwd<16, TileCfg<16>::NT><<<pair_grid, TileCfg<16>::NT, 0, s>>>(d); break;
-    case 32: k_raster_bwd<32, TileCfg<32>::NT><<<pair_grid, TileCfg<32>::NT, 0, s>>>(d); break;
+    case 8: return klaunch(d.pdl, k_raster_bwd<8>, pair_grid, kPairWarps * 32, 0, s, d);
+    case 16: return klaunch(d.pdl, k_raster_bwd<16>, pair_grid, kPairWarps * 32, 0, s, d);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_container(const Dev& d, cudaStream_t s) {
   switch (d.tile) {
     case 8: k_container<8, TileCfg<8>::NT><<<d.total_tiles, TileCfg<8>::NT, 0, s>>>(d); break;
     case 16: k_container<16, TileCfg<16>::NT><<<d.total_tiles, TileCfg<16>::NT, 0, s>>>(d); break;
-    case 32: k_container<32, TileCfg<32>::NT><<<d.total_tiles, TileCfg<32>::NT, 0, s>>>(d); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <int T>
-static void per_sm_t(int* pair_per_sm, int* tile_per_sm) {
+static void per_sm_t(RasterOcc* o) {
   constexpr int NT = TileCfg<T>::NT;
   int a = 1, b = 1, c = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pair_sd<T, NT>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T, NT>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_composite<T, NT>, NT, 0);
-  *pair_per_sm = a < b ? (a > 0 ? a : 1) : (b > 0 ? b : 1);
-  *tile_per_sm = c > 0 ? c : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T>, kPairWarps * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_composite<T>, kCompWarps * 32, 0);
+  o->fwd_per_sm = a > 0 ? a : 1;
+  o->bwd_per_sm = b > 0 ? b : 1;
+  o->tile_per_sm = c > 0 ? c : 1;
+  o->bwd_pairs_per_block = kPairWarps;
+  o->tiles_per_block = kCompWarps;
 }
 
-void raster_blocks_per_sm(int tile, int* pair_per_sm, int* tile_per_sm) {
-  switch (tile) {
-    case 8: per_sm_t<8>(pair_per_sm, tile_per_sm); break;
-    case 16: per_sm_t<16>(pair_per_sm, tile_per_sm); break;
-    default: per_sm_t<32>(pair_per_sm, tile_per_sm); break;
-  }
+void raster_occupancy(int tile, RasterOcc* o) {
+  if (tile == 16) per_sm_t<16>(o);
+  else per_sm_t<8>(o);
 }
 
 }  // namespace collage

@@ -21,7 +21,7 @@ def lib():
 def _declared():
     src = open(os.path.join(ROOT, "include", "collage.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(collage_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(collage_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -90,6 +90,7 @@ def test_invalid_problem_is_rejected_before_any_device_work(lib, mutate, needle)
 
 @pytest.mark.parametrize("over,needle", [
     (dict(tile=12), "tile must be"),
+    (dict(tile=32), "tile must be"),
     (dict(tau=1.0), "tau must be in"),
     (dict(n_levels=0), "n_levels"),
     (dict(rho_px=0.0), "rho_px"),

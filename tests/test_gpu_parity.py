@@ -43,7 +43,7 @@ def test_loss_and_gradient_match_oracle(env, name):
     col.close()
 
 
-@pytest.mark.parametrize("tile", [8, 32])
+@pytest.mark.parametrize("tile", [8])
 def test_other_tile_sizes_match_oracle(env, tile):
     prob, opts, grid = U.small_case("mixed120_pad2")
     col, terms, grad, ref, g, o = _run(env, prob, grid, opts, tile=tile)
@@ -69,7 +69,7 @@ def test_render_matches_oracle_per_pixel(env, name):
 
 
 @pytest.mark.parametrize("name,tile", [("mixed120_pad2", 16), ("open150_force", 8),
-                                       ("blobs40_ragged", 32)])
+                                       ("blobs40_ragged", 8)])
 def test_bins_are_bit_exact(env, name, tile):
     O, Collage = env
     prob, opts, grid = U.small_case(name)
@@ -132,6 +132,44 @@ def test_graph_replay_equals_eager_launches(env):
     for graphs in (0, 1):
         col = Collage(prob, level_res=[grid], deterministic=1, use_graphs=graphs, **g)
         col.step(7)
+        res.append((col.get_params().cpu().numpy().copy(), col.loss().cpu().numpy().copy()))
+        col.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_overlapped_launches_equal_serialised_launches(env, graphs):
+    O, Collage = env
+    prob, opts, grid = U.small_case("mixed120_pad2")
+    g, o = U.paired(**opts)
+    res = []
+    for pdl in (0, 1):
+        col = Collage(prob, level_res=[grid], deterministic=1, use_graphs=graphs,
+                      overlap_launches=pdl, **g)
+        col.step(5)
+        terms, grad = col.loss_backward()
+        res.append((col.get_params().cpu().numpy().copy(), terms.cpu().numpy().copy(),
+                    grad.cpu().numpy().copy()))
+        col.close()
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
+def test_async_steps_equal_synchronous_steps(env):
+    O, Collage = env
+    prob, opts, grid = U.small_case("mixed120_pad2")
+    g, o = U.paired(**opts)
+    res = []
+    for mode in ("sync", "async"):
+        col = Collage(prob, level_res=[grid], deterministic=1, **g)
+        if mode == "sync":
+            col.step(6)
+        else:
+            for _ in range(6):
+                col.step_async(1)
+            col.sync()
+        _, step, _ = col.get_state()
+        assert step == 6
         res.append((col.get_params().cpu().numpy().copy(), col.loss().cpu().numpy().copy()))
         col.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
@@ -240,4 +278,71 @@ def test_full_size_headline_level_matches_oracle(env):
     ihat, atau, _ = sc.render(q0, 1024, o)
     assert np.abs(bw.cpu().numpy().reshape(1024, 1024) - ihat).max() <= U.COV_ATOL
     assert np.abs(tau.cpu().numpy().reshape(1024, 1024) - atau).max() <= U.COV_ATOL
+    col.close()
+
+
+def _timed_form(Collage, prob, g, grid):
+    """A handle in the benchmark's launch configuration (persistent grids, CUDA graph, autotuned
+    tile) at one level of `grid`."""
+    col = Collage(prob, level_res=[grid], use_graphs=1, persistent=1, tile=0, **g)
+    col.autotune()
+    return col
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("cfg,grid,opts", [(1, 128, dict(gamma=0.0)), (2, 512, dict()),
+                                           (5, 2048, dict(pad_px=1.0, delta=1e3))])
+def test_full_size_configs_match_oracle(env, cfg, grid, opts):
+    """The 16-disk, 200-blob and 5000-element open-packing workloads at their full sizes: loss
+    terms, every gradient component (atomic and deterministic modes) and the bins."""
+    O, Collage = env
+    prob = W.config_problem(cfg)
+    g, o = U.paired(**opts)
+    sc = O.Scene(prob)
+    q0 = prob["params0"].astype(np.float64)
+    ref = sc.eval(q0, grid, o)
+    weights = (o.alpha, o.beta, o.gamma, o.delta)
+    for det in (0, 1):
+        col = _timed_form(Collage, prob, dict(g, deterministic=det), grid)
+        terms, grad = col.loss_backward()
+        U.check_terms(terms.cpu().numpy()[0], ref["terms"], grid, weights, use_u=o.gamma != 0)
+        U.check_grad(grad.cpu().numpy(), ref["grad_a"])
+        if det == 0:
+            t, e = col.bins()
+            rt, re_ = sc.bins(prob["params0"], grid, col.info()["tile"], 1.0, float(o.pad_px))
+            assert np.array_equal(t, rt) and np.array_equal(e, re_)
+        col.close()
+
+
+@pytest.mark.slow
+def test_full_batch_of_64_collages_matches_oracle(env):
+    """The 64-collage batch (uneven element counts and grids) in one batched handle: per-collage
+    loss terms and gradients for a sample of collages including the largest, bins of the whole
+    batch against the oracle's rule per collage."""
+    O, Collage = env
+    probs = [W.config_problem(4, i) for i in range(64)]
+    g, o = U.paired()
+    col = Collage(probs, level_res=[1], use_graphs=1, persistent=1, tile=0, **g)
+    tile, _ = col.autotune()
+    terms, grad = col.loss_backward()
+    terms, grad = terms.cpu().numpy(), grad.cpu().numpy()
+    t, e = col.bins()
+    sizes = [len(p["kind"]) * p["grid"] ** 2 for p in probs]
+    sample = sorted({0, 17, 40, 63, int(np.argmax(sizes)), int(np.argmin(sizes))})
+    off, tile_base = 0, 0
+    for i, p in enumerate(probs):
+        n, res = len(p["kind"]), p["grid"]
+        sc = O.Scene(p)
+        rt, re_ = sc.bins(p["params0"], res, tile, 1.0, 0.0)
+        sel = (e >= off) & (e < off + n)
+        assert np.array_equal(t[sel] - tile_base, rt) and np.array_equal(e[sel] - off, re_)
+        if i in sample:
+            ref = sc.eval(p["params0"].astype(np.float64), res, o)
+            try:
+                U.check_terms(terms[i], ref["terms"], res, (o.alpha, o.beta, o.gamma, o.delta))
+                U.check_grad(grad[off:off + n], ref["grad_a"])
+            except AssertionError as ex:
+                raise AssertionError(f"collage {i} (n={n}, grid {res}): {ex}") from None
+        off += n
+        tile_base += ((res + tile - 1) // tile) ** 2
     col.close()

@@ -48,6 +48,34 @@ def test_bin_overflow_regrows_and_runs_exactly_n_steps(Collage):
     ref.close()
 
 
+def test_async_overflow_is_latched_then_recovered(Collage):
+    from paper_2406_04008_gb300._lib import CollageError
+    prob, opts, grid = _case()
+    g, _ = U.paired(**opts)
+    kw = dict(level_res=[grid], deterministic=1, **g)
+    col = Collage(prob, **kw)
+    cap0 = col.info()["pair_capacity"]
+    q = torch.tensor(prob["params0"], device="cuda").view(-1, 4).clone()
+    q[:, 3] *= 4.0
+    col.set_params(q)
+    col.step_async(3)  # the first iteration overflows; the rest are no-ops
+    with pytest.raises(CollageError) as ei:
+        col.sync()
+    assert ei.value.status == -4
+    assert col.info()["pair_capacity"] > cap0
+    _, step, _ = col.get_state()
+    assert step == 0
+    col.step_async(3)
+    col.sync()
+    prob2 = dict(prob)
+    prob2["params0"] = q.reshape(-1).cpu().numpy()
+    ref = Collage(prob2, **kw)
+    ref.step(3)
+    assert torch.equal(col.get_params(), ref.get_params())
+    col.close()
+    ref.close()
+
+
 def test_nonfinite_params_are_reported(Collage):
     from paper_2406_04008_gb300._lib import CollageError
     prob, opts, grid = _case()
@@ -132,3 +160,15 @@ def test_step_host_round_trip(Collage):
     assert np.array_equal(pout, col.get_params().reshape(-1).cpu().numpy())
     assert np.array_equal(lout, col.loss().reshape(-1).cpu().numpy())
     col.close()
+
+
+def test_fp32_peak_is_plausible(Collage):
+    """The FMA-chain measurement lands between half and 1.05x of SMs x 128 lanes x 2 x max clock."""
+    import ctypes as C
+    from paper_2406_04008_gb300 import _lib
+    out = C.c_float()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _lib.check(_lib.load().collage_fp32_peak(stream, C.byref(out)))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * nominal < out.value < 1.05 * nominal
