@@ -627,6 +627,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   }
   CKC(dmalloc(h->owned, d.segA, h->V));
   CKC(dmalloc(h->owned, d.segB, h->V));
+  CKC(dmalloc(h->owned, d.segS, h->V));
   CKC(dmalloc(h->owned, d.tpx, h->N));
   CKC(dmalloc(h->owned, d.bbox, h->N));
   CKC(dmalloc(h->owned, d.rect, h->N));

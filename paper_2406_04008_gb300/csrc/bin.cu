@@ -125,14 +125,17 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     if (k < nv) {
       float4 sa = make_float4(a.x, a.y, 0.f, 0.f);
       float2 sb = make_float2(a.y, 0.f);
+      float slope = 0.0f;
       if (closed || k + 1 < nv) {
         const float ex = b.x - a.x, ey = b.y - a.y, ee = ex * ex + ey * ey;
         sa.z = ex;
         sa.w = ey;
         sb = make_float2(b.y, ee > 0.0f ? 1.0f / ee : 0.0f);
+        slope = ey != 0.0f ? ex / ey : 0.0f;
       }
       d.segA[v0 + k] = sa;
       d.segB[v0 + k] = sb;
+      d.segS[v0 + k] = slope;
     }
   }
   xmin = warp_min(xmin);
@@ -177,27 +180,37 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     atomicAdd(&d.tile_cnt[tb + (r.y + i / w) * ntx + r.x + i % w], 1);
 }
 
-// Exclusive scan of the per-tile counts into [begin, end) ranges: one block, rounds of 8192 tiles
-// staged through shared memory so that global loads and stores are coalesced; each thread scans 8
-// consecutive counts, the block scans the per-thread totals.  The total is the pair count; above
-// the capacity the overflow bit is latched.
-constexpr int kScanThreads = 1024, kScanPer = 8, kScanRound = kScanThreads * kScanPer;
+// Exclusive scan of the per-tile counts into [begin, end) ranges: one block, rounds of 16384
+// tiles; each thread loads 16 consecutive counts with vector loads, scans them in registers, the
+// block scans the per-thread totals, and the thread writes its 16 ranges with vector stores.  The
+// total is the pair count; above the capacity the overflow bit is latched.
+constexpr int kScanThreads = 1024, kScanPer = 16, kScanRound = kScanThreads * kScanPer;
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
   pdl_enter();
-  __shared__ int buf[kScanRound + 1];
   __shared__ int wsum[32];
   const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
   int carry = 0;
   for (int base = 0; base < n; base += kScanRound) {
-    for (int i = t; i < kScanRound; i += kScanThreads) buf[i] = base + i < n ? d.tile_cnt[base + i] : 0;
-    __syncthreads();
+    const int i0 = base + t * kScanPer;
+    const bool full = i0 + kScanPer <= n;
     int v[kScanPer];
+    if (full) {
+      const int4* src = reinterpret_cast<const int4*>(d.tile_cnt + i0);
+#pragma unroll
+      for (int q = 0; q < kScanPer / 4; ++q) {
+        const int4 a = src[q];
+        v[4 * q] = a.x;
+        v[4 * q + 1] = a.y;
+        v[4 * q + 2] = a.z;
+        v[4 * q + 3] = a.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kScanPer; ++i) v[i] = i0 + i < n ? d.tile_cnt[i0 + i] : 0;
+    }
     int s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-      v[i] = buf[t * kScanPer + i];
-      s += v[i];
-    }
+    for (int i = 0; i < kScanPer; ++i) s += v[i];
     int x = s;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -215,18 +228,26 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
     }
     __syncthreads();
     int run = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
+    const int round_total = wsum[31];
+    unsigned st[kScanPer + 1];
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {  // exclusive starts; buf[kScanRound] = end of the round
-      buf[t * kScanPer + i] = run;
+    for (int i = 0; i < kScanPer; ++i) {
+      st[i] = (unsigned)run;
       run += v[i];
     }
-    if (t == kScanThreads - 1) buf[kScanRound] = run;
-    const int round_total = wsum[31];
-    __syncthreads();
-    for (int i = t; i < kScanRound && base + i < n; i += kScanThreads)
-      d.range[base + i] = make_uint2((uint32_t)buf[i], (uint32_t)buf[i + 1]);
+    st[kScanPer] = (unsigned)run;
+    if (full) {
+      uint4* dst = reinterpret_cast<uint4*>(d.range + i0);
+#pragma unroll
+      for (int q = 0; q < kScanPer / 2; ++q)
+        dst[q] = make_uint4(st[2 * q], st[2 * q + 1], st[2 * q + 1], st[2 * q + 2]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kScanPer; ++i)
+        if (i0 + i < n) d.range[i0 + i] = make_uint2(st[i], st[i + 1]);
+    }
     carry += round_total;
-    __syncthreads();  // buf and wsum are reused by the next round
+    __syncthreads();  // wsum is reused by the next round
   }
   if (t == 0) {
     *d.total_pairs = carry;

@@ -70,6 +70,7 @@ struct Dev {
   // ---- per iteration ----
   float4* segA;                 // [V] segment k: start (px, relative to the translation), direction
   float2* segB;                 // [V] segment k: end point y, 1 / |direction|^2
+  float* segS;                  // [V] segment k: dx/dy of its direction (0 if horizontal)
   float4* tpx;                  // [n] translation in px: (hi.x, hi.y, lo.x, lo.y)
   float4* bbox;                 // [n] outline box relative to the translation, grown by the margin
   int4* rect;                   // [n] tile rectangle (tx0, ty0, tx1, ty1), empty if tx1 < tx0

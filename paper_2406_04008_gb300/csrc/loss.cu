@@ -12,8 +12,7 @@
 namespace collage {
 
 constexpr int kDT = 32;       // dilation tile side
-constexpr int kDThreads = 512;
-constexpr int kDPPT = kDT * kDT / kDThreads;
+constexpr int kDThreads = 256;
 
 __device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
   int lo = 0, hi = P - 1;
@@ -85,22 +84,28 @@ __device__ __forceinline__ void hsum_one(const Src& src, uint32_t* H, int it) {
   }
 }
 
-// One vertical running-window item of kernel k: rows r0..r0+kSeg-1 of output column c,
-// Bk[k][o][c] = sum_{|dr| <= r_k} H[k][o + r_k + dr][c].
-template <int K, int k>
-__device__ __forceinline__ void vsum_one(const uint32_t* H, uint32_t* Bk, int it) {
-  constexpr int r = dil_r(k);
-  const int c = it % kDT, r0 = (it / kDT) * kSeg;
-  const uint32_t* col = H + hbase(k) * kHP + c;
-  uint32_t acc = 0u;
+// Vertical pass fused with the per-pixel output: a thread forms the box sums of all K kernels at
+// kVRows consecutive output rows of one column (a running window per kernel), then uses them
+// directly, so no per-kernel result image is kept in shared memory.
+// B[k][i] = sum_{|dr| <= r_k} H[k][r0 + i + r_k + dr][c].
+constexpr int kVRows = 4;
+constexpr int kVItems = kDT * (kDT / kVRows);
+
+template <int K, int k = 0>
+__device__ __forceinline__ void vsums_col(const uint32_t* H, int c, int r0, uint32_t (&B)[K][kVRows]) {
+  if constexpr (k < K) {
+    constexpr int r = dil_r(k);
+    const uint32_t* col = H + hbase(k) * kHP + c;
+    uint32_t acc = 0u;
 #pragma unroll
-  for (int j = 0; j <= 2 * r; ++j) acc += col[(r0 + j) * kHP];
-  uint32_t* out = Bk + k * kDT * kDT + c;
-  out[r0 * kDT] = acc;
+    for (int j = 0; j <= 2 * r; ++j) acc += col[(r0 + j) * kHP];
+    B[k][0] = acc;
 #pragma unroll
-  for (int i = 1; i < kSeg; ++i) {
-    acc += col[(r0 + i + 2 * r) * kHP] - col[(r0 + i - 1) * kHP];
-    out[(r0 + i) * kDT] = acc;
+    for (int i = 1; i < kVRows; ++i) {
+      acc += col[(r0 + i + 2 * r) * kHP] - col[(r0 + i - 1) * kHP];
+      B[k][i] = acc;
+    }
+    vsums_col<K, k + 1>(H, c, r0, B);
   }
 }
 
@@ -112,14 +117,6 @@ __device__ __forceinline__ void hsum_item(const Src& src, uint32_t* H, int it) {
     constexpr int items_k = hrows(k) * kNSeg;
     if (it < items_k) hsum_one<K, k>(src, H, it);
     else hsum_item<K, k + 1>(src, H, it - items_k);
-  }
-}
-
-template <int K, int k = 0>
-__device__ __forceinline__ void vsum_item(const uint32_t* H, uint32_t* Bk, int it) {
-  if constexpr (k < K) {
-    if (it < kDT * kNSeg) vsum_one<K, k>(H, Bk, it);
-    else vsum_item<K, k + 1>(H, Bk, it - kDT * kNSeg);
   }
 }
 
@@ -144,17 +141,12 @@ __device__ __forceinline__ void hsums_all(const Src& src, uint32_t* H) {
   for (int it = threadIdx.x; it < DilGeom<K>::HR * kNSeg; it += blockDim.x) hsum_item<K>(src, H, it);
 }
 
-template <int K>
-__device__ __forceinline__ void vsums_all(const uint32_t* H, uint32_t* Bk) {
-  for (int it = threadIdx.x; it < K * kDT * kNSeg; it += blockDim.x) vsum_item<K>(H, Bk, it);
-}
-
 __device__ __forceinline__ int dil_flags(const Dev& d, int dt) {
   return d.dtile_flags ? (int)d.dtile_flags[dt] : (kFlagOwn | kFlagHalo);
 }
 
 template <int K>
-__global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
+__global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
   pdl_enter();
   constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
   constexpr float inv_q = 1.0f / (float)(1u << Q);
@@ -163,7 +155,6 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   uint32_t* sO = sm;
   uint32_t* H = sO + S * SP;
-  uint32_t* Bk = H + DilGeom<K>::HR * kHP;
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
@@ -191,32 +182,33 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
     __syncthreads();
     hsums_all<K>(OccSrc{sO, SP}, H);
     __syncthreads();
-    vsums_all<K>(H, Bk);
-    __syncthreads();
     float lu = 0.0f;
+    for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
+      const int c = it % kDT, r0 = (it / kDT) * kVRows;
+      uint32_t B[K][kVRows];
+      vsums_col<K>(H, c, r0, B);
 #pragma unroll
-    for (int i = 0; i < kDPPT; ++i) {
-      const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
-      const int X = x0 + c, Y = y0 + rr;
-      if (X >= res || Y >= res) continue;
-      const long long pix = pb + (long long)Y * res + X;
-      const float O = 1.0f - d.img_I[pix];
-      const float M = d.covc[pix];
-      const float mval = M * (1.0f - O);
-      float gdir = 0.0f;
-      unsigned mask = 0u;
+      for (int i = 0; i < kVRows; ++i) {
+        const int X = x0 + c, Y = y0 + r0 + i;
+        if (X >= res || Y >= res) continue;
+        const long long pix = pb + (long long)Y * res + X;
+        const float O = 1.0f - d.img_I[pix];
+        const float M = d.covc[pix];
+        const float mval = M * (1.0f - O);
+        float gdir = 0.0f;
+        unsigned mask = 0u;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const uint32_t Bq = Bk[k * kDT * kDT + local];
-        const float D = fminf(1.0f, (float)Bq * inv_q);
-        const float w = d.L.dil_w[k];
-        lu += w * mval * (1.0f - D);
-        if (Bq < (1u << Q)) mask |= 1u << k;  // B_k < 1, decided on the exact fixed-point sum
-        gdir -= w * (1.0f - D);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
+        for (int k = 0; k < K; ++k) {
+          const float D = fminf(1.0f, (float)B[k][i] * inv_q);
+          const float w = d.L.dil_w[k];
+          lu += w * mval * (1.0f - D);
+          if (B[k][i] < (1u << Q)) mask |= 1u << k;  // B_k < 1, decided on the exact fixed-point sum
+          gdir -= w * (1.0f - D);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
+        }
+        d.dil_m[pix] = mval;
+        d.dil_mask[pix] = (uint8_t)mask;
+        d.gOu[pix] = M * gdir;
       }
-      d.dil_m[pix] = mval;
-      d.dil_mask[pix] = (uint8_t)mask;
-      d.gOu[pix] = M * gdir;
     }
     // fixed-order block sum
     for (int o = 16; o; o >>= 1) lu += __shfl_xor_sync(0xffffffffu, lu, o);
@@ -231,7 +223,7 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_fwd(Dev d) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
+__global__ void __launch_bounds__(kDThreads, 5) k_dilate_bwd(Dev d) {
   pdl_enter();
   constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
   constexpr float inv_q = 1.0f / (float)(1u << Q);
@@ -239,8 +231,7 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   uint32_t* sM = sm;
   uint32_t* H = sM + S * SP;
-  uint32_t* Bk = H + DilGeom<K>::HR * kHP;
-  uint8_t* sMask = reinterpret_cast<uint8_t*>(Bk + K * kDT * kDT);
+  uint8_t* sMask = reinterpret_cast<uint8_t*>(H + DilGeom<K>::HR * kHP);
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     if (!(dil_flags(d, dt) & kFlagHalo)) continue;  // G = 0 over the tile and its halo
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
@@ -259,17 +250,19 @@ __global__ void __launch_bounds__(kDThreads) k_dilate_bwd(Dev d) {
     __syncthreads();
     hsums_all<K>(GSrc{sM, sMask, SP}, H);
     __syncthreads();
-    vsums_all<K>(H, Bk);
-    __syncthreads();
+    for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
+      const int c = it % kDT, r0 = (it / kDT) * kVRows;
+      uint32_t B[K][kVRows];
+      vsums_col<K>(H, c, r0, B);
 #pragma unroll
-    for (int i = 0; i < kDPPT; ++i) {
-      const int local = threadIdx.x + i * kDThreads, rr = local / kDT, c = local % kDT;
-      const int X = x0 + c, Y = y0 + rr;
-      if (X >= res || Y >= res) continue;
-      float acc = 0.0f;
+      for (int i = 0; i < kVRows; ++i) {
+        const int X = x0 + c, Y = y0 + r0 + i;
+        if (X >= res || Y >= res) continue;
+        float acc = 0.0f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * ((float)Bk[k * kDT * kDT + local] * inv_q);
-      d.gOu[pb + (long long)Y * res + X] += acc;
+        for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * ((float)B[k][i] * inv_q);
+        d.gOu[pb + (long long)Y * res + X] += acc;
+      }
     }
   }
 }
@@ -406,7 +399,7 @@ __global__ void k_adam_flush(Dev d) {
 
 static size_t dilate_smem(int K, bool backward) {
   const int S = kDT + 2 * dil_r(K - 1), SP = S | 1;
-  size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP + (size_t)K * kDT * kDT;
+  size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP;
   if (backward) f += ((size_t)S * SP + 3) / 4;  // mask bytes
   return f * sizeof(uint32_t);
 }

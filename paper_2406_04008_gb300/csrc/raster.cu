@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
   __shared__ float4 s_seg[kNearCap];
   __shared__ float2 s_seg2[kNearCap];
+  __shared__ float s_slope[kNearCap];
   __shared__ int s_idx[kNearCap];
   __shared__ float2 s_xt[kNearCap * T];  // per (near segment, row): crossing x and direction
   __shared__ int s_back[T];
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
           if (nr && pos >= 0 && pos < kNearCap) {
             s_seg[pos] = sa;
             s_seg2[pos] = sb;
+            s_slope[pos] = d.segS[v0 + j];
             s_idx[pos] = j;
           }
           cnt += __popc(bal);
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
           const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
           const bool a_le = yr - sa.y >= 0.0f, b_le = yr - bxy >= 0.0f;
           float2 xt = make_float2(-FLT_MAX, __int_as_float(0));
-          if (a_le != b_le) xt = make_float2(sa.x + sa.z * ((yr - sa.y) / sa.w), __int_as_float(a_le ? 1 : -1));
+          if (a_le != b_le) xt = make_float2(fmaf(yr - sa.y, s_slope[j], sa.x), __int_as_float(a_le ? 1 : -1));
           s_xt[e] = xt;
         }
         __syncthreads();
