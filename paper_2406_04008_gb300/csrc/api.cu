@@ -51,6 +51,8 @@ struct collage_s {
   int* ctl = nullptr;        // device: status, step, total_pairs, pending, 4 work counters
   int* h_ctl = nullptr;      // pinned mirror
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;  // side branch of an iteration (the loss assembly)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
   std::string err;
   std::vector<void*> owned;      // fixed-size allocations
@@ -114,6 +116,9 @@ void drop_graph(collage_t h) {
 collage_s::~collage_s() {
   if (graph) cudaGraphExecDestroy(graph);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (aux_stream) cudaStreamDestroy(aux_stream);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   if (h_ctl) cudaFreeHost(h_ctl);
   free_list(pair_bufs);
   free_list(level_bufs);
@@ -404,19 +409,29 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   MARK_(3);
   STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 2));
   MARK_(4);
-  if (dil) {
-    STEP_(launch_dilate(d, s, false));
-    STEP_(launch_dilate(d, s, true));
+  // the loss assembly needs only the composite's and the distribution term's partials: it runs on
+  // a side stream beside the distribution adjoint and the raster adjoint (joined at the end of
+  // the iteration); under stage timing it stays on the main stream
+  const bool side = bwd && !ev;
+  if (dil) STEP_(launch_dilate(d, s, false));
+  if (side) {
+    STEP_(cudaEventRecord(h->ev_fork, s));
+    STEP_(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+    STEP_(launch_loss(d, h->aux_stream));
+    STEP_(cudaEventRecord(h->ev_join, h->aux_stream));
   }
+  if (dil) STEP_(launch_dilate(d, s, true));
   MARK_(5);
-  if (bwd) STEP_(launch_raster_bwd(d, s, h->bwd_grid));
+  // in step mode the last block of the last gradient kernel marks this iteration's Adam step
+  // pending; the next transform (or a flush before params are read) applies it
+  const bool mark = mode == kStep;
+  if (bwd) STEP_(launch_raster_bwd(d, s, h->bwd_grid, mark && !d.deterministic));
   MARK_(6);
-  if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s));
+  if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s, mark));
   MARK_(7);
-  // in step mode the loss assembly marks this iteration's Adam step pending; the next transform
-  // (or a flush before params are read) applies it
-  if (bwd) STEP_(launch_loss(d, s, mode == kStep));
+  if (bwd && !side) STEP_(launch_loss(d, s));
   MARK_(8);
+  if (side) STEP_(cudaStreamWaitEvent(s, h->ev_join, 0));
   MARK_(9);
 #undef STEP_
 #undef MARK_
@@ -654,6 +669,9 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.prob_pix_base = h->d_prob_pix_base;
   CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
   CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CKC(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
 #undef CKC
   st = setup_level(h, 0);
   if (st) return bail(st);

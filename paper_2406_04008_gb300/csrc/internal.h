@@ -104,7 +104,8 @@ struct Dev {
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
   int* work;                    // [4] per-iteration counters, zeroed by the tile scan:
                                 //   [0] near pairs taken by the distance kernel's blocks,
-                                //   [1] entries of live_list, [2] entries of near_list, [3] spare
+                                //   [1] entries of live_list, [2] entries of near_list,
+                                //   [3] blocks of the last gradient kernel that have finished
   LossParams L;
   int deterministic;
   int pdl;                      // launch the iteration's kernels with programmatic serialisation
@@ -167,6 +168,23 @@ inline cudaError_t klaunch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 b
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// The last block of the kernel that completes an iteration's gradient marks the iteration's Adam
+// step pending (applied by the next transform) and advances the step count, unless the iteration
+// overflowed or met non-finite params.  Every block calls this once, after its last write to the
+// gradient; the counter work[3] is zeroed by the tile scan of each iteration.
+__device__ __forceinline__ void mark_step_if_last(const Dev& d) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's gradient writes are visible before it is counted
+    if (atomicAdd(&d.work[3], 1) == (int)gridDim.x - 1 &&
+        !(atomicAdd(d.status, 0) & (kStatusOverflow | kStatusBadParam))) {
+      __threadfence();
+      *d.step += 1;
+      *d.pending = 1;
+    }
+  }
+}
+
 // ---- launchers (each enqueues on `s`, returns the launch error) ----
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
 cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
@@ -178,11 +196,12 @@ cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int t
 cudaError_t prepare_dilate(int n_dil);  // sets dynamic shared memory limits (not capturable)
 cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward);
 cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s);  // once per level, after the container
-cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid);
-cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s);
+// mark_step: the kernel's last block marks the iteration's Adam step (step mode)
+cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid, bool mark_step);
+cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s, bool mark_step);
 // applies a pending Adam step to all elements and clears the flag (before params are read)
 cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s);
-cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step);
+cudaError_t launch_loss(const Dev& d, cudaStream_t s);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
 // Resident blocks per SM of the raster kernels, the pairs one adjoint block and the tiles one
 // composite block take at once (the forward distance kernel takes one pair per block).

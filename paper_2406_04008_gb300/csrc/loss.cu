@@ -305,7 +305,7 @@ __device__ __forceinline__ float warp_sum_f(float x) {
   for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
-__global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
+__global__ void __launch_bounds__(kLossThreads) k_loss(Dev d) {
   pdl_enter();
   __shared__ float s_red[4][kLossThreads / 32];
   const int p = blockIdx.x;
@@ -350,20 +350,13 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d, int count_step) {
       out[2] = u;
       out[3] = Ld;
       out[4] = d.L.alpha * Lc + d.L.beta * Lo + d.L.gamma * u + d.L.delta * Ld;
-      if (count_step && p == 0 && !(*d.status & (kStatusOverflow | kStatusBadParam))) {
-        *d.step += 1;  // this iteration's Adam step is now pending (applied by the next transform)
-        *d.pending = 1;
-      }
     }
   }
 }
 
 // Deterministic mode: each element sums its (tile, element) partials over its tile rectangle in
 // row-major order (a tile's list is ordered by element id, so the pair is found by bisection).
-__global__ void k_grad_reduce(Dev d) {
-  pdl_enter();
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= d.n_elems || (*d.status & kStatusOverflow)) return;
+__device__ __forceinline__ void grad_reduce_one(const Dev& d, int g) {
   const int4 rc = d.rect[g];
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (rc.z >= rc.x && rc.w >= rc.y) {
@@ -388,6 +381,13 @@ __global__ void k_grad_reduce(Dev d) {
       }
   }
   d.dq[g] = acc;
+}
+
+__global__ void k_grad_reduce(Dev d, int mark) {
+  pdl_enter();
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < d.n_elems && !(*d.status & kStatusOverflow)) grad_reduce_one(d, g);
+  if (mark) mark_step_if_last(d);
 }
 
 // Applies a pending Adam step to every element (see adam_update); the caller then clears the flag.
@@ -460,12 +460,12 @@ cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const Dev& d, cudaStream_t s, bool count_step) {
-  return klaunch(d.pdl, k_loss, d.n_probs, kLossThreads, 0, s, d, count_step ? 1 : 0);
+cudaError_t launch_loss(const Dev& d, cudaStream_t s) {
+  return klaunch(d.pdl, k_loss, d.n_probs, kLossThreads, 0, s, d);
 }
 
-cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s) {
-  return klaunch(d.pdl, k_grad_reduce, (d.n_elems + 255) / 256, 256, 0, s, d);
+cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s, bool mark_step) {
+  return klaunch(d.pdl, k_grad_reduce, (d.n_elems + 255) / 256, 256, 0, s, d, mark_step ? 1 : 0);
 }
 
 cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s) {

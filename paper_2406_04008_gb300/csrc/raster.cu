@@ -72,6 +72,7 @@ __device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, floa
 
 constexpr int kSegCap = 1024;   // container segments staged per chunk
 constexpr int kNearCap = 64;    // near segments staged per chunk of one (tile, element) pair
+constexpr int kStageSegs = 128; // outlines up to this many segments are staged whole per pair
 constexpr int kPairWarps = 4;   // pairs per block of the per-pair adjoint (one per warp)
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
 
@@ -107,6 +108,9 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   __shared__ float s_slope[kNearCap];
   __shared__ int s_idx[kNearCap];
   __shared__ float2 s_xt[kNearCap * T];  // per (near segment, row): crossing x and direction
+  __shared__ float4 s_allA[kStageSegs];   // the whole outline (when it has <= kStageSegs segments)
+  __shared__ float2 s_allB[kStageSegs];
+  __shared__ float s_allS[kStageSegs];
   __shared__ int s_back[T];
   __shared__ int s_near;
   if (*d.status & kStatusOverflow) return;
@@ -152,8 +156,22 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
       bj[k] = -1;
       wn[k] = 0;
     }
+    // a short outline is loaded once by the whole block (one round trip) and both the compaction
+    // and the backdrop read it from shared memory; a long one is read from global memory
+    const bool staged = ns <= kStageSegs;
+    const float4* SA = staged ? s_allA : d.segA + v0;
+    const float2* SB = staged ? s_allB : d.segB + v0;
+    const float* SS = staged ? s_allS : d.segS + v0;
     for (int base = 0;; base += kNearCap) {
       __syncthreads();  // the previous users of the shared lists are done
+      if (base == 0 && staged) {
+        for (int j = threadIdx.x; j < ns; j += NT) {
+          s_allA[j] = d.segA[v0 + j];
+          s_allB[j] = d.segB[v0 + j];
+          s_allS[j] = d.segS[v0 + j];
+        }
+        __syncthreads();
+      }
       if (wid == 0) {
         // ordered compaction of the near segments with positions in [base, base + kNearCap)
         int cnt = 0;
@@ -163,8 +181,8 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
           float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
           float2 sb = make_float2(0.f, 0.f);
           if (j < ns) {
-            sa = d.segA[v0 + j];
-            sb = d.segB[v0 + j];
+            sa = SA[j];
+            sb = SB[j];
             const float bx = sa.x + sa.z;
             nr = !(fmaxf(sa.x, bx) < gx0 || fminf(sa.x, bx) > gx1 || fmaxf(sa.y, sb.x) < gy0 ||
                    fminf(sa.y, sb.x) > gy1);
@@ -174,7 +192,7 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
           if (nr && pos >= 0 && pos < kNearCap) {
             s_seg[pos] = sa;
             s_seg2[pos] = sb;
-            s_slope[pos] = d.segS[v0 + j];
+            s_slope[pos] = SS[j];
             s_idx[pos] = j;
           }
           cnt += __popc(bal);
@@ -189,8 +207,8 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
         const float yr0 = ((float)(ty * T) + 0.5f - tp.y) - tp.w;
         const float yr1 = ((float)(ty * T + T - 1) + 0.5f - tp.y) - tp.w;
         for (int j = threadIdx.x - 32; j < ns; j += NT - 32) {
-          const float4 sa = d.segA[v0 + j];
-          const float2 sb = d.segB[v0 + j];
+          const float4 sa = SA[j];
+          const float2 sb = SB[j];
           if (fminf(sa.x, sa.x + sa.z) <= gx1) continue;  // near, left or overlapping in x
           if (fmaxf(sa.y, sb.x) <= yr0 || fminf(sa.y, sb.x) > yr1) continue;
           const int up = sa.y < sb.x ? 1 : -1;
@@ -397,7 +415,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
 // tile's pixels by a fixed shuffle tree and added to the element's gradient (or stored per pair).
 // ------------------------------------------------------------------------------------------------
 template <int T>
-__global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d) {
+__global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark) {
   pdl_enter();
   constexpr int NP = T * T, PPL = NP / 32;
   if (*d.status & kStatusOverflow) return;
@@ -492,6 +510,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d) {
       }
     }
   }
+  if (mark) mark_step_if_last(d);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -589,10 +608,11 @@ cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int t
   }
 }
 
-cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid) {
+cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid, bool mark_step) {
+  const int mk = mark_step ? 1 : 0;
   switch (d.tile) {
-    case 8: return klaunch(d.pdl, k_raster_bwd<8>, pair_grid, kPairWarps * 32, 0, s, d);
-    case 16: return klaunch(d.pdl, k_raster_bwd<16>, pair_grid, kPairWarps * 32, 0, s, d);
+    case 8: return klaunch(d.pdl, k_raster_bwd<8>, pair_grid, kPairWarps * 32, 0, s, d, mk);
+    case 16: return klaunch(d.pdl, k_raster_bwd<16>, pair_grid, kPairWarps * 32, 0, s, d, mk);
     default: return cudaErrorInvalidValue;
   }
 }
