@@ -650,8 +650,8 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   CKC(cudaMemset(d.dq, 0, sizeof(float4) * h->N));
   CKC(dmalloc(h->owned, d.loss_terms, 5 * h->P));
   CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
-  CKC(dmalloc(h->owned, h->ctl, 8));
-  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 8));
+  CKC(dmalloc(h->owned, h->ctl, 12));
+  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 12));
   d.status = h->ctl;
   d.step = h->ctl + 1;
   d.total_pairs = h->ctl + 2;

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
     *d.total_pairs = carry;
     if (carry > d.cap) atomicOr(d.status, kStatusOverflow);
     *d.pending = 0;  // every transform block has applied the pending Adam step
-    for (int i = 0; i < 4; ++i) d.work[i] = 0;
+    for (int i = 0; i < 8; ++i) d.work[i] = 0;
   }
 }
 
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
 constexpr int kEmitThreads = 128, kEmitChunkRows = 32, kEmitMaxW = 64;
 __global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
   pdl_enter();
-  __shared__ uint8_t s_near[kEmitChunkRows * kEmitMaxW];
+  __shared__ int s_near[kEmitChunkRows * kEmitMaxW];  // segments marking the tile near
   __shared__ int s_wind[kEmitChunkRows * kEmitMaxW];
   const int g = blockIdx.x;
   const int lane = threadIdx.x & 31;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
         const int ay = max((int)floorf((y0 - m - (fT - 0.5f)) / fT) + 1, ty_lo);
         const int byt = min((int)floorf((y1 + m - 0.5f) / fT), ty_lo + ch - 1);
         for (int ty = ay; ty <= byt; ++ty)
-          for (int tx = ax; tx <= bxt; ++tx) s_near[(ty - ty_lo) * cw + (tx - tx_lo)] = 1;
+          for (int tx = ax; tx <= bxt; ++tx) atomicAdd(&s_near[(ty - ty_lo) * cw + (tx - tx_lo)], 1);
         // crossings of the tiles' first pixel rows
         if (closed) {
           for (int ty = ty_lo; ty < ty_lo + ch; ++ty) {
@@ -358,12 +358,19 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
             if (cls != kPairNear && d.deterministic) d.partial[pos] = make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
+        // near pairs with many segments near the tile go to the front of the list (taken first,
+        // so that the costliest pairs do not trail), the others to the back
         const bool near = pos >= 0 && cls == kPairNear;
-        const unsigned bal = __ballot_sync(0xffffffffu, near);
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&d.work[2], __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (near) d.near_list[base + __popc(bal & ((1u << lane) - 1u))] = pos;
+        const bool heavy = near && s_near[i] > kHeavyNear;
+        const unsigned bh = __ballot_sync(0xffffffffu, heavy), bl = __ballot_sync(0xffffffffu, near && !heavy);
+        int hb = 0, lb = 0;
+        if (lane == 0 && bh) hb = atomicAdd(&d.work[2], __popc(bh));
+        if (lane == 0 && bl) lb = atomicAdd(&d.work[4], __popc(bl));
+        hb = __shfl_sync(0xffffffffu, hb, 0);
+        lb = __shfl_sync(0xffffffffu, lb, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (heavy) d.near_list[hb + __popc(bh & below)] = pos;
+        else if (near) d.near_list[d.cap - 1 - (lb + __popc(bl & below))] = pos;
       }
     }
   }

@@ -29,6 +29,7 @@ constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bu
 constexpr uint8_t kPairOut = 0;   // not near, outside the outline: c = c^pad = 0
 constexpr uint8_t kPairIn = 1;    // not near, inside: c = c^pad = 1
 constexpr uint8_t kPairNear = 2;  // per-pixel signed distances (the distance kernel)
+constexpr int kHeavyNear = 24;    // a near pair with more segments near its tile is taken first
 
 struct LossParams {
   float alpha, beta, gamma, delta;
@@ -80,7 +81,8 @@ struct Dev {
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
   int* pair_tile;               // [cap] tile of each pair slot
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
-  int* near_list;               // [cap] slots of the near pairs (the distance kernel's work list)
+  int* near_list;               // [cap] slots of the near pairs (the distance kernel's work list):
+                                //   heavy ones from the front, light ones from the back
   int* live_list;               // [cap] slots of the pairs with some non-saturated pixel
                                 //   (the adjoint's work list; order depends on atomics)
   int* pair_sorted;             // [cap] each tile's elements in increasing element order
@@ -102,10 +104,11 @@ struct Dev {
   int* status;                  // [1]
   int* step;                    // [1] Adam step count (the loss assembly advances it)
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
-  int* work;                    // [4] per-iteration counters, zeroed by the tile scan:
+  int* work;                    // [8] per-iteration counters, zeroed by the tile scan:
                                 //   [0] near pairs taken by the distance kernel's blocks,
-                                //   [1] entries of live_list, [2] entries of near_list,
-                                //   [3] blocks of the last gradient kernel that have finished
+                                //   [1] entries of live_list, [2] heavy near pairs (front of
+                                //   near_list), [3] blocks of the last gradient kernel that have
+                                //   finished, [4] light near pairs (back of near_list), [5..7] spare
   LossParams L;
   int deterministic;
   int pdl;                      // launch the iteration's kernels with programmatic serialisation

@@ -116,14 +116,14 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int n_near = d.work[2];
+  const int n_heavy = d.work[2], n_near = n_heavy + d.work[4];
   // the near pairs: a block's first is its block index in the list, the others are taken from a
   // shared counter as blocks finish (pair costs vary by two orders of magnitude); s_next is
   // double-buffered so that thread 0's next write never meets a read of the previous value
   __shared__ int s_next[2];
   for (int i = blockIdx.x, it = 0; i < n_near; ++it) {
     if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
-    const int slot = d.near_list[i];
+    const int slot = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
     const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
