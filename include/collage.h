@@ -4,7 +4,7 @@
  * (SIGGRAPH Conference Papers 2025, arXiv 2406.04008).  The collage problem (Sec. 3, Eq. 1) places
  * n vector items inside a container by optimising one similarity transform per item; items are
  * transformed (Eq. 2), rasterised with anti-aliased coverage, scored by image-space losses against
- * the rasterised container (Sec. 4.2, Eqs. 5-8, plus the downward force of Sec. 5) and updated by
+ * the rasterised container (Sec. 4.2, Eqs. 5-8, plus the downward or point force of Sec. 5) and updated by
  * gradient steps (Eq. 4, here Adam), coarse to fine over a resolution pyramid (Sec. 4.3).
  *
  * Conventions.  Unit-square world coordinates, y down.  Pixel (i, j) of an R x R grid has its
@@ -66,7 +66,8 @@ typedef struct {
  * alpha, beta, gamma = 3e3, 8e4, 5e-4 (Eq. 8); w_in, w_out = 1, 100 (Sec. 4.2 containment);
  * dilation widths 5 + 6k pixels (Sec. 4.2 even distribution) with weights k + 1. */
 typedef struct {
-  float alpha, beta, gamma, delta_down; /* Eq. 8 weights and the downward-force weight (0 = off) */
+  float alpha, beta, gamma, delta_down; /* Eq. 8 weights and the force weight (0 = off; < 0
+                                           repels), force potential per force_kind below */
   float tau;                            /* opacity of the overlap render (Eq. 6), in (0, 1) */
   float w_in, w_out;                    /* containment penalty inside / outside (Eq. 5) */
   int n_dilations;                      /* 0..8 dilation kernels of the uniform loss (Eq. 7) */
@@ -90,6 +91,11 @@ typedef struct {
                                            programmatic stream serialisation, so its launch and
                                            block scheduling overlap the previous kernel's tail;
                                            results are bitwise the same either way */
+  int force_kind;                       /* force term of Sec. 5 (force attraction), weight
+                                           delta_down: 0 = downward, (1/wh) sum_p O(p) (1 - y_p);
+                                           1 = towards the point (force_x, force_y) in unit
+                                           coordinates, (1/wh) sum_p O(p) |p - (force_x, force_y)| */
+  float force_x, force_y;
 } collage_options;
 
 /* Per-level sizes, for callers that allocate image buffers. */
@@ -125,7 +131,7 @@ collage_status collage_set_level(collage_t h, int level);
 collage_status collage_render(collage_t h, void* stream, float* d_img_bw, float* d_img_tau);
 
 /* One forward + backward pass at the current params: d_loss_terms [n_probs*5] receives
- * (L_c, L_o, L_u, L_down, L) per problem (Eqs. 5, 6, 7, force, 8) and d_dparams [4*n_elems] the
+ * (L_c, L_o, L_u, L_force, L) per problem (Eqs. 5, 6, 7, force, 8) and d_dparams [4*n_elems] the
  * gradient dL/d(tx, ty, theta, s).  Either may be NULL.  Params are not changed.  Asynchronous. */
 collage_status collage_loss_backward(collage_t h, void* stream, float* d_loss_terms,
                                      float* d_dparams);
@@ -216,6 +222,18 @@ collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
 collage_status collage_uniform_term_noalloc(void* stream, int res, int n_dilations,
                                             const float* h_dil_weight, const float* d_ihat,
                                             const float* d_cov, float* d_loss, float* d_grad_occ);
+
+/* Quality metrics of the collage at the current params (Sec. 6, "Metrics of Collage Quality";
+ * the layout non-uniformity of the uniformity ablation, Sec. 6.1), from a render pass at the
+ * current level.  A pixel is object where O = 1 - Ihat >= 1/2, shape where the container coverage
+ * is >= 1/2, and overlap where at least two elements have sd >= 0.  h_metrics (host memory,
+ * [n_probs * 8] doubles) receives per problem: object pixels inside the shape, shape pixels,
+ * overlap pixels, object pixels outside the shape, then LC = inside / shape, OO = overlap /
+ * shape, EA = outside / shape, and L-nU = the mean over the non-object shape pixels of the
+ * squared distance (unit coordinates) to the nearest object pixel centre (0 when there is no
+ * object pixel or no such pixel).  Applies a pending Adam step first; synchronises `stream`;
+ * allocates its scratch on the first call at a level size. */
+collage_status collage_metrics(collage_t h, void* stream, double* h_metrics);
 
 /* Measurement helper, no counterpart in the paper: the FP32 FMA rate of the current device in
  * TFLOP/s (eight independent FMA chains per thread at full occupancy, best of three timed launches

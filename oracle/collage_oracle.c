@@ -19,7 +19,8 @@
  *    max(0, A_tau - tau) with A_tau = 1 - prod_i (1 - tau c_i^pad), tau = 1/2 by default;
  *  - Eq. 7: K box kernels of widths 5 + 6k pixels (k = 0..K-1), D_k = min(1, box sum of O),
  *    L_u = sum_k w_k sum_p M_C(p) (1 - O(p)) (1 - D_k(p)), unnormalised, zero padding;
- *  - downward force: L_down = (1/wh) sum_p O(p) (1 - y_p);
+ *  - force terms (Sec. 5, force attraction): L_f = (1/wh) sum_p O(p) phi(p) with the potential
+ *    phi = 1 - y (downward) or phi = |p - c| (towards a point c; a negative weight repels);
  *  - W = w_in where the container coverage is >= 1/2, else w_out;
  *  - one-sided derivatives at kinks: d max(0,x)/dx = 0 and d min(1,B)/dB = 0 at the kink, and
  *    the first closest segment (lowest index) wins ties.
@@ -373,6 +374,12 @@ static double box_sum(const double* img, int R, int i, int j, int r) {
 /* ---------------------------------------------------------------------------------------------
  * Loss (Eqs. 5-8) and gradient
  * ------------------------------------------------------------------------------------------- */
+/* Potential of the force term at pixel centre (x, y) (unit coordinates). */
+static double force_potential(const ora_opts* o, double x, double y) {
+  if (o->force_kind == 1) return hypot(x - o->force_x, y - o->force_y);
+  return 1.0 - y;
+}
+
 void ora_eval(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* terms,
               double* grad_a, double* grad_b, double* grad_v) {
   const long NP = (long)R * R;
@@ -392,11 +399,12 @@ void ora_eval(const ora_scene* sc, const double* params, int R, const ora_opts* 
     double y = ((double)i + 0.5) / (double)R;
     for (int j = 0; j < R; ++j) {
       long p = (long)i * R + j;
+      double x = ((double)j + 0.5) / (double)R;
       double ic = 1.0 - covc[p];
       double w = covc[p] >= 0.5 ? o->w_in : o->w_out;
       Lc += w * (ihat[p] - ic) * (ihat[p] - ic);
       Lo += atau[p] > tau ? atau[p] - tau : 0.0;
-      Ld += occ[p] * (1.0 - y);
+      Ld += occ[p] * force_potential(o, x, y);
     }
   }
   Lc *= inv_wh;
@@ -458,11 +466,12 @@ void ora_eval(const ora_scene* sc, const double* params, int R, const ora_opts* 
       double y = ((double)i + 0.5) / (double)R;
       for (int j = 0; j < R; ++j) {
         long p = (long)i * R + j;
+        double x = ((double)j + 0.5) / (double)R;
         double ic = 1.0 - covc[p];
         double w = covc[p] >= 0.5 ? o->w_in : o->w_out;
         /* O = 1 - Ihat, so the O-terms enter with a minus sign */
         gI[p] = o->alpha * inv_wh * 2.0 * w * (ihat[p] - ic) - o->gamma * gou[p] -
-                o->delta * inv_wh * (1.0 - y);
+                o->delta * inv_wh * force_potential(o, x, y);
         gA[p] = atau[p] > tau ? o->beta * inv_wh : 0.0;
       }
     }
@@ -749,6 +758,96 @@ double ora_pair_work(const ora_scene* sc, const double* params, int R, const ora
   }
   free_world(&g);
   return work;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Quality metrics (Sec. 6 and Sec. 6.1)
+ * ------------------------------------------------------------------------------------------- */
+void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* out) {
+  double rho = o->rho_px / R, pad = o->pad_px / R;
+  long NP = (long)R * R;
+  double* covc = (double*)malloc(sizeof(double) * NP);
+  unsigned char* obj = (unsigned char*)malloc(NP);
+  unsigned char* over = (unsigned char*)malloc(NP);
+  container_images(sc, R, rho, covc);
+  world_geom g = make_world(sc, params, rho, pad);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < R; ++i)
+    for (int j = 0; j < R; ++j) {
+      vec2 p = pixel_centre(i, j, R);
+      double keep = 1.0;
+      int n_in = 0;
+      for (int e = 0; e < sc->n; ++e) {
+        if (o->cull && culled(&g, e, p)) continue;
+        chain_query cq = element_query(sc, e, g.wv + sc->voff[e], p);
+        double sd = element_sd(sc, e, &cq);
+        keep *= 1.0 - S(sd / rho);
+        if (sd >= 0.0) n_in += 1;
+      }
+      obj[(long)i * R + j] = 1.0 - keep >= 0.5;
+      over[(long)i * R + j] = n_in >= 2;
+    }
+  free_world(&g);
+  double n_obj_in = 0, n_shape = 0, n_over = 0, n_exceed = 0;
+  for (long p = 0; p < NP; ++p) {
+    int shape = covc[p] >= 0.5;
+    n_shape += shape;
+    n_obj_in += shape && obj[p];
+    n_exceed += !shape && obj[p];
+    n_over += over[p];
+  }
+  /* squared distance (pixels^2) to the nearest object pixel centre, from its definition: the
+   * nearest object pixel of column k lies gcol(i, k) rows away, so the distance^2 is the minimum
+   * over the columns k of (j - k)^2 + gcol(i, k)^2 */
+  const long INF = 1L << 40;
+  long* gcol = (long*)malloc(sizeof(long) * NP);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < R; ++k) {
+    long last = -INF;  /* row of the last object pixel above */
+    for (int i = 0; i < R; ++i) {
+      if (obj[(long)i * R + k]) last = i;
+      gcol[(long)i * R + k] = last > -INF ? i - last : INF;
+    }
+    last = INF;
+    for (int i = R - 1; i >= 0; --i) {
+      if (obj[(long)i * R + k]) last = i;
+      if (last < INF && last - i < gcol[(long)i * R + k]) gcol[(long)i * R + k] = last - i;
+    }
+  }
+  double* rowsum = (double*)calloc(R, sizeof(double));
+  double n_free = 0;
+  for (long p = 0; p < NP; ++p) n_free += covc[p] >= 0.5 && !obj[p];
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < R; ++i)
+    for (int j = 0; j < R; ++j) {
+      long p = (long)i * R + j;
+      if (!(covc[p] >= 0.5) || obj[p]) continue;
+      long best = INF;
+      for (int k = 0; k < R; ++k) {
+        long gk = gcol[(long)i * R + k];
+        if (gk >= INF) continue;
+        long d2 = (long)(j - k) * (j - k) + gk * gk;
+        if (d2 < best) best = d2;
+      }
+      if (best < INF) rowsum[i] += (double)best;
+    }
+  double tot = 0.0; /* rows summed in order */
+  for (int i = 0; i < R; ++i) tot += rowsum[i];
+  int any_obj = 0;
+  for (long p = 0; p < NP && !any_obj; ++p) any_obj = obj[p];
+  out[0] = n_obj_in;
+  out[1] = n_shape;
+  out[2] = n_over;
+  out[3] = n_exceed;
+  out[4] = n_shape > 0 ? n_obj_in / n_shape : 0.0;
+  out[5] = n_shape > 0 ? n_over / n_shape : 0.0;
+  out[6] = n_shape > 0 ? n_exceed / n_shape : 0.0;
+  out[7] = (any_obj && n_free > 0) ? tot / n_free / ((double)R * (double)R) : 0.0;
+  free(rowsum);
+  free(gcol);
+  free(covc);
+  free(obj);
+  free(over);
 }
 
 int ora_set_threads(int n) {

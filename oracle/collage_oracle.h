@@ -41,6 +41,9 @@ typedef struct {
   double pad_px;                    /* padding offset in pixels (overlap render only) */
   double rho_px;                    /* anti-aliasing filter half-width in pixels */
   int cull;                         /* 1: skip elements whose grown bounding box misses the pixel */
+  int force_kind;                   /* 0: downward, potential 1 - y; 1: towards the point
+                                       (force_x, force_y), potential |p - (force_x, force_y)| */
+  double force_x, force_y;          /* the force point, unit coordinates */
 } ora_opts;
 
 /* Scene: element outlines (flattened once) and the container rings.  Inputs are copied. */
@@ -89,6 +92,18 @@ float ora_bin_radius(const ora_scene* sc, int e);
 /* Algorithmic work: sum over elements of (pixel centres inside the element's world bounding box
  * grown by rho + pad (+ stroke half-width)) x (segments of the element). */
 double ora_pair_work(const ora_scene* sc, const double* params, int res, const ora_opts* o);
+
+/* Quality metrics of the render at params on the R x R grid (Sec. 6, "Metrics of Collage
+ * Quality", and the layout non-uniformity of the uniformity ablation, Sec. 6.1).  A pixel is
+ * object where O = 1 - Ihat >= 1/2, shape where the container coverage is >= 1/2, and overlap
+ * where at least two elements have sd >= 0 (c_i >= 1/2).  out[8]:
+ *   [0] object pixels inside the shape, [1] shape pixels, [2] overlap pixels,
+ *   [3] object pixels outside the shape,
+ *   [4] LC = [0]/[1], [5] OO = [2]/[1], [6] EA = [3]/[1],
+ *   [7] L-nU: mean over the non-object shape pixels of the squared distance (unit coordinates)
+ *       from the pixel centre to the nearest object pixel centre (0 if there is no object pixel
+ *       or no such pixel). */
+void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* out);
 
 /* Threads the OpenMP loops use from now on (n < 1: all the host's cores); returns the previous
  * setting.  For timing the oracle on one core. */

@@ -41,11 +41,13 @@ class Opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
                 ("delta", C.c_double), ("tau", C.c_double), ("w_in", C.c_double),
                 ("w_out", C.c_double), ("n_dil", C.c_int), ("dil_weight", C.c_double * 8),
-                ("pad_px", C.c_double), ("rho_px", C.c_double), ("cull", C.c_int)]
+                ("pad_px", C.c_double), ("rho_px", C.c_double), ("cull", C.c_int),
+                ("force_kind", C.c_int), ("force_x", C.c_double), ("force_y", C.c_double)]
 
 
 def options(alpha=3e3, beta=8e4, gamma=5e-4, delta=0.0, tau=0.5, w_in=1.0, w_out=100.0,
-            n_dil=4, dil_weight=(1.0, 2.0, 3.0, 4.0), pad_px=0.0, rho_px=1.0, cull=1) -> Opts:
+            n_dil=4, dil_weight=(1.0, 2.0, 3.0, 4.0), pad_px=0.0, rho_px=1.0, cull=1,
+            force_kind=0, force_x=0.5, force_y=0.5) -> Opts:
     """Oracle options; the defaults are the weights of Eq. 8 and the readings of Eqs. 5-7."""
     o = Opts()
     o.alpha, o.beta, o.gamma, o.delta = alpha, beta, gamma, delta
@@ -54,6 +56,7 @@ def options(alpha=3e3, beta=8e4, gamma=5e-4, delta=0.0, tau=0.5, w_in=1.0, w_out
     for k in range(8):
         o.dil_weight[k] = dil_weight[k] if k < len(dil_weight) else 0.0
     o.pad_px, o.rho_px, o.cull = pad_px, rho_px, cull
+    o.force_kind, o.force_x, o.force_y = force_kind, force_x, force_y
     return o
 
 
@@ -86,6 +89,7 @@ def _load():
     lib.ora_bin_radius.argtypes = [vp, C.c_int]
     lib.ora_pair_work.restype = C.c_double
     lib.ora_pair_work.argtypes = [vp, _dp, C.c_int, opt]
+    lib.ora_metrics.argtypes = [vp, _dp, C.c_int, opt, _dp]
     lib.ora_set_threads.restype = C.c_int
     lib.ora_set_threads.argtypes = [C.c_int]
     _lib = lib
@@ -189,6 +193,12 @@ class Scene:
 
     def bin_radius(self, e):
         return self.lib.ora_bin_radius(self.h, e)
+
+    def metrics(self, params, res, opts):
+        """[obj in shape, shape, overlap, obj outside shape, LC, OO, EA, L-nU] (see ora_metrics)."""
+        out = np.zeros(8)
+        self.lib.ora_metrics(self.h, _d(params), res, C.byref(opts), out)
+        return out
 
     def pair_work(self, params, res, opts):
         return self.lib.ora_pair_work(self.h, _d(params), res, C.byref(opts))

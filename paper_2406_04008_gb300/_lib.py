@@ -41,7 +41,8 @@ class collage_options(C.Structure):
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("s_min", C.c_float), ("s_max", C.c_float), ("deterministic", C.c_int),
                 ("tile", C.c_int), ("persistent", C.c_int), ("use_graphs", C.c_int),
-                ("overlap_launches", C.c_int)]
+                ("overlap_launches", C.c_int), ("force_kind", C.c_int), ("force_x", C.c_float),
+                ("force_y", C.c_float)]
 
 
 class collage_info(C.Structure):
@@ -60,6 +61,7 @@ SIGNATURES = {
     "collage_render": (C.c_int, [_vp, _vp, _vp, _vp]),
     "collage_loss_backward": (C.c_int, [_vp, _vp, _vp, _vp]),
     "collage_fp32_peak": (C.c_int, [_vp, C.c_void_p]),
+    "collage_metrics": (C.c_int, [_vp, _vp, C.c_void_p]),
     "collage_step": (C.c_int, [_vp, _vp, C.c_int]),
     "collage_step_async": (C.c_int, [_vp, _vp, C.c_int]),
     "collage_run_schedule": (C.c_int, [_vp, _vp]),

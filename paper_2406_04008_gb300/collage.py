@@ -139,6 +139,13 @@ class Collage:
         self._check(self.lib.collage_autotune(self.h, _stream(), C.byref(best)))
         return self.info()["tile"], best.value
 
+    def metrics(self):
+        """[n_probs, 8]: object-in-shape, shape, overlap, object-outside-shape pixel counts, then
+        LC, OO, EA and L-nU (Sec. 6 and Sec. 6.1) at the current params."""
+        out = np.zeros((self.n_probs, 8), np.float64)
+        self._check(self.lib.collage_metrics(self.h, _stream(), out.ctypes.data_as(C.c_void_p)))
+        return out
+
     def sync(self):
         self._check(self.lib.collage_sync(self.h, _stream()))
 

@@ -54,6 +54,11 @@ struct collage_s {
   cudaStream_t aux_stream = nullptr;  // side branch of an iteration (the loss assembly)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // quality-metric scratch (allocated by collage_metrics)
+  uint8_t* met_obj = nullptr;
+  int* met_gcol = nullptr;
+  unsigned long long* met_cnt = nullptr;  // [5 * P]: 4 counts, then the distance sums
+  size_t met_pix = 0;
   std::string err;
   std::vector<void*> owned;      // fixed-size allocations
   std::vector<void*> level_bufs; // per-pixel / per-tile buffers, regrown with the level size
@@ -117,6 +122,9 @@ collage_s::~collage_s() {
   if (graph) cudaGraphExecDestroy(graph);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (aux_stream) cudaStreamDestroy(aux_stream);
+  if (met_obj) cudaFree(met_obj);
+  if (met_gcol) cudaFree(met_gcol);
+  if (met_cnt) cudaFree(met_cnt);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (h_ctl) cudaFreeHost(h_ctl);
@@ -157,6 +165,9 @@ extern "C" void collage_default_options(collage_options* o) {
   o->persistent = 1;
   o->use_graphs = 1;
   o->overlap_launches = 1;
+  o->force_kind = 0;
+  o->force_x = 0.5f;
+  o->force_y = 0.5f;
 }
 
 static std::string check_options(const collage_options& o) {
@@ -178,6 +189,8 @@ static std::string check_options(const collage_options& o) {
   if (o.segs_per_cubic < 1 || o.segs_per_cubic > 4096) return "segs_per_cubic must be in 1..4096";
   if (!(o.beta1 >= 0.0f && o.beta1 < 1.0f) || !(o.beta2 >= 0.0f && o.beta2 < 1.0f)) return "Adam betas must be in [0, 1)";
   if (!(o.s_min > 0.0f) || !(o.s_max >= o.s_min) || !is_finite_f(o.s_max)) return "need 0 < s_min <= s_max";
+  if (o.force_kind != 0 && o.force_kind != 1) return "force_kind must be 0 or 1";
+  if (!is_finite_f(o.force_x) || !is_finite_f(o.force_y)) return "force_x and force_y must be finite";
   return "";
 }
 
@@ -586,6 +599,9 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.L.beta = o.beta;
   d.L.gamma = o.gamma;
   d.L.delta = o.delta_down;
+  d.L.force_kind = o.force_kind;
+  d.L.fx = o.force_x;
+  d.L.fy = o.force_y;
   d.L.tau = o.tau;
   d.L.w_in = o.w_in;
   d.L.w_out = o.w_out;
@@ -939,6 +955,48 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   collage_status st = setup_level(h, h->level);
   if (st) return st;
   if (h_best_ms) *h_best_ms = best;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_metrics(collage_t h, void* stream, double* h_metrics) {
+  if (!h || !h_metrics) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t np = (size_t)h->d.total_pix;
+  if (np > h->met_pix) {
+    CK(h, cudaDeviceSynchronize());
+    if (h->met_obj) cudaFree(h->met_obj);
+    if (h->met_gcol) cudaFree(h->met_gcol);
+    h->met_obj = nullptr;
+    h->met_gcol = nullptr;
+    h->met_pix = 0;
+    CK(h, cudaMalloc(&h->met_obj, np));
+    CK(h, cudaMalloc(&h->met_gcol, sizeof(int) * np));
+    h->met_pix = np;
+  }
+  if (!h->met_cnt) CK(h, cudaMalloc(&h->met_cnt, sizeof(unsigned long long) * 5 * h->P));
+  CK(h, launch_adam_flush(h->d, s));
+  collage_status st = run_checked(h, s, kRender, nullptr, nullptr);
+  if (st) return st;
+  int max_res = 1;
+  for (int p = 0; p < h->P; ++p) max_res = std::max(max_res, h->res[p]);
+  CK(h, launch_metrics(h->d, s, h->met_obj, h->met_gcol, h->met_cnt, h->met_cnt + 4 * h->P, max_res));
+  std::vector<unsigned long long> c(5 * (size_t)h->P);
+  CK(h, cudaMemcpyAsync(c.data(), h->met_cnt, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  for (int p = 0; p < h->P; ++p) {
+    const double in = (double)c[4 * p], shape = (double)c[4 * p + 1], over = (double)c[4 * p + 2],
+                 out = (double)c[4 * p + 3], sum = (double)c[4 * h->P + p];
+    const double free_px = shape - in, r = (double)h->res[p];
+    double* m = h_metrics + 8 * p;
+    m[0] = in;
+    m[1] = shape;
+    m[2] = over;
+    m[3] = out;
+    m[4] = shape > 0 ? in / shape : 0.0;
+    m[5] = shape > 0 ? over / shape : 0.0;
+    m[6] = shape > 0 ? out / shape : 0.0;
+    m[7] = (in + out > 0 && free_px > 0) ? sum / free_px / (r * r) : 0.0;
+  }
   return COLLAGE_OK;
 }
 

@@ -33,6 +33,8 @@ constexpr int kHeavyNear = 24;    // a near pair with more segments near its til
 
 struct LossParams {
   float alpha, beta, gamma, delta;
+  int force_kind;               // 0: downward potential 1 - y; 1: |p - (fx, fy)|
+  float fx, fy;
   float tau, w_in, w_out;
   int n_dil;
   float dil_w[kMaxDil];
@@ -143,6 +145,12 @@ __device__ __forceinline__ void adam_update(const Dev& d, int g, int t, float4 g
   d.v[g] = v;
 }
 
+// Potential of the force term at the pixel centre (px, py), unit coordinates.
+__device__ __forceinline__ float force_potential(const LossParams& L, float px, float py) {
+  if (L.force_kind == 1) return hypotf(px - L.fx, py - L.fy);
+  return 1.0f - py;
+}
+
 // ---- programmatic dependent launch ----
 // With Dev::pdl set, the kernels of an iteration are launched with programmatic stream
 // serialisation: a kernel may be scheduled while its predecessor on the stream still runs.  Every
@@ -212,5 +220,8 @@ struct RasterOcc {
   int fwd_per_sm, bwd_per_sm, tile_per_sm, bwd_pairs_per_block, tiles_per_block;
 };
 void raster_occupancy(int tile, RasterOcc* o);
+// quality metrics after a render pass: counts [4 * n_probs] and squared-distance sums [n_probs]
+cudaError_t launch_metrics(const Dev& d, cudaStream_t s, uint8_t* obj, int* gcol,
+                           unsigned long long* cnt, unsigned long long* sums, int max_res);
 
 }  // namespace collage

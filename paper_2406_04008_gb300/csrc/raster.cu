@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
       // c^pad is tiny; so the side of the kink is taken from the counts in that case (exact)
       const bool over = nfull[k] >= 2 || (nfull[k] == 1 ? partial[k] : A > tau);
       lo += over ? fmaxf(A - tau, 0.0f) : 0.0f;
-      ld += (1.0f - ihat) * (1.0f - ((float)Y + 0.5f) / (float)res);
+      ld += (1.0f - ihat) * force_potential(d.L, ((float)X + 0.5f) / (float)res, ((float)Y + 0.5f) / (float)res);
       d.img_I[pix] = ihat;
       d.img_Pt[pix] = over ? -keept[k] : keept[k];  // the sign carries the side of the kink
       if (out_bw) out_bw[pix] = ihat;
@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
       const float py = (float)Y + 0.5f;
       // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
       const float gI = d.L.alpha * inv_np * 2.0f * W * (ihat - (1.0f - cov)) - d.L.gamma * gou -
-                       d.L.delta * inv_np * (1.0f - py / (float)res);
+                       d.L.delta * inv_np *
+                           force_potential(d.L, ((float)X + 0.5f) / (float)res, py / (float)res);
       const float gA = pt_s < 0.0f ? d.L.beta * inv_np : 0.0f;
       const float omc = Sfun(-x), cp = Sfun(xp);
       // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)

@@ -27,7 +27,8 @@ def paired(**kw):
     """(GPU option kwargs, oracle options) for the same loss configuration."""
     from oracle import oracle as O
     loss = dict(alpha=3e3, beta=8e4, gamma=5e-4, delta=0.0, tau=0.5, w_in=1.0, w_out=100.0,
-                pad_px=0.0, rho_px=1.0, n_dil=4, dil_weight=(1.0, 2.0, 3.0, 4.0))
+                pad_px=0.0, rho_px=1.0, n_dil=4, dil_weight=(1.0, 2.0, 3.0, 4.0),
+                force_kind=0, force_x=0.5, force_y=0.5)
     gpu_extra = {}
     for k, v in kw.items():
         if k in loss:
@@ -37,12 +38,14 @@ def paired(**kw):
     g = dict(alpha=loss["alpha"], beta=loss["beta"], gamma=loss["gamma"],
              delta_down=loss["delta"], tau=loss["tau"], w_in=loss["w_in"], w_out=loss["w_out"],
              pad_px=loss["pad_px"], rho_px=loss["rho_px"], n_dilations=loss["n_dil"],
-             dil_weight=list(loss["dil_weight"]))
+             dil_weight=list(loss["dil_weight"]), force_kind=loss["force_kind"],
+             force_x=loss["force_x"], force_y=loss["force_y"])
     g.update(gpu_extra)
     o = O.options(alpha=loss["alpha"], beta=loss["beta"], gamma=loss["gamma"],
                   delta=loss["delta"], tau=loss["tau"], w_in=loss["w_in"], w_out=loss["w_out"],
                   n_dil=loss["n_dil"], dil_weight=loss["dil_weight"], pad_px=loss["pad_px"],
-                  rho_px=loss["rho_px"])
+                  rho_px=loss["rho_px"], force_kind=loss["force_kind"], force_x=loss["force_x"],
+                  force_y=loss["force_y"])
     return g, o
 
 
@@ -83,4 +86,7 @@ def small_case(name):
         return W.config_problem(3, n_elems=120, grid=256), dict(pad_px=2.0), 256
     if name == "open150_force":
         return W.config_problem(5, n_elems=150, grid=240), dict(pad_px=1.0, delta=1e3), 240
+    if name == "mixed120_point_force":  # force towards a point (Sec. 5), off-centre
+        return (W.config_problem(3, n_elems=120, grid=256),
+                dict(pad_px=2.0, delta=300.0, force_kind=1, force_x=0.42, force_y=0.57), 256)
     raise KeyError(name)

@@ -30,7 +30,7 @@ def _run(env, prob, grid, opts, **gpu_extra):
     return col, terms.cpu().numpy()[0], grad.cpu().numpy(), ref, g, o
 
 
-CASES = ["disks16", "blobs40_ragged", "mixed120_pad2", "open150_force"]
+CASES = ["disks16", "blobs40_ragged", "mixed120_pad2", "open150_force", "mixed120_point_force"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -345,4 +345,68 @@ def test_full_batch_of_64_collages_matches_oracle(env):
                 raise AssertionError(f"collage {i} (n={n}, grid {res}): {ex}") from None
         off += n
         tile_base += ((res + tile - 1) // tile) ** 2
+    col.close()
+
+
+def _check_metrics(m, ref, amb):
+    """GPU metrics against the oracle's: pixel counts may differ only where the oracle's value
+    sits within rounding of a threshold (amb such pixels, plus two for overlap decisions)."""
+    tol = amb + 2
+    for k in range(4):
+        assert abs(m[k] - ref[k]) <= tol, (k, m[k], ref[k], tol)
+    for k in range(4, 7):
+        assert abs(m[k] - ref[k]) <= tol / max(ref[1], 1.0) + 1e-15, (k, m[k], ref[k])
+    if np.array_equal(m[:4], ref[:4]):
+        assert abs(m[7] - ref[7]) <= 1e-9 * ref[7] + 1e-15, (m[7], ref[7])
+    else:
+        assert abs(m[7] - ref[7]) <= 1e-3 * ref[7], (m[7], ref[7])
+
+
+@pytest.mark.parametrize("name", ["disks16", "mixed120_pad2", "open150_force"])
+def test_quality_metrics_match_oracle(env, name):
+    O, Collage = env
+    prob, opts, grid = U.small_case(name)
+    g, o = U.paired(**opts)
+    col = Collage(prob, level_res=[grid], **g)
+    m = col.metrics()[0]
+    sc = O.Scene(prob)
+    q0 = prob["params0"].astype(np.float64)
+    ref = sc.metrics(q0, grid, o)
+    ihat, _, covc = sc.render(q0, grid, o)
+    amb = int(((np.abs(ihat - 0.5) < 1e-5) | (np.abs(covc - 0.5) < 1e-5)).sum())
+    _check_metrics(m, ref, amb)
+    assert ref[0] > 0 and ref[1] > 0
+    col.close()
+
+
+@pytest.mark.slow
+def test_quality_metrics_full_size(env):
+    """The headline level (1000 elements at 1024^2) after a few steps, in the benchmark's launch
+    configuration, and the 64-collage batch (every collage)."""
+    O, Collage = env
+    prob = W.config_problem(3)
+    g, o = U.paired(pad_px=2.0)
+    col = Collage(prob, level_res=[1024], use_graphs=1, persistent=1, tile=0, **g)
+    col.autotune()
+    col.step(5)
+    q = col.get_params().cpu().numpy().astype(np.float64).reshape(-1)
+    m = col.metrics()[0]
+    sc = O.Scene(prob)
+    ref = sc.metrics(q, 1024, o)
+    ihat, _, covc = sc.render(q, 1024, o)
+    amb = int(((np.abs(ihat - 0.5) < 1e-5) | (np.abs(covc - 0.5) < 1e-5)).sum())
+    _check_metrics(m, ref, amb)
+    col.close()
+    probs = [W.config_problem(4, i) for i in range(64)]
+    gb, ob = U.paired()
+    col = Collage(probs, level_res=[1], use_graphs=1, persistent=1, tile=0, **gb)
+    mb = col.metrics()
+    for i in (0, 23, 63):
+        p = probs[i]
+        sc = O.Scene(p)
+        q0 = p["params0"].astype(np.float64)
+        ref = sc.metrics(q0, p["grid"], ob)
+        ihat, _, covc = sc.render(q0, p["grid"], ob)
+        amb = int(((np.abs(ihat - 0.5) < 1e-5) | (np.abs(covc - 0.5) < 1e-5)).sum())
+        _check_metrics(mb[i], ref, amb)
     col.close()

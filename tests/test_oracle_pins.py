@@ -363,6 +363,58 @@ def test_force_term_closed_form(oracle_mod):
     assert abs(g[3] - 2 * A * (1 - y)) / (2 * A * (1 - y)) < 2e-3
 
 
+def _point_potential(D, rr):
+    """Integral of |p - c| over a disk of radius rr whose centre lies at distance D from c, and
+    its derivatives in D and rr, by Gauss-Legendre quadrature in polar coordinates about the
+    disk's centre (independent of the oracle)."""
+    from numpy.polynomial.legendre import leggauss
+    xr, wr = leggauss(64)
+    xt, wt = leggauss(128)
+    rho = 0.5 * rr * (xr + 1.0)
+    th = np.pi * (xt + 1.0)
+    P, TH = np.meshgrid(rho, th, indexing="ij")
+    Wt = np.outer(wr * 0.5 * rr, wt * np.pi)
+    dist = np.sqrt(D * D + P * P + 2 * D * P * np.cos(TH))
+    phi = np.sum(Wt * dist * P)
+    dphi_dD = np.sum(Wt * (D + P * np.cos(TH)) / np.maximum(dist, 1e-300) * P)
+    # d/drr: the boundary integral of |p - c| over the circle of radius rr
+    ring = np.sqrt(D * D + rr * rr + 2 * D * rr * np.cos(th))
+    dphi_dr = np.sum(wt * np.pi * ring) * rr
+    return phi, dphi_dD, dphi_dr
+
+
+def test_point_force_closed_form(oracle_mod):
+    """Force towards a point (Sec. 5, force attraction): for a disk the term is the integral of
+    |p - c| over the disk, whose value and derivatives come from quadrature; at D = 0 the value is
+    2 pi r^3 / 3 and the translation gradient vanishes by symmetry."""
+    R, r = 512, 0.12
+    c = (0.5, 0.5)
+    rr = float(np.float32(r))
+    for D in (0.0, 0.2):
+        def run(dx, dy):  # the element and the force point move together
+            o = oracle_mod.options(alpha=0, beta=0, gamma=0, delta=1.0, force_kind=1,
+                                   force_x=c[0] + dx, force_y=c[1] + dy)
+            q = (c[0] + D + dx, c[1] + dy, 0.0, 1.0)
+            prob = W.make_problem([(1, W.regular_polygon(r, 1024), 0.0)], _square_ring(-1, 2), [q], R)
+            out = oracle_mod.Scene(prob).eval(_params(q), R, o)
+            return np.concatenate([[out["terms"][3]], out["grad_a"]])
+
+        res = _shift_average(run, R)
+        phi, dD, dr = _point_potential(D, rr)
+        # the smoothstep filter adds 0.6 (rho / r)^2 relative at a circle centred on c (its first
+        # moment across the edge); the bound leaves room for it
+        assert abs(res[0] - phi) / phi < 2.5e-4, (D, res[0], phi)
+        g = res[1:]
+        scale = abs(dr)
+        assert abs(g[0] - dD) < 3e-3 * scale, (D, g[0], dD)
+        assert abs(g[1]) < 3e-3 * scale
+        assert abs(g[3] - dr * rr) / (dr * rr) < 3e-3, (D, g[3], dr * rr)  # radius = s r
+        if D == 0.0:
+            assert abs(phi - 2 * np.pi * rr ** 3 / 3) / phi < 1e-9
+            g0 = run(0.0, 0.0)[1:]  # centred on a pixel corner: mirror-symmetric sampling
+            assert abs(g0[0]) < 1e-9 * scale and abs(g0[1]) < 1e-9 * scale
+
+
 def _small_scene(oracle_mod, seed=41, n=6, R=96):
     rng = W.PCG32(seed)
     els, params = [], []
@@ -380,6 +432,14 @@ def _small_scene(oracle_mod, seed=41, n=6, R=96):
 def test_gradient_routes_agree(oracle_mod):
     sc, q = _small_scene(oracle_mod)
     out = sc.eval(q, 96, oracle_mod.options(pad_px=1.0, delta=50.0))
+    np.testing.assert_allclose(out["grad_a"], out["grad_b"], rtol=0,
+                               atol=1e-10 * np.abs(out["grad_a"]).max())
+
+
+def test_gradient_routes_agree_with_point_force(oracle_mod):
+    sc, q = _small_scene(oracle_mod, seed=43)
+    out = sc.eval(q, 96, oracle_mod.options(pad_px=1.0, delta=50.0, force_kind=1, force_x=0.4,
+                                            force_y=0.55))
     np.testing.assert_allclose(out["grad_a"], out["grad_b"], rtol=0,
                                atol=1e-10 * np.abs(out["grad_a"]).max())
 
@@ -463,3 +523,61 @@ def test_bins_rule_equals_brute_force_and_is_conservative(oracle_mod, tile):
         tiles = set(t1[e1 == e].tolist())
         need = {(i // R // tile) * nt + (i % R) // tile for i in live}
         assert need <= tiles, (e, sorted(need - tiles))
+
+
+# ------------------------------------------------------------------------------------------------
+# Quality metrics (Sec. 6 "Metrics of Collage Quality"; L-nU of the Sec. 6.1 ablation)
+def _disk_scene_masks(disks, box, R):
+    """Object, overlap and shape masks of disks in a square container, from the circles' own
+    signed distances (numpy), with the renderer's composite O = 1 - prod(1 - S(sd/rho))."""
+    yy, xx = np.mgrid[0:R, 0:R]
+    px, py = (xx + 0.5) / R, (yy + 0.5) / R
+    rho = 1.0 / R
+
+    def S(x):
+        x = np.clip(x, -1, 1)
+        return 0.5 + 0.75 * x - 0.25 * x ** 3
+
+    keep = np.ones((R, R))
+    n_in = np.zeros((R, R), int)
+    for cx, cy, r in disks:
+        sd = r - np.hypot(px - cx, py - cy)
+        keep *= 1 - S(sd / rho)
+        n_in += sd >= 0
+    lo, hi = box
+    shape = (px >= lo) & (px <= hi) & (py >= lo) & (py <= hi)
+    return 1 - keep >= 0.5, n_in >= 2, shape
+
+
+def test_metrics_counts_match_masks(oracle_mod):
+    R = 200
+    disks = [(0.4, 0.5, 0.15), (0.62, 0.47, 0.12), (0.3, 0.28, 0.05)]
+    box = (0.2, 0.7)
+    prob = W.make_problem([(1, W.regular_polygon(r, 2048), 0.0) for _, _, r in disks],
+                          _square_ring(*box), [(cx, cy, 0.0, 1.0) for cx, cy, _ in disks], R)
+    out = oracle_mod.Scene(prob).metrics(_params([(cx, cy, 0.0, 1.0) for cx, cy, _ in disks]), R,
+                                         oracle_mod.options())
+    obj, over, shape = _disk_scene_masks(disks, box, R)
+    assert out[0] == (obj & shape).sum() and out[1] == shape.sum()
+    assert out[2] == over.sum() and out[3] == (obj & ~shape).sum()
+    assert out[3] > 0 and out[2] > 0  # the case exercises both
+    assert abs(out[4] - out[0] / out[1]) < 1e-15 and abs(out[5] - out[2] / out[1]) < 1e-15
+    assert abs(out[6] - out[3] / out[1]) < 1e-15
+
+
+def test_layout_nonuniformity_matches_brute_force(oracle_mod):
+    R = 48
+    rng = W.PCG32(91)
+    disks = [(0.25 + 0.5 * rng.uniform(), 0.25 + 0.5 * rng.uniform(), 0.03 + 0.04 * rng.uniform())
+             for _ in range(5)]
+    box = (0.1, 0.9)
+    prob = W.make_problem([(1, W.regular_polygon(r, 2048), 0.0) for _, _, r in disks],
+                          _square_ring(*box), [(cx, cy, 0.0, 1.0) for cx, cy, _ in disks], R)
+    out = oracle_mod.Scene(prob).metrics(_params([(cx, cy, 0.0, 1.0) for cx, cy, _ in disks]), R,
+                                         oracle_mod.options())
+    obj, _, shape = _disk_scene_masks(disks, box, R)
+    assert out[0] == (obj & shape).sum() and out[3] == (obj & ~shape).sum()
+    oy, ox = np.nonzero(obj)
+    fy, fx = np.nonzero(shape & ~obj)
+    d2 = ((fy[:, None] - oy[None, :]) ** 2 + (fx[:, None] - ox[None, :]) ** 2).min(1)
+    assert abs(out[7] - d2.mean() / R ** 2) <= 1e-12 * out[7]
