@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
       continue;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
       sO[(idx / S) * SP + idx % S] =
           (X >= 0 && Y >= 0 && X < res && Y < res) ? to_fixed<K>(1.0f - d.img_I[pb + (long long)Y * res + X]) : 0u;
@@ -239,7 +240,8 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_bwd(Dev d) {
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
     __syncthreads();
-    for (int idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
       const bool in = X >= 0 && Y >= 0 && X < res && Y < res;
       const long long pix = pb + (long long)Y * res + X;

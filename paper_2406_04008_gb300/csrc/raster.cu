@@ -107,7 +107,6 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   __shared__ float2 s_seg2[kNearCap];
   __shared__ float s_slope[kNearCap];
   __shared__ int s_idx[kNearCap];
-  __shared__ float2 s_xt[kNearCap * T];  // per (near segment, row): crossing x and direction
   __shared__ float4 s_allA[kStageSegs];   // the whole outline (when it has <= kStageSegs segments)
   __shared__ float2 s_allB[kStageSegs];
   __shared__ float s_allS[kStageSegs];
@@ -221,35 +220,17 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
       __syncthreads();
       const int total_near = s_near;
       const int cn = min(kNearCap, total_near - base);
-      if (closed && cn > 0) {
-        // crossings of the pixel rows with the near segments.  Row r crosses segment j when its
-        // end points lie on different sides of the row (the half-open test, on the same dy the
-        // pixels form); the crossing counts for a pixel left of the crossing x, +1 upward and -1
-        // downward.  (This is the sign of cross(e, p - a) read as a comparison of x: the two can
-        // differ only for a pixel within rounding of the segment, where sd ~ 0 and c ~ 1/2 on
-        // either side.)
-        for (int e = threadIdx.x; e < cn * T; e += NT) {
-          const int j = e / T, r = e % T;
-          const float4 sa = s_seg[j];
-          const float bxy = s_seg2[j].x;
-          const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
-          const bool a_le = yr - sa.y >= 0.0f, b_le = yr - bxy >= 0.0f;
-          float2 xt = make_float2(-FLT_MAX, __int_as_float(0));
-          if (a_le != b_le) xt = make_float2(fmaf(yr - sa.y, s_slope[j], sa.x), __int_as_float(a_le ? 1 : -1));
-          s_xt[e] = xt;
-        }
-        __syncthreads();
-      }
       if (any && cn > 0) {
 #pragma unroll 2
         for (int j = 0; j < cn; ++j) {
           const float4 s = s_seg[j];
-          const float ie = s_seg2[j].y;
+          const float2 s2 = s_seg2[j];
+          const float sl = s_slope[j];
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
             if (!act[k]) continue;
             const float wx = dx[k] - s.x, wy = dy[k] - s.y;
-            const float t = __saturatef((wx * s.z + wy * s.w) * ie);
+            const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
             const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
             const float d2 = fmaf(qx, qx, qy * qy);
             if (d2 < best[k]) {
@@ -257,8 +238,12 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
               bj[k] = j;
             }
             if (closed) {
-              const float2 xt = s_xt[j * T + (threadIdx.x + k * NT) / T];
-              if (dx[k] < xt.x) wn[k] += __float_as_int(xt.y);
+              // the row crosses the segment when its end points lie on different sides of it
+              // (half-open); the crossing counts when it lies right of the pixel, +1 upward,
+              // -1 downward.  (x of the crossing instead of the sign of cross(e, p - a): the two
+              // differ only for a pixel within rounding of the segment, where sd ~ 0.)
+              const bool a_le = wy >= 0.0f, b_le = dy[k] - s2.x >= 0.0f;
+              if (a_le != b_le && dx[k] < fmaf(wy, sl, s.x)) wn[k] += a_le ? 1 : -1;
             }
           }
         }
