@@ -50,6 +50,8 @@ struct collage_s {
   long long* d_prob_pix_base = nullptr;
   int* ctl = nullptr;        // device: status, step, total_pairs, pending, 4 work counters
   int* h_ctl = nullptr;      // pinned mirror
+  bool ctl_current = false;  // h_ctl[1] (the step count) is the device's: no step was enqueued
+                             // since the last read
   cudaStream_t cap_stream = nullptr;
   cudaStream_t aux_stream = nullptr;  // side branch of an iteration (the loss assembly)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -321,6 +323,7 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
 static collage_status read_ctl(collage_t h, cudaStream_t s) {
   CK(h, cudaMemcpyAsync(h->h_ctl, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
+  h->ctl_current = true;
   return COLLAGE_OK;
 }
 
@@ -746,7 +749,7 @@ extern "C" collage_status collage_step(collage_t h, void* stream, int n_iters) {
   if (n_iters < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "n_iters must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   int remaining = n_iters;
-  collage_status st = remaining > 0 ? read_ctl(h, s) : COLLAGE_OK;
+  collage_status st = remaining > 0 && !h->ctl_current ? read_ctl(h, s) : COLLAGE_OK;
   if (st) return st;
   for (int attempt = 0; remaining > 0 && attempt < 8; ++attempt) {
     const int step0 = h->h_ctl[1];
@@ -765,6 +768,7 @@ extern "C" collage_status collage_step(collage_t h, void* stream, int n_iters) {
 extern "C" collage_status collage_step_async(collage_t h, void* stream, int n_iters) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
   if (n_iters < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "n_iters must be >= 0");
+  if (n_iters > 0) h->ctl_current = false;
   return enqueue_steps(h, (cudaStream_t)stream, n_iters);
 }
 
@@ -785,20 +789,47 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
                                             const float* h_params_in, float* h_params_out,
                                             float* h_loss_out) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  if (n_iters < 0) return fail(h, COLLAGE_ERR_INVALID_ARG, "n_iters must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
+  collage_status st = h->ctl_current ? COLLAGE_OK : read_ctl(h, s);
+  if (st) return st;
+  const int step0 = h->h_ctl[1];
   if (h_params_in) {
     CK(h, launch_adam_flush(h->d, s));  // the step belongs to the old params
     CK(h, cudaMemcpyAsync(h->d.q, h_params_in, sizeof(float4) * h->N, cudaMemcpyHostToDevice, s));
   }
-  collage_status st = collage_step(h, stream, n_iters);
+  // one host round trip when nothing overflows: the steps, the copies out and the status word are
+  // enqueued together and the stream is synchronised once
+  st = enqueue_steps(h, s, n_iters);
   if (st) return st;
-  if (h_params_out) {
-    CK(h, launch_adam_flush(h->d, s));
-    CK(h, cudaMemcpyAsync(h_params_out, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToHost, s));
+  auto copy_out = [&]() -> collage_status {
+    if (h_params_out) {
+      CK(h, launch_adam_flush(h->d, s));
+      CK(h, cudaMemcpyAsync(h_params_out, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToHost, s));
+    }
+    if (h_loss_out)
+      CK(h, cudaMemcpyAsync(h_loss_out, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToHost, s));
+    return COLLAGE_OK;
+  };
+  st = copy_out();
+  if (st) return st;
+  st = read_ctl(h, s);
+  if (st) return st;
+  const int status = h->h_ctl[0], done = h->h_ctl[1] - step0;
+  if (!(status & (kStatusOverflow | kStatusBadParam | kStatusInternal)) && done == n_iters &&
+      (size_t)h->h_ctl[2] * 4 <= h->pair_cap * 3)
+    return COLLAGE_OK;
+  // an overflow (or a status to report): the synchronous path regrows and runs the rest
+  bool over = false;
+  st = check_and_grow(h, s, &over);
+  if (st) return st;
+  if (done < n_iters) {
+    st = collage_step(h, stream, n_iters - done);
+    if (st) return st;
+    st = copy_out();
+    if (st) return st;
+    CK(h, cudaStreamSynchronize(s));
   }
-  if (h_loss_out)
-    CK(h, cudaMemcpyAsync(h_loss_out, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToHost, s));
-  CK(h, cudaStreamSynchronize(s));
   return COLLAGE_OK;
 }
 
@@ -856,6 +887,7 @@ extern "C" collage_status collage_set_state(collage_t h, void* stream, const flo
   CK(h, cudaMemcpyAsync(h->d.step, &h->h_ctl[1], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(h, cudaMemsetAsync(h->d.pending, 0, sizeof(int), s));  // the state replaces everything
   CK(h, cudaStreamSynchronize(s));
+  h->ctl_current = true;
   return COLLAGE_OK;
 }
 

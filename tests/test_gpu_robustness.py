@@ -162,6 +162,32 @@ def test_step_host_round_trip(Collage):
     col.close()
 
 
+def test_step_host_recovers_an_overflow(Collage):
+    """Host-buffer steps whose params outgrow the bins: the one-round-trip path detects the
+    overflow and the synchronous one finishes, so exactly n iterations run."""
+    prob, opts, grid = _case()
+    g, _ = U.paired(**opts)
+    kw = dict(level_res=[grid], deterministic=1, **g)
+    col = Collage(prob, **kw)
+    q = np.asarray(prob["params0"], np.float32).reshape(-1, 4).copy()
+    q[:, 3] *= 4.0
+    pout, lout = col.step_host(3, params_in=q.reshape(-1))
+    _, step, _ = col.get_state()
+    assert step == 3
+    prob2 = dict(prob)
+    prob2["params0"] = q.reshape(-1)
+    ref = Collage(prob2, **kw)
+    ref.step(3)
+    assert np.array_equal(pout, ref.get_params().reshape(-1).cpu().numpy())
+    assert np.array_equal(lout, ref.loss().reshape(-1).cpu().numpy())
+    # further calls take the one-round-trip path and stay equal to synchronous steps
+    pout2, _ = col.step_host(2)
+    ref.step(2)
+    assert np.array_equal(pout2, ref.get_params().reshape(-1).cpu().numpy())
+    col.close()
+    ref.close()
+
+
 def test_fp32_peak_is_plausible(Collage):
     """The FMA-chain measurement lands between half and 1.05x of SMs x 128 lanes x 2 x max clock."""
     import ctypes as C
