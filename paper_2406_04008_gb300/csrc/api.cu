@@ -306,6 +306,7 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   Dev& d = h->d;
   CK(h, dmalloc(h->pair_bufs, d.pair_elem, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_tile, cap));
+  CK(h, dmalloc(h->pair_bufs, d.pair_txy, cap));
   CK(h, dmalloc(h->pair_bufs, d.live_list, cap));
   CK(h, dmalloc(h->pair_bufs, d.near_list, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_cls, cap));

@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
             cls = s_near[i] ? kPairNear : (closed && s_wind[i] != 0 ? kPairIn : kPairOut);
             d.pair_elem[pos] = g;
             d.pair_tile[pos] = t;
+            d.pair_txy[pos] = (tx_lo + i % cw) | ((ty_lo + i / cw) << 16);
             d.pair_cls[pos] = cls;
             if (cls != kPairNear && d.deterministic) d.partial[pos] = make_float4(0.f, 0.f, 0.f, 0.f);
           }

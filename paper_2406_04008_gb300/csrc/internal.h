@@ -82,6 +82,7 @@ struct Dev {
   int cap;                      // pair capacity
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
   int* pair_tile;               // [cap] tile of each pair slot
+  int* pair_txy;                // [cap] the tile's column | row << 16 within its problem
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
   int* near_list;               // [cap] slots of the near pairs (the distance kernel's work list):
                                 //   heavy ones from the front, light ones from the back

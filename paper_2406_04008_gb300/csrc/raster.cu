@@ -123,9 +123,8 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   for (int i = blockIdx.x, it = 0; i < n_near; ++it) {
     if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
     const int slot = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
-    const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
-    int p, tx, ty, res;
-    tile_coords(d, tile, T, p, tx, ty, res);
+    const int g = d.pair_elem[slot], txy = d.pair_txy[slot];
+    const int tx = txy & 0xffff, ty = txy >> 16, p = d.elem_prob[g], res = d.prob_res[p];
     const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
     const bool closed = d.elem_closed[g] != 0;
     const int ns = closed ? nv : nv - 1;
@@ -409,9 +408,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
   const int n_live = d.work[1];  // pairs without a gradient-carrying pixel are not listed
   for (int i = blockIdx.x * kPairWarps + wid; i < n_live; i += gridDim.x * kPairWarps) {
     const int slot = d.live_list[i];
-    const int g = d.pair_elem[slot], tile = d.pair_tile[slot];
-    int p, tx, ty, res;
-    tile_coords(d, tile, T, p, tx, ty, res);
+    const int g = d.pair_elem[slot], txy = d.pair_txy[slot];
+    const int tx = txy & 0xffff, ty = txy >> 16, p = d.elem_prob[g], res = d.prob_res[p];
     const long long pixbase = d.prob_pix_base[p];
     const float inv_np = 1.0f / ((float)res * (float)res);
     const int v0 = d.elem_voff[g];
