@@ -84,9 +84,10 @@ struct Dev {
   int* pair_tile;               // [cap] tile of each pair slot
   int* pair_txy;                // [cap] the tile's column | row << 16 within its problem
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
-  int* near_list;               // [cap] slots of the near pairs (the distance kernel's work list):
+  int4* near_list;              // [cap] near pairs (slot, element, tile column | row << 16, 0), the
+                                //   distance kernel's work list:
                                 //   heavy ones from the front, light ones from the back
-  int* live_list;               // [cap] slots of the pairs with some non-saturated pixel
+  int4* live_list;              // [cap] pairs with some non-saturated pixel, as near_list
                                 //   (the adjoint's work list; order depends on atomics)
   int* pair_sorted;             // [cap] each tile's elements in increasing element order
   int* pair_slot;               // [cap] the pair slot of each pair_sorted entry

@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   __shared__ int s_next[2];
   for (int i = blockIdx.x, it = 0; i < n_near; ++it) {
     if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
-    const int slot = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
-    const int g = d.pair_elem[slot], txy = d.pair_txy[slot];
+    const int4 rec = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
+    const int slot = rec.x, g = rec.y, txy = rec.z;
     const int tx = txy & 0xffff, ty = txy >> 16, p = d.elem_prob[g], res = d.prob_res[p];
     const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
     const bool closed = d.elem_closed[g] != 0;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
     }
     live = __syncthreads_or(live);
     if (threadIdx.x == 0) {
-      if (live) d.live_list[atomicAdd(&d.work[1], 1)] = slot;
+      if (live) d.live_list[atomicAdd(&d.work[1], 1)] = rec;
       else if (d.deterministic) d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     i = s_next[it & 1];
@@ -407,8 +407,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int n_live = d.work[1];  // pairs without a gradient-carrying pixel are not listed
   for (int i = blockIdx.x * kPairWarps + wid; i < n_live; i += gridDim.x * kPairWarps) {
-    const int slot = d.live_list[i];
-    const int g = d.pair_elem[slot], txy = d.pair_txy[slot];
+    const int4 rec = d.live_list[i];
+    const int slot = rec.x, g = rec.y, txy = rec.z;
     const int tx = txy & 0xffff, ty = txy >> 16, p = d.elem_prob[g], res = d.prob_res[p];
     const long long pixbase = d.prob_pix_base[p];
     const float inv_np = 1.0f / ((float)res * (float)res);
