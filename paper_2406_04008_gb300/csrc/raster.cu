@@ -73,6 +73,7 @@ __device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, floa
 constexpr int kSegCap = 1024;   // container segments staged per chunk
 constexpr int kNearCap = 64;    // near segments staged per chunk of one (tile, element) pair
 constexpr int kStageSegs = 128; // outlines up to this many segments are staged whole per pair
+constexpr int kRowCross = 16;   // crossings listed per pixel row of a pair
 constexpr int kPairWarps = 4;   // pairs per block of the per-pair adjoint (one per warp)
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
 
@@ -98,6 +99,19 @@ __device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& 
 // near crossings; if no near segment is within m the coverage is saturated (0 or 1, as the full
 // loop would give) and sd = +-1e30, else the near minimum is the true distance.
 // ------------------------------------------------------------------------------------------------
+// Winding number of a point (element frame) over every segment of an outline: the crossing test of
+// the distance kernel applied to all segments (the far ones are well conditioned).
+__device__ __noinline__ int winding_all(const Dev& d, int v0, int ns, float px, float py) {
+  int w = 0;
+  for (int j = 0; j < ns; ++j) {
+    const float4 sa = d.segA[v0 + j];
+    const float wy = py - sa.y;
+    const bool a_le = wy >= 0.0f, b_le = py - d.segB[v0 + j].x >= 0.0f;
+    if (a_le != b_le && px < fmaf(wy, d.segS[v0 + j], sa.x)) w += a_le ? 1 : -1;
+  }
+  return w;
+}
+
 template <int T, int NT>
 __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d) {
   pdl_enter();
@@ -111,6 +125,9 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
   __shared__ float2 s_allB[kStageSegs];
   __shared__ float s_allS[kStageSegs];
   __shared__ int s_back[T];
+  __shared__ float s_rx[T][kRowCross];  // per pixel row: x of its crossings with near segments
+  __shared__ signed char s_rd[T][kRowCross];  // and their direction
+  __shared__ int s_rc[T];
   __shared__ int s_near;
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
@@ -198,7 +215,10 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
         if (lane == 0) s_near = cnt;
       } else if (base == 0 && closed) {
         // winding backdrop of the far segments right of the tile
-        for (int r = threadIdx.x - 32; r < T; r += NT - 32) s_back[r] = 0;
+        for (int r = threadIdx.x - 32; r < T; r += NT - 32) {
+          s_back[r] = 0;
+          s_rc[r] = 0;
+        }
         asm volatile("bar.sync 1, %0;" ::"r"(NT - 32));
         // the rows' dy as the pixels form them: non-decreasing in the row, so a segment whose y
         // range misses [first row, last row] crosses no row's ray
@@ -219,30 +239,41 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
       __syncthreads();
       const int total_near = s_near;
       const int cn = min(kNearCap, total_near - base);
+      if (closed && cn > 0) {
+        // the crossings of the pixel rows with the chunk's near segments, listed per row.  Row r
+        // crosses segment j when its end points lie on different sides of the row (half-open, on
+        // the dy the pixels form); the crossing counts for a pixel left of its x, +1 upward and
+        // -1 downward.  (x of the crossing instead of the sign of cross(e, p - a): the two differ
+        // only for a pixel within rounding of the segment, where sd ~ 0 and c ~ 1/2 either way.)
+        for (int e = threadIdx.x; e < cn * T; e += NT) {
+          const int j = e / T, r = e % T;
+          const float4 sa = s_seg[j];
+          const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
+          const bool a_le = yr - sa.y >= 0.0f, b_le = yr - s_seg2[j].x >= 0.0f;
+          if (a_le != b_le) {
+            const int q = atomicAdd(&s_rc[r], 1);
+            if (q < kRowCross) {
+              s_rx[r][q] = fmaf(yr - sa.y, s_slope[j], sa.x);
+              s_rd[r][q] = a_le ? 1 : -1;
+            }
+          }
+        }
+      }
       if (any && cn > 0) {
 #pragma unroll 2
         for (int j = 0; j < cn; ++j) {
           const float4 s = s_seg[j];
-          const float2 s2 = s_seg2[j];
-          const float sl = s_slope[j];
+          const float ie = s_seg2[j].y;
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
             if (!act[k]) continue;
             const float wx = dx[k] - s.x, wy = dy[k] - s.y;
-            const float t = __saturatef((wx * s.z + wy * s.w) * s2.y);
+            const float t = __saturatef((wx * s.z + wy * s.w) * ie);
             const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
             const float d2 = fmaf(qx, qx, qy * qy);
             if (d2 < best[k]) {
               best[k] = d2;
               bj[k] = j;
-            }
-            if (closed) {
-              // the row crosses the segment when its end points lie on different sides of it
-              // (half-open); the crossing counts when it lies right of the pixel, +1 upward,
-              // -1 downward.  (x of the crossing instead of the sign of cross(e, p - a): the two
-              // differ only for a pixel within rounding of the segment, where sd ~ 0.)
-              const bool a_le = wy >= 0.0f, b_le = dy[k] - s2.x >= 0.0f;
-              if (a_le != b_le && dx[k] < fmaf(wy, sl, s.x)) wn[k] += a_le ? 1 : -1;
             }
           }
         }
@@ -255,13 +286,24 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d
       }
       if (total_near <= base + kNearCap) break;
     }
+    if (closed) __syncthreads();  // the row crossing lists are complete
     float2* sv = d.saved + (size_t)slot * NP;
     bool live = false;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       float sd = -kFar;
+      if (act[k] && closed) {
+        const int row = (threadIdx.x + k * NT) / T, rc = s_rc[row];
+        if (rc <= kRowCross) {
+          wn[k] = s_back[row];
+          for (int q = 0; q < rc; ++q)
+            if (dx[k] < s_rx[row][q]) wn[k] += s_rd[row][q];
+        } else {  // a row crossing the outline more often than the list holds: all segments
+          wn[k] = winding_all(d, v0, ns, dx[k], dy[k]);
+        }
+      }
       if (act[k]) {
-        const int w = closed ? wn[k] + s_back[(threadIdx.x + k * NT) / T] : 0;
+        const int w = closed ? wn[k] : 0;
         if (best[k] < mrg2) {
           const float dist = sqrtf(best[k]);
           sd = closed ? (w != 0 ? dist : -dist) : hwpx - dist;
