@@ -45,9 +45,9 @@ constexpr int kFlagHalo = 2;  // ... or somewhere within the halo of the largest
 __host__ __device__ constexpr int dil_r(int k) { return 2 + 3 * k; }  // (5 + 6k - 1) / 2
 __host__ __device__ constexpr int hrows(int k) { return kDT + 2 * dil_r(k); }
 __host__ __device__ constexpr int hbase(int k) { return k == 0 ? 0 : hbase(k - 1) + hrows(k - 1); }
-__host__ __device__ constexpr int qbits(int w) {
+__host__ __device__ constexpr int qbits(int w) {  // at most 23: bits 24..31 carry the B_k < 1 mask
   int q = 0;
-  while (q < 30 && ((unsigned long long)(w * w + w) << (q + 1)) < (1ull << 32)) ++q;
+  while (q < 23 && ((unsigned long long)(w * w + w) << (q + 1)) < (1ull << 32)) ++q;
   return q;
 }
 
@@ -126,13 +126,13 @@ struct OccSrc {  // occupancy O of the staged region, the same for every kernel
   __device__ uint32_t operator()(int, int rr, int cc) const { return sO[rr * SP + cc]; }
 };
 
-struct GSrc {  // G_k = M_C (1 - O) where B_k < 1, else 0
+struct GSrc {  // G_k = M_C (1 - O) where B_k < 1, else 0; the staged word holds the fixed-point
+               // M_C (1 - O) in bits 0..23 and the B_k < 1 bits from bit 24 on (one load per use)
   const uint32_t* sM;
-  const uint8_t* sMask;
   int SP;
   __device__ uint32_t operator()(int k, int rr, int cc) const {
-    const int i = rr * SP + cc;
-    return ((sMask[i] >> k) & 1u) ? sM[i] : 0u;
+    const uint32_t x = sM[rr * SP + cc];
+    return ((x >> (24 + k)) & 1u) ? (x & 0xffffffu) : 0u;
   }
 };
 
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kDThreads, 5) k_dilate_bwd(Dev d) {
+__global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
   pdl_enter();
   constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
   constexpr float inv_q = 1.0f / (float)(1u << Q);
@@ -232,7 +232,6 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_bwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   uint32_t* sM = sm;
   uint32_t* H = sM + S * SP;
-  uint8_t* sMask = reinterpret_cast<uint8_t*>(H + DilGeom<K>::HR * kHP);
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
     if (!(dil_flags(d, dt) & kFlagHalo)) continue;  // G = 0 over the tile and its halo
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
@@ -246,11 +245,10 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_bwd(Dev d) {
       const bool in = X >= 0 && Y >= 0 && X < res && Y < res;
       const long long pix = pb + (long long)Y * res + X;
       const int si = (idx / S) * SP + idx % S;
-      sM[si] = in ? to_fixed<K>(d.dil_m[pix]) : 0u;
-      sMask[si] = in ? d.dil_mask[pix] : (uint8_t)0;
+      sM[si] = in ? to_fixed<K>(d.dil_m[pix]) | ((uint32_t)d.dil_mask[pix] << 24) : 0u;
     }
     __syncthreads();
-    hsums_all<K>(GSrc{sM, sMask, SP}, H);
+    hsums_all<K>(GSrc{sM, SP}, H);
     __syncthreads();
     for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
       const int c = it % kDT, r0 = (it / kDT) * kVRows;
@@ -401,8 +399,8 @@ __global__ void k_adam_flush(Dev d) {
 
 static size_t dilate_smem(int K, bool backward) {
   const int S = kDT + 2 * dil_r(K - 1), SP = S | 1;
-  size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP;
-  if (backward) f += ((size_t)S * SP + 3) / 4;  // mask bytes
+  (void)backward;  // the backward pass packs its masks into the staged words
+  const size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP;
   return f * sizeof(uint32_t);
 }
 
