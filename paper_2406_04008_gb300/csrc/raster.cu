@@ -113,7 +113,7 @@ __device__ __noinline__ int winding_all(const Dev& d, int v0, int ns, float px, 
 }
 
 template <int T, int NT>
-__global__ void __launch_bounds__(NT, NT == 64 ? 24 : 1024 / NT) k_pair_sd(Dev d) {
+__global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d) {
   pdl_enter();
   constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
   static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
