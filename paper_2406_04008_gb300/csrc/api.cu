@@ -369,6 +369,8 @@ static collage_status setup_level(collage_t h, int level) {
     CK(h, dmalloc(h->level_bufs, d.lossA, nt));
     CK(h, dmalloc(h->level_bufs, d.lossU, nd));
     CK(h, dmalloc(h->level_bufs, d.dtile_flags, nd));
+    CK(h, dmalloc(h->level_bufs, d.dtile_list, 2 * nd));
+    CK(h, dmalloc(h->level_bufs, d.dtile_n, 2));
     h->pix_cap = np;
     h->tile_cap = nt;
     h->dtile_cap = nd;
@@ -382,6 +384,13 @@ static collage_status setup_level(collage_t h, int level) {
   cudaStream_t s = h->cap_stream;
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));  // clear latched status
   CK(h, launch_container(d, s));
+  // the distribution term's kernels visit only the tiles listed by the flags; every other tile
+  // keeps the zeros written here for the whole level
+  CK(h, cudaMemsetAsync(d.dtile_n, 0, 2 * sizeof(int), s));
+  CK(h, cudaMemsetAsync(d.gOu, 0, sizeof(float) * (size_t)d.total_pix, s));
+  CK(h, cudaMemsetAsync(d.dil_m, 0, sizeof(float) * (size_t)d.total_pix, s));
+  CK(h, cudaMemsetAsync(d.dil_mask, 0, (size_t)d.total_pix, s));
+  CK(h, cudaMemsetAsync(d.lossU, 0, sizeof(float) * (size_t)d.total_dtiles, s));
   CK(h, launch_dtile_flags(d, s));
   // size the pair buffers from the current params: count with an unbounded capacity
   CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));

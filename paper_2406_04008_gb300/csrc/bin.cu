@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
         lb = __shfl_sync(0xffffffffu, lb, 0);
         const unsigned below = (1u << lane) - 1u;
         if (near) {
-          const int4 rec = make_int4(pos, g, (tx_lo + i % cw) | ((ty_lo + i / cw) << 16), 0);
+          const int4 rec = make_int4(pos, g, (tx_lo + i % cw) | ((ty_lo + i / cw) << 16), p);
           if (heavy) d.near_list[hb + __popc(bh & below)] = rec;
           else d.near_list[d.cap - 1 - (lb + __popc(bl & below))] = rec;
         }

@@ -84,7 +84,7 @@ struct Dev {
   int* pair_tile;               // [cap] tile of each pair slot
   int* pair_txy;                // [cap] the tile's column | row << 16 within its problem
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
-  int4* near_list;              // [cap] near pairs (slot, element, tile column | row << 16, 0), the
+  int4* near_list;              // [cap] near pairs (slot, element, tile column | row << 16, problem), the
                                 //   distance kernel's work list:
                                 //   heavy ones from the front, light ones from the back
   int4* live_list;              // [cap] pairs with some non-saturated pixel, as near_list
@@ -102,6 +102,9 @@ struct Dev {
   float4* lossA;                // [total_tiles] (sum W(I-Ic)^2, sum relu(A-tau), sum O(1-y), 0)
   float* lossU;                 // [total_dtiles] weighted uniform-loss partial
   uint8_t* dtile_flags;         // [total_dtiles] container coverage on the tile / its halo (or null)
+  int* dtile_list;              // [2 total_dtiles] the tiles with kFlagOwn from 0, with kFlagHalo
+                                //   from total_dtiles, in no particular order (or null: all tiles)
+  int* dtile_n;                 // [2] lengths of the two lists
   float4* dq;                   // [n] gradient
   float4* partial;              // [cap] deterministic gradient partials, at emit position
   float* loss_terms;            // [P*5]

@@ -145,6 +145,15 @@ __device__ __forceinline__ int dil_flags(const Dev& d, int dt) {
   return d.dtile_flags ? (int)d.dtile_flags[dt] : (kFlagOwn | kFlagHalo);
 }
 
+// The tiles a pass visits: those with the given flag, from the per-level list (every tile when
+// there is no list).  Tiles off the list hold zeros written once per level.
+__device__ __forceinline__ int dil_count(const Dev& d, int which) {
+  return d.dtile_list ? d.dtile_n[which] : d.total_dtiles;
+}
+__device__ __forceinline__ int dil_tile(const Dev& d, int which, int i) {
+  return d.dtile_list ? d.dtile_list[which * d.total_dtiles + i] : i;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
   pdl_enter();
@@ -155,24 +164,15 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   uint32_t* sO = sm;
   uint32_t* H = sO + S * SP;
-  for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
+  // the tiles with container coverage; on the others M_C (1 - O) = 0, dL_u/dO = 0 and the loss
+  // partial is 0, as written once per level
+  const int n_own = dil_count(d, 0);
+  for (int li = blockIdx.x; li < n_own; li += gridDim.x) {
+    const int dt = dil_tile(d, 0, li);
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
-    if (!(dil_flags(d, dt) & kFlagOwn)) {
-      // no container coverage on this tile: M_C (1 - O) = 0, dL_u/dO = 0, no loss
-      for (int local = threadIdx.x; local < kDT * kDT; local += kDThreads) {
-        const int X = x0 + local % kDT, Y = y0 + local / kDT;
-        if (X >= res || Y >= res) continue;
-        const long long pix = pb + (long long)Y * res + X;
-        d.dil_m[pix] = 0.0f;
-        d.dil_mask[pix] = 0;
-        d.gOu[pix] = 0.0f;
-      }
-      if (threadIdx.x == 0) d.lossU[dt] = 0.0f;
-      continue;
-    }
     __syncthreads();
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
@@ -232,8 +232,12 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
   if (*d.status & kStatusOverflow) return;
   uint32_t* sM = sm;
   uint32_t* H = sM + S * SP;
-  for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
-    if (!(dil_flags(d, dt) & kFlagHalo)) continue;  // G = 0 over the tile and its halo
+  // the tiles with container coverage within the halo (G = 0 over the others and their halos)
+  const int n_halo = dil_count(d, 1);
+  for (int li = blockIdx.x; li < n_halo; li += gridDim.x) {
+    const int dt = dil_tile(d, 1, li);
+    // a tile without coverage of its own was not written by the forward pass: store, not add
+    const bool own = (dil_flags(d, dt) & kFlagOwn) != 0;
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
@@ -261,14 +265,16 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
         float acc = 0.0f;
 #pragma unroll
         for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * ((float)B[k][i] * inv_q);
-        d.gOu[pb + (long long)Y * res + X] += acc;
+        float* g = d.gOu + pb + (long long)Y * res + X;
+        *g = own ? *g + acc : acc;
       }
     }
   }
 }
 
 // Per dilation tile, once per level: whether the container coverage is nonzero on the tile, and
-// whether it is nonzero within the halo of the widest kernel.
+// whether it is nonzero within the halo of the widest kernel; each flag also lists the tile for the
+// pass that visits it (the forward pass the first kind, the adjoint the second).
 __global__ void k_dtile_flags(Dev d, int h) {
   __shared__ int s_own, s_halo;
   for (int dt = blockIdx.x; dt < d.total_dtiles; dt += gridDim.x) {
@@ -292,7 +298,11 @@ __global__ void k_dtile_flags(Dev d, int h) {
     if (own) atomicOr(&s_own, 1);
     if (halo) atomicOr(&s_halo, 1);
     __syncthreads();
-    if (threadIdx.x == 0) d.dtile_flags[dt] = (uint8_t)((s_own ? kFlagOwn : 0) | (s_halo ? kFlagHalo : 0));
+    if (threadIdx.x == 0) {
+      d.dtile_flags[dt] = (uint8_t)((s_own ? kFlagOwn : 0) | (s_halo ? kFlagHalo : 0));
+      if (s_own) d.dtile_list[atomicAdd(&d.dtile_n[0], 1)] = dt;
+      if (s_halo) d.dtile_list[d.total_dtiles + atomicAdd(&d.dtile_n[1], 1)] = dt;
+    }
     __syncthreads();
   }
 }
@@ -455,7 +465,7 @@ cudaError_t launch_dilate(const Dev& d, cudaStream_t s, bool backward) {
 }
 
 cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s) {
-  if (d.L.n_dil <= 0 || !d.dtile_flags) return cudaSuccess;
+  if (d.L.n_dil <= 0 || !d.dtile_flags || !d.dtile_list) return cudaSuccess;
   k_dtile_flags<<<d.total_dtiles, 256, 0, s>>>(d, dil_r(d.L.n_dil - 1));
   return cudaGetLastError();
 }

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d
     if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
     const int4 rec = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
     const int slot = rec.x, g = rec.y, txy = rec.z;
-    const int tx = txy & 0xffff, ty = txy >> 16, p = d.elem_prob[g], res = d.prob_res[p];
+    const int tx = txy & 0xffff, ty = txy >> 16, p = rec.w, res = d.prob_res[p];
     const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
     const bool closed = d.elem_closed[g] != 0;
     const int ns = closed ? nv : nv - 1;
@@ -446,12 +446,17 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
   constexpr int NP = T * T, PPL = NP / 32;
   if (*d.status & kStatusOverflow) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
+  const bool use_u = d.L.gamma != 0.0f;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int n_live = d.work[1];  // pairs without a gradient-carrying pixel are not listed
-  for (int i = blockIdx.x * kPairWarps + wid; i < n_live; i += gridDim.x * kPairWarps) {
-    const int4 rec = d.live_list[i];
-    const int slot = rec.x, g = rec.y, txy = rec.z;
-    const int tx = txy & 0xffff, ty = txy >> 16, p = d.elem_prob[g], res = d.prob_res[p];
+  const int stride = (int)gridDim.x * kPairWarps;
+  int i = blockIdx.x * kPairWarps + wid;
+  int4 rec = i < n_live ? d.live_list[i] : make_int4(0, 0, 0, 0);
+  for (; i < n_live; i += stride) {
+    // the next pair's record is read while this one is worked on
+    const int4 rec_next = i + stride < n_live ? d.live_list[i + stride] : rec;
+    const int slot = rec.x, g = rec.y, txy = rec.z, p = rec.w;
+    const int tx = txy & 0xffff, ty = txy >> 16, res = d.prob_res[p];
     const long long pixbase = d.prob_pix_base[p];
     const float inv_np = 1.0f / ((float)res * (float)res);
     const int v0 = d.elem_voff[g];
@@ -459,41 +464,64 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
     const float4 tp = d.tpx[g];
     const float s_inv = 1.0f / d.q[g].w;
     const float2* sv = d.saved + (size_t)slot * NP;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    // every per-pixel input of the warp's pixels in one round of loads
+    float2 srec[PPL];
+    float ihat[PPL], pt_s[PPL], cov[PPL], gou[PPL];
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
       const int local = lane + 32 * k;
       const int X = tx * T + local % T, Y = ty * T + local / T;
-      if (X >= res || Y >= res) continue;
-      const float2 rec = sv[local];
-      const float sd = rec.x;
+      srec[k] = make_float2(kFar, 0.0f);
+      ihat[k] = pt_s[k] = cov[k] = gou[k] = 0.0f;
+      if (X < res && Y < res) {
+        const long long pix = pixbase + (long long)Y * res + X;
+        srec[k] = sv[local];
+        ihat[k] = d.img_I[pix];
+        pt_s[k] = d.img_Pt[pix];
+        cov[k] = d.covc[pix];
+        if (use_u) gou[k] = d.gOu[pix];
+      }
+    }
+    // dL/dsd per pixel, then the closest segments of the pixels that carry a gradient
+    float gsd[PPL];
+    float4 sa[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int local = lane + 32 * k;
+      const int X = tx * T + local % T, Y = ty * T + local / T;
+      const float sd = srec[k].x;
       const float x = sd * inv_rho, xp = (sd + pad) * inv_rho;
-      if (!(fabsf(x) < 1.0f || fabsf(xp) < 1.0f)) continue;
-      const long long pix = pixbase + (long long)Y * res + X;
-      const float ihat = d.img_I[pix], pt_s = d.img_Pt[pix], cov = d.covc[pix];
-      const float pt = fabsf(pt_s);  // negative: the pixel is on the rising side of the Eq. 6 kink
-      const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
-      const float gou = d.L.gamma != 0.0f ? d.gOu[pix] : 0.0f;
-      const float py = (float)Y + 0.5f;
-      // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
-      const float gI = d.L.alpha * inv_np * 2.0f * W * (ihat - (1.0f - cov)) - d.L.gamma * gou -
-                       d.L.delta * inv_np *
-                           force_potential(d.L, ((float)X + 0.5f) / (float)res, py / (float)res);
-      const float gA = pt_s < 0.0f ? d.L.beta * inv_np : 0.0f;
-      const float omc = Sfun(-x), cp = Sfun(xp);
-      // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)
-      const float gc = omc > 0.0f ? -gI * ihat / omc : 0.0f;
-      // dA/dc^pad_i = tau prod_{j != i}(1 - tau c^pad_j)
-      const float gcp = gA * tau * pt / (1.0f - tau * cp);
-      const float gsd = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
-      if (gsd == 0.0f) continue;
-      const int j = __float_as_int(rec.y);
-      const float4 sa = d.segA[v0 + j];
-      const float dx = ((float)X + 0.5f - tp.x) - tp.z, dy = (py - tp.y) - tp.w;
-      const float ex = sa.z, ey = sa.w, ee = ex * ex + ey * ey;
-      const float wx = dx - sa.x, wy = dy - sa.y;
+      gsd[k] = 0.0f;
+      if (fabsf(x) < 1.0f || fabsf(xp) < 1.0f) {  // never for the out-of-range pixels (sd = 1e30)
+        const float pt = fabsf(pt_s[k]);  // negative: the pixel is on the rising side of the Eq. 6 kink
+        const float W = cov[k] >= 0.5f ? d.L.w_in : d.L.w_out;
+        const float py = (float)Y + 0.5f;
+        // O = 1 - Ihat: the uniform and force terms enter dL/dIhat with a minus sign
+        const float gI = d.L.alpha * inv_np * 2.0f * W * (ihat[k] - (1.0f - cov[k])) - d.L.gamma * gou[k] -
+                         d.L.delta * inv_np *
+                             force_potential(d.L, ((float)X + 0.5f) / (float)res, py / (float)res);
+        const float gA = pt_s[k] < 0.0f ? d.L.beta * inv_np : 0.0f;
+        const float omc = Sfun(-x), cp = Sfun(xp);
+        // dIhat/dc_i = -prod_{j != i}(1 - c_j) = -Ihat / (1 - c_i)   (0 when another c_j = 1)
+        const float gc = omc > 0.0f ? -gI * ihat[k] / omc : 0.0f;
+        // dA/dc^pad_i = tau prod_{j != i}(1 - tau c^pad_j)
+        const float gcp = gA * tau * pt / (1.0f - tau * cp);
+        gsd[k] = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
+      }
+      if (gsd[k] != 0.0f) sa[k] = d.segA[v0 + __float_as_int(srec[k].y)];
+    }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      if (gsd[k] == 0.0f) continue;
+      const int local = lane + 32 * k;
+      const int X = tx * T + local % T, Y = ty * T + local / T;
+      const float sd = srec[k].x;
+      const float dx = ((float)X + 0.5f - tp.x) - tp.z, dy = ((float)Y + 0.5f - tp.y) - tp.w;
+      const float ex = sa[k].z, ey = sa[k].w, ee = ex * ex + ey * ey;
+      const float wx = dx - sa[k].x, wy = dy - sa[k].y;
       const float u = ee > 0.0f ? __saturatef((wx * ex + wy * ey) / ee) : 0.0f;
-      const float qx = fmaf(u, ex, sa.x), qy = fmaf(u, ey, sa.y);  // closest point, rel. to t
+      const float qx = fmaf(u, ex, sa[k].x), qy = fmaf(u, ey, sa[k].y);  // closest point, rel. to t
       // unit normal from the closest point towards the pixel: for a closest point inside the
       // segment it is the segment's perpendicular on the pixel's side (well conditioned even
       // when the pixel is almost on the outline); at an end point it is the direction to the pixel
@@ -512,7 +540,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
       }
       // sd = sig * dist (closed: sig = +-1 by the winding; open: sd = hw - dist, sig = -1)
       const float sig = closed ? (sd > 0.0f ? 1.0f : -1.0f) : -1.0f;
-      const float gs = -sig * gsd;
+      const float gs = -sig * gsd[k];
       a0 += gs * nx * (float)res;              // d(dist)/dt = -n, t in unit coords
       a1 += gs * ny * (float)res;
       a2 += gs * (ny * qx - nx * qy);          // d(dist)/dtheta = -n . J q
@@ -535,6 +563,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
         atomicAdd(&d.dq[g].w, a3);
       }
     }
+    rec = rec_next;
   }
   if (mark) mark_step_if_last(d);
 }
