@@ -50,8 +50,10 @@ struct collage_s {
   long long* d_prob_pix_base = nullptr;
   int* ctl = nullptr;        // device: status, step, total_pairs, pending, 4 work counters
   int* h_ctl = nullptr;      // pinned mirror
-  bool ctl_current = false;  // h_ctl[1] (the step count) is the device's: no step was enqueued
-                             // since the last read
+  float* d_stage = nullptr;  // device: params, loss terms and control words gathered for one copy
+  float* h_stage = nullptr;  // pinned: their host copy ([4n | 5 n_probs | 4], see k_adam_flush)
+  bool ctl_current = false;  // h_ctl[1] (step count) and h_ctl[3] (pending) are the device's:
+                             // no step was enqueued since the last read
   cudaStream_t cap_stream = nullptr;
   cudaStream_t aux_stream = nullptr;  // side branch of an iteration (the loss assembly)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -130,6 +132,7 @@ collage_s::~collage_s() {
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (h_ctl) cudaFreeHost(h_ctl);
+  if (h_stage) cudaFreeHost(h_stage);
   free_list(pair_bufs);
   free_list(level_bufs);
   free_list(owned);
@@ -320,6 +323,9 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   set_grids(h);
   return COLLAGE_OK;
 }
+
+// floats of the gathered output: params, loss terms, control words
+static size_t stage_floats(const collage_s* h) { return 4 * (size_t)h->N + 5 * (size_t)h->P + 4; }
 
 static collage_status read_ctl(collage_t h, cudaStream_t s) {
   CK(h, cudaMemcpyAsync(h->h_ctl, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -697,6 +703,8 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.prob_dtile_base = h->d_prob_dtile_base;
   d.prob_pix_base = h->d_prob_pix_base;
   CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
+  CKC(dmalloc(h->owned, h->d_stage, stage_floats(h)));
+  CKC(cudaMallocHost(&h->h_stage, sizeof(float) * stage_floats(h)));
   CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CKC(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
   CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -805,25 +813,27 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
   if (st) return st;
   const int step0 = h->h_ctl[1];
   if (h_params_in) {
-    CK(h, launch_adam_flush(h->d, s));  // the step belongs to the old params
+    // a pending step belongs to the old params (none is pending right after this call's own flush)
+    if (h->h_ctl[3] != 0) CK(h, launch_adam_flush(h->d, s));
     CK(h, cudaMemcpyAsync(h->d.q, h_params_in, sizeof(float4) * h->N, cudaMemcpyHostToDevice, s));
   }
-  // one host round trip when nothing overflows: the steps, the copies out and the status word are
-  // enqueued together and the stream is synchronised once
+  // one host round trip when nothing overflows: the steps, then one kernel that applies the last
+  // Adam step and gathers the params, the loss terms and the control words, one copy of those to
+  // pinned memory, and one synchronisation
   st = enqueue_steps(h, s, n_iters);
   if (st) return st;
   auto copy_out = [&]() -> collage_status {
-    if (h_params_out) {
-      CK(h, launch_adam_flush(h->d, s));
-      CK(h, cudaMemcpyAsync(h_params_out, h->d.q, sizeof(float4) * h->N, cudaMemcpyDeviceToHost, s));
-    }
-    if (h_loss_out)
-      CK(h, cudaMemcpyAsync(h_loss_out, h->d.loss_terms, sizeof(float) * 5 * h->P, cudaMemcpyDeviceToHost, s));
+    CK(h, launch_adam_flush(h->d, s, h->d_stage));
+    CK(h, cudaMemcpyAsync(h->h_stage, h->d_stage, sizeof(float) * stage_floats(h), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    const float* tail = h->h_stage + 4 * (size_t)h->N;
+    if (h_params_out) std::memcpy(h_params_out, h->h_stage, sizeof(float4) * h->N);
+    if (h_loss_out) std::memcpy(h_loss_out, tail, sizeof(float) * 5 * h->P);
+    std::memcpy(h->h_ctl, tail + 5 * h->P, 4 * sizeof(int));
+    h->ctl_current = true;
     return COLLAGE_OK;
   };
   st = copy_out();
-  if (st) return st;
-  st = read_ctl(h, s);
   if (st) return st;
   const int status = h->h_ctl[0], done = h->h_ctl[1] - step0;
   if (!(status & (kStatusOverflow | kStatusBadParam | kStatusInternal)) && done == n_iters &&
@@ -838,7 +848,6 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
     if (st) return st;
     st = copy_out();
     if (st) return st;
-    CK(h, cudaStreamSynchronize(s));
   }
   return COLLAGE_OK;
 }
@@ -897,6 +906,7 @@ extern "C" collage_status collage_set_state(collage_t h, void* stream, const flo
   CK(h, cudaMemcpyAsync(h->d.step, &h->h_ctl[1], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(h, cudaMemsetAsync(h->d.pending, 0, sizeof(int), s));  // the state replaces everything
   CK(h, cudaStreamSynchronize(s));
+  h->h_ctl[3] = 0;
   h->ctl_current = true;
   return COLLAGE_OK;
 }

@@ -115,7 +115,9 @@ struct Dev {
                                 //   [0] near pairs taken by the distance kernel's blocks,
                                 //   [1] entries of live_list, [2] heavy near pairs (front of
                                 //   near_list), [3] blocks of the last gradient kernel that have
-                                //   finished, [4] light near pairs (back of near_list), [5..7] spare
+                                //   finished, [4] light near pairs (back of near_list), [5] blocks
+                                //   of the Adam flush that have finished (its last block resets
+                                //   it), [6..7] spare
   LossParams L;
   int deterministic;
   int pdl;                      // launch the iteration's kernels with programmatic serialisation
@@ -216,7 +218,7 @@ cudaError_t launch_dtile_flags(const Dev& d, cudaStream_t s);  // once per level
 cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid, bool mark_step);
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s, bool mark_step);
 // applies a pending Adam step to all elements and clears the flag (before params are read)
-cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s);
+cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s, float* out = nullptr);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
 // Resident blocks per SM of the raster kernels, the pairs one adjoint block and the tiles one

@@ -400,11 +400,33 @@ __global__ void k_grad_reduce(Dev d, int mark) {
   if (mark) mark_step_if_last(d);
 }
 
-// Applies a pending Adam step to every element (see adam_update); the caller then clears the flag.
-__global__ void k_adam_flush(Dev d) {
+// Applies a pending Adam step to every element (see adam_update); the last block to finish clears
+// the flag, once every block has read it.  With `out`, also gathers the params, the loss terms and
+// the control words (status, step, pair count, 0) into one buffer, [4n | 5 n_probs | 4], so that one
+// copy brings all of them to the host.
+__global__ void k_adam_flush(Dev d, float* out) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= d.n_elems || !*d.pending) return;
-  adam_update(d, g, *d.step, d.dq[g]);
+  const bool pend = *d.pending != 0;
+  if (g < d.n_elems) {
+    if (pend) adam_update(d, g, *d.step, d.dq[g]);
+    if (out) reinterpret_cast<float4*>(out)[g] = d.q[g];
+  }
+  if (out && blockIdx.x == 0) {
+    float* tail = out + 4 * (size_t)d.n_elems;
+    for (int i = threadIdx.x; i < 5 * d.n_probs; i += blockDim.x) tail[i] = d.loss_terms[i];
+    if (threadIdx.x == 0) {
+      int* c = reinterpret_cast<int*>(tail + 5 * d.n_probs);
+      c[0] = *d.status;
+      c[1] = *d.step;
+      c[2] = *d.total_pairs;
+      c[3] = 0;
+    }
+  }
+  __syncthreads();  // every thread of the block has read the flag
+  if (threadIdx.x == 0 && atomicAdd(&d.work[5], 1) == (int)gridDim.x - 1) {
+    *d.pending = 0;
+    d.work[5] = 0;
+  }
 }
 
 static size_t dilate_smem(int K, bool backward) {
@@ -478,11 +500,9 @@ cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s, bool mark_step) {
   return klaunch(d.pdl, k_grad_reduce, (d.n_elems + 255) / 256, 256, 0, s, d, mark_step ? 1 : 0);
 }
 
-cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s) {
-  k_adam_flush<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(d.pending, 0, sizeof(int), s);
+cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s, float* out) {
+  k_adam_flush<<<(d.n_elems + 255) / 256, 256, 0, s>>>(d, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out) {
