@@ -222,3 +222,59 @@ def adam(params, m, v, g, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, trainable=N
     tr = None if trainable is None else np.ascontiguousarray(trainable, np.uint8)
     lib.ora_adam(len(p) // 4, p, m, v, g, step, lr, b1, b2, eps, _ptr(tr), s_min, s_max)
     return p, m, v
+
+
+# outline fitting (Sec. 3, "Vector Representation") -------------------------------------------------
+def bernstein_weights(segs_per_cubic: int) -> np.ndarray:
+    """[segs, 4] cubic Bernstein weights at the samples t = j / segs (j = 0..segs-1) of one curve,
+    the flattening of Sec. 3's cubic paths: sample j = sum_r w[j, r] P_r."""
+    t = np.arange(segs_per_cubic, dtype=np.float64) / segs_per_cubic
+    u = 1.0 - t
+    return np.stack([u * u * u, 3.0 * u * u * t, 3.0 * u * t * t, t * t * t], axis=1)
+
+
+def control_grad(prob: dict, params, res: int, opts, segs_per_cubic: int = 16):
+    """dL/d(points) of every element, [n_pts, 2], and the loss terms, for the points of Sec. 3's
+    vector representation (cubic control points; polygon and polyline vertices).
+
+    Chain, step by step: ora_eval gives dL/d(world vertex) (unit coordinates); a world vertex is
+    t + s R(theta) v (Eq. 2), so dL/dv = s R(theta)^T dL/d(world vertex); a flattened vertex of curve
+    c at sample j is sum_r w[j, r] P[3c + r mod 3N] (Bernstein), so each point collects w[j, r] times
+    the vertex gradient over the samples it moves; polygon and polyline points are the vertices."""
+    sc = Scene(prob, segs_per_cubic)
+    out = sc.eval(params, res, opts, grad=False, grad_v=True)
+    gv = out["grad_v"].reshape(-1, 2)
+    kind = np.asarray(prob["kind"])
+    off = np.asarray(prob["pt_off"])
+    p = np.asarray(params, np.float64).reshape(-1, 4)
+    w = bernstein_weights(segs_per_cubic)
+    dpts = np.zeros((int(off[-1]), 2))
+    v0 = 0
+    for e in range(len(kind)):
+        nvert = sc.n_vertices(e)
+        ge = gv[v0:v0 + nvert]
+        v0 += nvert
+        c, s = np.cos(p[e, 2]), np.sin(p[e, 2])
+        # s R^T g, R = [[c, -s], [s, c]]
+        gl = p[e, 3] * np.stack([c * ge[:, 0] + s * ge[:, 1], -s * ge[:, 0] + c * ge[:, 1]], axis=1)
+        npt = int(off[e + 1] - off[e])
+        if kind[e] != 0:
+            dpts[off[e]:off[e + 1]] = gl
+            continue
+        for cv in range(npt // 3):
+            gc = gl[cv * segs_per_cubic:(cv + 1) * segs_per_cubic]
+            for r in range(4):
+                k = (3 * cv + r) % npt
+                dpts[off[e] + k] += w[:, r] @ gc
+    return dpts, out["terms"]
+
+
+def adam_points(pts, m, v, g, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
+    """One FP64 Adam step (bias-corrected, as for the transforms, without a clamp) on the points;
+    returns new (pts, m, v)."""
+    pts, m, v, g = (np.array(x, np.float64) for x in (pts, m, v, g))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    bc1, bc2 = 1.0 - b1 ** step, 1.0 - b2 ** step
+    pts = pts - (lr / bc1) * m / (np.sqrt(v) / np.sqrt(bc2) + eps)
+    return pts, m, v

@@ -32,7 +32,8 @@ import numpy as np
 __all__ = [
     "PCG32", "config_problem", "CONFIGS", "regular_polygon", "blob_controls",
     "convex_polygon", "polyline", "disk_container", "annulus_container",
-    "star_container", "open_rect_container", "make_problem",
+    "star_container", "open_rect_container", "make_problem", "circle_controls", "fit_problem",
+    "FIT_LOSS",
 ]
 
 _MASK64 = (1 << 64) - 1
@@ -83,6 +84,20 @@ def blob_controls(rng: PCG32, scale: float, n_cubics: int = 8) -> np.ndarray:
         a = 2.0 * np.pi * k / m
         pts[k] = (rad * math.cos(a), rad * math.sin(a))
     return pts
+
+
+def circle_controls(r: float, n_cubics: int) -> np.ndarray:
+    """Closed path of n_cubics curves close to a circle of radius r: anchors at equal angles,
+    handles along the tangents with length (4/3) tan(pi / (2 n_cubics)) r."""
+    h = 4.0 / 3.0 * math.tan(math.pi / (2 * n_cubics)) * r
+    pts = []
+    for k in range(n_cubics):
+        a0, a1 = 2.0 * np.pi * k / n_cubics, 2.0 * np.pi * (k + 1) / n_cubics
+        p0 = np.array([r * math.cos(a0), r * math.sin(a0)])
+        p1 = np.array([r * math.cos(a1), r * math.sin(a1)])
+        pts += [p0, p0 + h * np.array([-math.sin(a0), math.cos(a0)]),
+                p1 - h * np.array([-math.sin(a1), math.cos(a1)])]
+    return np.array(pts)
 
 
 def convex_polygon(rng: PCG32, r: float, n_sides: int) -> np.ndarray:
@@ -250,6 +265,20 @@ def config_problem(config: int, collage_index: int = 0, n_elems: int | None = No
     if grid is not None:
         g = grid
     return make_problem(els, rings, params, g)
+
+
+def fit_problem(index: int = 0, n_cubics: int = 20, grid: int = 256, r0: float = 0.3):
+    """Outline fitting (Sec. 3, Vector Representation): one closed path of n_cubics curves (the
+    paper uses 20), initially a circle of radius r0 about the centre, fitted to a seeded 12-point
+    star silhouette given as the container rings; the transform is the identity about the centre."""
+    rng = PCG32(7000 + index)
+    r_in, r_out = rng.uniform(0.18, 0.28), rng.uniform(0.36, 0.46)
+    rings = star_container(rng, r_in=r_in, r_out=r_out)
+    return make_problem([(0, circle_controls(r0, n_cubics), 0.0)], rings, [(0.5, 0.5, 0.0, 1.0)], grid)
+
+
+# Fitting loss: L_c of Eq. 5 alone with the same weight inside and outside the silhouette.
+FIT_LOSS = dict(alpha=1.0, beta=0.0, gamma=0.0, delta=0.0, w_in=1.0, w_out=1.0, pad_px=0.0)
 
 
 # Loss weights and schedules of the five workloads (Eq. 8 weights 3e3 / 8e4 / 5e-4).

@@ -581,3 +581,95 @@ def test_layout_nonuniformity_matches_brute_force(oracle_mod):
     fy, fx = np.nonzero(shape & ~obj)
     d2 = ((fy[:, None] - oy[None, :]) ** 2 + (fx[:, None] - ox[None, :]) ** 2).min(1)
     assert abs(out[7] - d2.mean() / R ** 2) <= 1e-12 * out[7]
+
+
+# ---- outline fitting (Sec. 3, Vector Representation): gradients of the points ------------------
+def _fit_loss(oracle_mod, **extra):
+    return oracle_mod.options(**dict(W.FIT_LOSS, **extra))
+
+
+def test_bernstein_weights_reproduce_oracle_flattening(oracle_mod):
+    # the weights control_grad takes transposed are the ones the oracle flattens with
+    prob = W.fit_problem(1, n_cubics=7, grid=64)
+    sc = oracle_mod.Scene(prob, segs_per_cubic=12)
+    P = np.asarray(prob["pts"], np.float64).reshape(-1, 2)
+    w = oracle_mod.bernstein_weights(12)
+    v = np.concatenate([w @ P[[3 * c, 3 * c + 1, 3 * c + 2, (3 * c + 3) % len(P)]]
+                        for c in range(len(P) // 3)])
+    np.testing.assert_allclose(sc.local_vertices(0), v, rtol=0, atol=1e-15)
+
+
+def test_control_grad_central_differences(oracle_mod):
+    R = 64
+    prob = W.fit_problem(0, n_cubics=20, grid=R)
+    o = _fit_loss(oracle_mod)
+    g, _ = oracle_mod.control_grad(prob, prob["params0"], R, o)
+    P = np.asarray(prob["pts"], np.float64).reshape(-1, 2)
+
+    def loss(pp):
+        pr = dict(prob)
+        pr["pts"] = pp.reshape(-1).astype(np.float32)
+        return oracle_mod.Scene(pr).eval(prob["params0"], R, o, grad=False)["terms"][4]
+
+    floor = 1e-2 * np.abs(g).max()
+    for k in (0, 1, 2, 5, 17, 30, 44, 59):
+        for c in range(2):
+            # the points are float32: step between float32 neighbours of the point
+            a, b = P.copy(), P.copy()
+            a[k, c] += 1e-4
+            b[k, c] -= 1e-4
+            a, b = (x.astype(np.float32).astype(np.float64) for x in (a, b))
+            fd = (loss(a) - loss(b)) / (a[k, c] - b[k, c])
+            assert abs(g[k, c] - fd) <= 1e-4 * max(abs(fd), floor), (k, c, g[k, c], fd)
+
+
+@pytest.mark.parametrize("force_kind", [0, 1])
+def test_control_grad_rigid_motions(oracle_mod, force_kind):
+    # moving every point of an element by a rigid motion or a scaling about its origin moves the
+    # element as its transform would: sum_k dP_k = s R^T dL/dt, sum_k (J P_k) . dP_k = dL/dtheta,
+    # sum_k P_k . dP_k = s dL/ds, against the spatial-gradient route of the transform gradient
+    R = 96
+    rng = W.PCG32(47)
+    els, params = [], []
+    for k in range(6):
+        kind = k % 3
+        r = 0.05 + 0.05 * rng.uniform()
+        shape = (W.blob_controls(rng, r) if kind == 0 else
+                 W.convex_polygon(rng, r, 7) if kind == 1 else W.polyline(rng, r, 5))
+        els.append((kind, shape, 0.012 if kind == 2 else 0.0))
+        params.append((0.3 + 0.4 * rng.uniform(), 0.3 + 0.4 * rng.uniform(),
+                       rng.uniform(0, 6.28), 0.8 + 0.4 * rng.uniform()))
+    prob = W.make_problem(els, W.star_container(rng, r_in=0.3, r_out=0.45), params, R)
+    q = np.asarray(params, np.float64).reshape(-1)
+    o = oracle_mod.options(pad_px=1.0, delta=50.0, force_kind=force_kind, force_x=0.4, force_y=0.55)
+    g, _ = oracle_mod.control_grad(prob, q, R, o)
+    gb = oracle_mod.Scene(prob).eval(q, R, o)["grad_b"].reshape(-1, 4)
+    P = np.asarray(prob["pts"], np.float32).astype(np.float64).reshape(-1, 2)
+    off = prob["pt_off"]
+    scale = np.abs(gb).max()
+    for e in range(len(els)):
+        th, s = q[4 * e + 2], q[4 * e + 3]
+        c, sn = np.cos(th), np.sin(th)
+        ge, Pe = g[off[e]:off[e + 1]], P[off[e]:off[e + 1]]
+        t_loc = s * np.array([c * gb[e, 0] + sn * gb[e, 1], -sn * gb[e, 0] + c * gb[e, 1]])
+        np.testing.assert_allclose(ge.sum(0), t_loc, rtol=0, atol=1e-9 * scale)
+        rot = np.sum(Pe[:, 0] * ge[:, 1] - Pe[:, 1] * ge[:, 0])
+        assert abs(rot - gb[e, 2]) <= 1e-9 * scale, (e, rot, gb[e, 2])
+        dil = np.sum(Pe * ge)
+        assert abs(dil - s * gb[e, 3]) <= 1e-9 * scale, (e, dil, s * gb[e, 3])
+
+
+def test_adam_points_matches_torch(oracle_mod):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    p0 = rng.normal(size=(10, 2))
+    grads = [rng.normal(size=(10, 2)) for _ in range(3)]
+    tp = torch.tensor(p0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for k, gk in enumerate(grads):
+        opt.zero_grad()
+        tp.grad = torch.tensor(gk)
+        opt.step()
+        p, m, v = oracle_mod.adam_points(p, m, v, gk, k + 1)
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=0, atol=1e-15)
