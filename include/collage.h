@@ -96,6 +96,16 @@ typedef struct {
                                            1 = towards the point (force_x, force_y) in unit
                                            coordinates, (1/wh) sum_p O(p) |p - (force_x, force_y)| */
   float force_x, force_y;
+  int fit_controls;                     /* 1: optimise the element outlines instead of their
+                                           transforms (Sec. 3, Vector Representation: closed
+                                           cubic paths fitted to an item silhouette by
+                                           differentiable rendering).  The parameters are then
+                                           the points of every element (pts of
+                                           collage_problem: cubic control points, polygon and
+                                           polyline vertices) in element-local coordinates; the
+                                           transforms stay at params0.  The silhouette to fit
+                                           is given as the container rings (L_c of Eq. 5 with
+                                           w_in = w_out is the fitting loss).  0 = off */
 } collage_options;
 
 /* Per-level sizes, for callers that allocate image buffers. */
@@ -169,6 +179,18 @@ collage_status collage_step_host(collage_t h, void* stream, int n_iters, const f
 collage_status collage_get_loss(collage_t h, void* stream, float* d_loss_terms);
 collage_status collage_get_params(collage_t h, void* stream, float* d_params);
 collage_status collage_set_params(collage_t h, void* stream, const float* d_params);
+
+/* Outline points (fit_controls mode, and readable in any mode): d_pts [2*n_pts], the pts arrays of
+ * the problems concatenated in problem order (element-local unit coordinates, CSR by pt_off).
+ * get_controls reads the current points; set_controls replaces them (re-flattening every outline on
+ * the device with the segs_per_cubic samples of Sec. 3 and resetting nothing else); get_control_grad
+ * writes dL/d(points) of the most recent collage_loss_backward or collage_step iteration in
+ * fit_controls mode (zeros before the first).  Cubic control points map to flattened vertices by
+ * the Bernstein weights of their curve; polygon and polyline points are the vertices.  NULL
+ * pointers return COLLAGE_ERR_INVALID_ARG; all three are asynchronous. */
+collage_status collage_get_controls(collage_t h, void* stream, float* d_pts);
+collage_status collage_set_controls(collage_t h, void* stream, const float* d_pts);
+collage_status collage_get_control_grad(collage_t h, void* stream, float* d_dpts);
 
 /* Checkpoint: d_state [12*n_elems] = params, Adam m, Adam v (device); *h_step and *h_level are
  * the Adam step count and the level.  set_state restores all of it (and sets the level). */

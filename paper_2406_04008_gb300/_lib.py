@@ -42,7 +42,7 @@ class collage_options(C.Structure):
                 ("s_min", C.c_float), ("s_max", C.c_float), ("deterministic", C.c_int),
                 ("tile", C.c_int), ("persistent", C.c_int), ("use_graphs", C.c_int),
                 ("overlap_launches", C.c_int), ("force_kind", C.c_int), ("force_x", C.c_float),
-                ("force_y", C.c_float)]
+                ("force_y", C.c_float), ("fit_controls", C.c_int)]
 
 
 class collage_info(C.Structure):
@@ -69,6 +69,9 @@ SIGNATURES = {
     "collage_get_loss": (C.c_int, [_vp, _vp, _vp]),
     "collage_get_params": (C.c_int, [_vp, _vp, _vp]),
     "collage_set_params": (C.c_int, [_vp, _vp, _vp]),
+    "collage_get_controls": (C.c_int, [_vp, _vp, _vp]),
+    "collage_set_controls": (C.c_int, [_vp, _vp, _vp]),
+    "collage_get_control_grad": (C.c_int, [_vp, _vp, _vp]),
     "collage_get_state": (C.c_int, [_vp, _vp, _vp, _ip, _ip]),
     "collage_set_state": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int]),
     "collage_get_bins": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _ip]),

@@ -38,6 +38,7 @@ class Collage:
         self.h = h
         self.n_probs = len(arrs)
         self.n_elems = int(sum(len(a.kind) for a in arrs))
+        self.n_pts = int(sum(int(a.pt_off[-1]) for a in arrs))
 
     def close(self):
         if getattr(self, "h", None):
@@ -108,6 +109,23 @@ class Collage:
     def set_params(self, params: torch.Tensor):
         p = params.detach().reshape(-1).contiguous().float()
         self._check(self.lib.collage_set_params(self.h, _stream(), _dptr(p)))
+
+    # outline points (fit_controls) ------------------------------------------------------------
+    def get_controls(self) -> torch.Tensor:
+        t = torch.empty(self.n_pts * 2, device="cuda", dtype=torch.float32)
+        self._check(self.lib.collage_get_controls(self.h, _stream(), _dptr(t)))
+        return t.view(self.n_pts, 2)
+
+    def set_controls(self, pts: torch.Tensor):
+        p = pts.detach().reshape(-1).contiguous().float()
+        if p.numel() != 2 * self.n_pts:
+            raise ValueError(f"expected {2 * self.n_pts} floats")
+        self._check(self.lib.collage_set_controls(self.h, _stream(), _dptr(p)))
+
+    def control_grad(self) -> torch.Tensor:
+        t = torch.empty(self.n_pts * 2, device="cuda", dtype=torch.float32)
+        self._check(self.lib.collage_get_control_grad(self.h, _stream(), _dptr(t)))
+        return t.view(self.n_pts, 2)
 
     def get_state(self):
         t = torch.empty(self.n_elems * 12, device="cuda", dtype=torch.float32)

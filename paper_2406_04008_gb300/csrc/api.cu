@@ -29,6 +29,9 @@ struct collage_s {
   std::vector<uint8_t> elem_closed;
   std::vector<float> elem_hw, elem_rbin;
   std::vector<float2> vloc;
+  std::vector<float2> ctrl;        // the problems' points (cubic control points, polygon and
+  std::vector<int> elem_coff;      //   polyline vertices), CSR by element
+  std::vector<uint8_t> elem_cubic;
   std::vector<double> ring_pts;
   bool has_trainable = false;
   // level state
@@ -182,6 +185,7 @@ static std::string check_options(const collage_options& o) {
     if (o.level_iters[l] < 0) return "level_iters[" + std::to_string(l) + "] must be >= 0";
   }
   if (!(o.tile == 0 || o.tile == 8 || o.tile == 16)) return "tile must be 0, 8 or 16";
+  if (o.fit_controls != 0 && o.fit_controls != 1) return "fit_controls must be 0 or 1";
   if (o.n_dilations < 0 || o.n_dilations > 8) return "n_dilations must be in 0..8";
   const float f[] = {o.alpha, o.beta, o.gamma, o.delta_down, o.w_in, o.w_out, o.lr, o.eps};
   for (float x : f)
@@ -463,6 +467,8 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   MARK_(7);
   if (bwd && !side) STEP_(launch_loss(d, s));
   MARK_(8);
+  // outline fitting: the points' gradient, and in step mode their Adam step and new outlines
+  if (bwd && d.fit) STEP_(launch_ctrl_step(d, s, mode == kStep ? 1 : 0));
   if (side) STEP_(cudaStreamWaitEvent(s, h->ev_join, 0));
   MARK_(9);
 #undef STEP_
@@ -561,6 +567,10 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
     for (int e = 0; e < pr.n_elems; ++e) {
       h->elem_prob.push_back(p);
       h->elem_voff.push_back((int)h->vloc.size());
+      h->elem_coff.push_back((int)h->ctrl.size());
+      h->elem_cubic.push_back(pr.kind[e] == COLLAGE_CUBIC_PATH ? 1 : 0);
+      for (int k = pr.pt_off[e]; k < pr.pt_off[e + 1]; ++k)
+        h->ctrl.push_back(make_float2(pr.pts[2 * k], pr.pts[2 * k + 1]));
       h->elem_closed.push_back(pr.kind[e] == COLLAGE_POLYLINE ? 0 : 1);
       h->elem_hw.push_back(pr.kind[e] == COLLAGE_POLYLINE && pr.stroke_hw ? pr.stroke_hw[e] : 0.0f);
       float rb = 0.0f;
@@ -585,6 +595,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
     h->prob_grid.push_back(pr.grid ? pr.grid : o.level_res[o.n_levels - 1]);
   }
   h->elem_voff.push_back((int)h->vloc.size());
+  h->elem_coff.push_back((int)h->ctrl.size());
   h->N = (int)h->elem_prob.size();
   h->V = (int)h->vloc.size();
 
@@ -665,6 +676,29 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.ring_pts = p_ring;
   d.ring_off = p_roff;
   d.prob_ring_base = p_prb;
+  {
+    // the points, and for fit_controls their Adam state, gradient and the per-vertex gradient
+    int* p_coff;
+    uint8_t* p_cubic;
+    CKC(upload(h->owned, p_coff, h->elem_coff));
+    CKC(upload(h->owned, p_cubic, h->elem_cubic));
+    CKC(upload(h->owned, d.ctrl, h->ctrl));
+    d.elem_coff = p_coff;
+    d.elem_cubic = p_cubic;
+    d.spc = o.segs_per_cubic;
+    d.fit = o.fit_controls ? 1 : 0;
+    const size_t nc = h->ctrl.size();
+    CKC(dmalloc(h->owned, d.dctrl, nc));
+    CKC(cudaMemset(d.dctrl, 0, sizeof(float2) * nc));
+    if (d.fit) {
+      CKC(dmalloc(h->owned, d.ctrl_m, nc));
+      CKC(dmalloc(h->owned, d.ctrl_v, nc));
+      CKC(dmalloc(h->owned, d.dv, h->V));
+      CKC(cudaMemset(d.ctrl_m, 0, sizeof(float2) * nc));
+      CKC(cudaMemset(d.ctrl_v, 0, sizeof(float2) * nc));
+      CKC(cudaMemset(d.dv, 0, sizeof(float2) * h->V));
+    }
+  }
   CKC(upload(h->owned, d.q, q));
   CKC(dmalloc(h->owned, d.m, h->N));
   CKC(dmalloc(h->owned, d.v, h->N));
@@ -873,6 +907,28 @@ extern "C" collage_status collage_set_params(collage_t h, void* stream, const fl
   return COLLAGE_OK;
 }
 
+extern "C" collage_status collage_get_controls(collage_t h, void* stream, float* d_pts) {
+  if (!h || !d_pts) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, cudaMemcpyAsync(d_pts, h->d.ctrl, sizeof(float2) * h->ctrl.size(), cudaMemcpyDeviceToDevice,
+                        (cudaStream_t)stream));
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_set_controls(collage_t h, void* stream, const float* d_pts) {
+  if (!h || !d_pts) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(h, cudaMemcpyAsync(h->d.ctrl, d_pts, sizeof(float2) * h->ctrl.size(), cudaMemcpyDeviceToDevice, s));
+  CK(h, launch_ctrl_step(h->d, s, 2));  // new outlines and bin radii
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_control_grad(collage_t h, void* stream, float* d_dpts) {
+  if (!h || !d_dpts) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  CK(h, cudaMemcpyAsync(d_dpts, h->d.dctrl, sizeof(float2) * h->ctrl.size(), cudaMemcpyDeviceToDevice,
+                        (cudaStream_t)stream));
+  return COLLAGE_OK;
+}
+
 extern "C" collage_status collage_get_state(collage_t h, void* stream, float* d_state, int* h_step,
                                             int* h_level) {
   if (!h || !d_state) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
@@ -1065,7 +1121,7 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   // transform (with the previous Adam step), tile scan, emit, pair distances, composite,
   // (2 dilation), raster bwd, (gradient reduce), loss
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 5 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 1;
+  out->kernels_per_iter = 5 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 1 + (h->d.fit ? 1 : 0);
   return COLLAGE_OK;
 }
 

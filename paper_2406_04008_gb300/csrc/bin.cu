@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = d.elem_prob[g];
   const int res = d.prob_res[p];
-  if (threadIdx.x == 0 && *d.pending) adam_update(d, g, *d.step, d.dq[g]);  // previous step
+  // the previous iteration's step (when the outlines are fitted the transforms stay fixed)
+  if (threadIdx.x == 0 && *d.pending && !d.fit) adam_update(d, g, *d.step, d.dq[g]);
   __syncthreads();
   const float4 q = d.q[g];
   if (threadIdx.x < 4) {

@@ -48,8 +48,9 @@ struct Dev {
   const int* elem_voff;         // [n+1]
   const uint8_t* elem_closed;
   const float* elem_hw;         // unit coords
-  const float* elem_rbin;       // bin radius (largest |control point|), float
-  const float2* vloc;           // flattened local vertices, unit coords
+  float* elem_rbin;             // bin radius (largest |control point|), float
+  float2* vloc;                 // flattened local vertices, unit coords (rewritten by
+                                //   k_ctrl_step when the outlines are fitted)
   const int* prob_elem_base;    // [P+1]
   const double* ring_pts;       // container rings, unit coords (double)
   const int* ring_off;          // [total rings + 1]
@@ -121,6 +122,16 @@ struct Dev {
   LossParams L;
   int deterministic;
   int pdl;                      // launch the iteration's kernels with programmatic serialisation
+  // ---- outline fitting (fit_controls): the points of each element are the parameters ----
+  int fit;                      // 1: the adjoint accumulates dv and k_ctrl_step runs Adam on ctrl
+  int spc;                      // segments per cubic
+  const int* elem_coff;         // [n+1] CSR offsets of each element's points in ctrl
+  const uint8_t* elem_cubic;    // [n] 1: closed cubic path (points are control points)
+  float2* ctrl;                 // [C] points, element-local unit coordinates
+  float2* ctrl_m;               // [C] Adam moments
+  float2* ctrl_v;
+  float2* dctrl;                // [C] dL/d(points) of the last backward pass
+  float2* dv;                   // [V] dL/d(flattened vertex), element-local unit coordinates
 };
 
 // Adam (bias-corrected, the update torch.optim.Adam performs; it stands in for the plain descent
@@ -219,6 +230,10 @@ cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid, bool 
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s, bool mark_step);
 // applies a pending Adam step to all elements and clears the flag (before params are read)
 cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s, float* out = nullptr);
+// outline fitting, one block per element: mode 0 maps dv to dctrl (and clears dv); mode 1 also
+// takes an Adam step on ctrl at step *d.step and flattens again (vertices and bin radii); mode 2
+// only flattens
+cudaError_t launch_ctrl_step(const Dev& d, cudaStream_t s, int mode);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
 // Resident blocks per SM of the raster kernels, the pairs one adjoint block and the tiles one

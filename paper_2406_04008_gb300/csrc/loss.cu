@@ -408,7 +408,7 @@ __global__ void k_adam_flush(Dev d, float* out) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const bool pend = *d.pending != 0;
   if (g < d.n_elems) {
-    if (pend) adam_update(d, g, *d.step, d.dq[g]);
+    if (pend && !d.fit) adam_update(d, g, *d.step, d.dq[g]);
     if (out) reinterpret_cast<float4*>(out)[g] = d.q[g];
   }
   if (out && blockIdx.x == 0) {

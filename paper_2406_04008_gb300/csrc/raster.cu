@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
 // dL/dc -> dc/dsd -> dsd/d(closest segment) -> d/d(tx, ty, theta, s) of Eq. 2, reduced over the
 // tile's pixels by a fixed shuffle tree and added to the element's gradient (or stored per pair).
 // ------------------------------------------------------------------------------------------------
-template <int T>
+template <int T, bool FIT>  // FIT: also dL/d(vertex) for outline fitting (d.fit)
 __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark) {
   pdl_enter();
   constexpr int NP = T * T, PPL = NP / 32;
@@ -462,8 +462,17 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
     const int v0 = d.elem_voff[g];
     const bool closed = d.elem_closed[g] != 0;
     const float4 tp = d.tpx[g];
-    const float s_inv = 1.0f / d.q[g].w;
+    const float4 qg = d.q[g];
+    const float s_inv = 1.0f / qg.w;
     const float2* sv = d.saved + (size_t)slot * NP;
+    // outline fitting: d(pixel)/d(local vertex) = s res R(theta), applied transposed below
+    float fc = 0.0f, fs = 0.0f, sres = 0.0f;
+    int nv = 0;
+    if (FIT) {
+      sincosf(qg.z, &fs, &fc);
+      sres = qg.w * (float)res;
+      nv = d.elem_voff[g + 1] - v0;
+    }
     // every per-pixel input of the warp's pixels in one round of loads
     float2 srec[PPL];
     float ihat[PPL], pt_s[PPL], cov[PPL], gou[PPL];
@@ -545,6 +554,18 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
       a1 += gs * ny * (float)res;
       a2 += gs * (ny * qx - nx * qy);          // d(dist)/dtheta = -n . J q
       a3 += gs * (nx * qx + ny * qy) * s_inv;  // d(dist)/ds = -n . q / s
+      if (FIT) {
+        // d(dist)/d(end points) = -n (1 - u), -n u (the closest point moves with them), taken to
+        // element-local unit coordinates
+        const float gx = gs * nx, gy = gs * ny;
+        const float lx = sres * (fc * gx + fs * gy), ly = sres * (fc * gy - fs * gx);
+        const int j = __float_as_int(srec[k].y);
+        const int ja = v0 + j, jb = v0 + (j + 1 == nv ? 0 : j + 1);
+        atomicAdd(&d.dv[ja].x, lx * (1.0f - u));
+        atomicAdd(&d.dv[ja].y, ly * (1.0f - u));
+        atomicAdd(&d.dv[jb].x, lx * u);
+        atomicAdd(&d.dv[jb].y, ly * u);
+      }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -666,8 +687,12 @@ cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int t
 cudaError_t launch_raster_bwd(const Dev& d, cudaStream_t s, int pair_grid, bool mark_step) {
   const int mk = mark_step ? 1 : 0;
   switch (d.tile) {
-    case 8: return klaunch(d.pdl, k_raster_bwd<8>, pair_grid, kPairWarps * 32, 0, s, d, mk);
-    case 16: return klaunch(d.pdl, k_raster_bwd<16>, pair_grid, kPairWarps * 32, 0, s, d, mk);
+    case 8:
+      return klaunch(d.pdl, d.fit ? k_raster_bwd<8, true> : k_raster_bwd<8, false>, pair_grid,
+                     kPairWarps * 32, 0, s, d, mk);
+    case 16:
+      return klaunch(d.pdl, d.fit ? k_raster_bwd<16, true> : k_raster_bwd<16, false>, pair_grid,
+                     kPairWarps * 32, 0, s, d, mk);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -686,7 +711,7 @@ static void per_sm_t(RasterOcc* o) {
   constexpr int NT = TileCfg<T>::NT;
   int a = 1, b = 1, c = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pair_sd<T, NT>, NT, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T>, kPairWarps * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T, false>, kPairWarps * 32, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_composite<T>, kCompWarps * 32, 0);
   o->fwd_per_sm = a > 0 ? a : 1;
   o->bwd_per_sm = b > 0 ? b : 1;
