@@ -271,6 +271,12 @@ def cpu_per_config():
         per_iter(p, p["grid"], {})
     out["batch64_first8"] = time.perf_counter() - t0
     out["open5000_rect_2048"] = per_iter(W.config_problem(5), 2048, dict(pad_px=1.0, delta=1e3))
+    # outline fitting: gradient of the 60 control points and their Adam step, 256^2
+    fp = W.fit_problem(0)
+    t0 = time.perf_counter()
+    g, _ = O.control_grad(fp, fp["params0"], 256, O.options(**W.FIT_LOSS))
+    O.adam_points(np.asarray(fp["pts"]).reshape(-1, 2), 0.0, 0.0, g, 1)
+    out["fit20_star_256"] = time.perf_counter() - t0
     prev = O.set_threads(1)
     try:
         out["mixed1000_annulus_1024_1core"] = per_iter(_workload(), 1024, dict(pad_px=2.0))
@@ -316,6 +322,30 @@ def batch_vs_plain(steps, flush, torch):
     return {"workload": "batch64: 64 collages, %d elements in all, grids 256/512/1024" % n_elems,
             "batched": steps / bt, "plain_sequential": steps / pt, "speedup": pt / bt,
             "unit": "batch iterations/s (every collage one fwd+bwd+Adam iteration)", "tile": tile}
+
+
+def outline_fitting(steps, flush, torch):
+    """Outline fitting (Sec. 3, Vector Representation): closed paths of 20 cubics (the paper's N)
+    fitted to seeded star silhouettes at 256^2 by Adam on their control points; one outline, and 64
+    outlines in one batched handle.  A step is one fwd+bwd+Adam iteration of every outline."""
+    from paper_2406_04008_gb300 import workloads as W
+    from paper_2406_04008_gb300.collage import Collage
+    kw = dict(W.FIT_LOSS)
+    kw["delta_down"] = kw.pop("delta")
+    kw.update(fit_controls=1, n_levels=1, level_res=[256], level_iters=[50], n_dilations=0)
+    out = {"workload": "fit20_star_256: closed paths of 20 cubics (320 segments) fitted to 12-point "
+                       "star silhouettes at 256^2, L_c with w_in = w_out = 1",
+           "unit": "iters/s (one fwd+bwd+Adam iteration of every outline)"}
+    for name, probs in (("one", [W.fit_problem(0)]), ("batch64", [W.fit_problem(i) for i in range(64)])):
+        col = Collage(probs, use_graphs=1, persistent=1, tile=0, **kw)
+        col.autotune()
+        # the outlines grow towards the star tips: the synchronous warm-up regrows the bins, so
+        # the timed asynchronous steps meet no overflow
+        col.step(150)
+        torch.cuda.synchronize()
+        out[name] = steps / sum(_time_steps(col, steps, flush, torch))
+        col.close()
+    return out
 
 
 def open_packing(steps, flush, torch):
@@ -464,6 +494,7 @@ def main():
         extra["batch64"] = batch_vs_plain(10, flush, torch)
         extra["open5000"] = open_packing(10, flush, torch)
         extra["schedule_mixed1000"] = schedule_time(torch)
+        extra["fit20"] = outline_fitting(50, flush, torch)
 
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
