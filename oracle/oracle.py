@@ -278,3 +278,79 @@ def adam_points(pts, m, v, g, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
     bc1, bc2 = 1.0 - b1 ** step, 1.0 - b2 ** step
     pts = pts - (lr / bc1) * m / (np.sqrt(v) / np.sqrt(bc2) + eps)
     return pts, m, v
+
+
+# skeleton-based initialisation (Sec. 4.1) ---------------------------------------------------------
+def medial_axis(covc: np.ndarray):
+    """(D2, axis) of a container raster covc [R, R] (Sec. 4.1: the medial axis and the medial width).
+
+    inside = covc >= 1/2, the pixels one step beyond the image outside.  D2 is the squared distance
+    in pixels from each inside pixel centre to the nearest outside pixel centre (0 outside): per
+    column the row distance g to the nearest outside pixel, then per row the minimum over columns
+    k of (j - k)^2 + g(k)^2, the two columns beyond the image included with g = 0.  The axis is the
+    ridge of D2: inside pixels that are a maximum of D2 along one of the four lines through them
+    (horizontal, vertical, the two diagonals), D2(p) >= both line neighbours and > at least one
+    (neighbours beyond the image count 0)."""
+    R = covc.shape[0]
+    inside = covc >= 0.5
+    g = np.zeros((R, R), np.int64)
+    last = np.full(R, -1, np.int64)
+    for i in range(R):
+        last = np.where(inside[i], last, i)
+        g[i] = i - last
+    last = np.full(R, R, np.int64)
+    for i in range(R - 1, -1, -1):
+        last = np.where(inside[i], last, i)
+        g[i] = np.minimum(g[i], last - i)
+    j = np.arange(R, dtype=np.int64)
+    D2 = np.zeros((R, R), np.int64)
+    for i in range(R):
+        best = ((j[:, None] - j[None, :]) ** 2 + g[i][None, :] ** 2).min(axis=1)
+        best = np.minimum(best, np.minimum((j + 1) ** 2, (R - j) ** 2))
+        D2[i] = np.where(inside[i], best, 0)
+    pad = np.zeros((R + 2, R + 2), np.int64)
+    pad[1:-1, 1:-1] = D2
+    axis = np.zeros((R, R), bool)
+    for dx, dy in ((1, 0), (0, 1), (1, 1), (1, -1)):
+        a = pad[1 + dy:R + 1 + dy, 1 + dx:R + 1 + dx]
+        b = pad[1 - dy:R + 1 - dy, 1 - dx:R + 1 - dx]
+        axis |= (D2 >= a) & (D2 >= b) & ((D2 > a) | (D2 > b))
+    return D2, axis & (D2 > 0)
+
+
+def mat_init(prob: dict, params, res: int, opts, segs_per_cubic: int = 16):
+    """Initial translations along the medial axis (Sec. 4.1): returns (params [n, 4] float32, D2,
+    axis).  The elements in decreasing radius r = (bin radius x s) x res (float32; ties: lower
+    index) each take the axis pixel of largest D2 (ties: lower pixel index) whose clearance
+    min_j (|p - c_j| - r_j) over the elements placed so far is >= r, else the axis pixel of largest
+    clearance (ties: lower pixel index); clearances in float32, |p - c|^2 an exact integer.  The
+    translation becomes the pixel centre ((x + 1/2) / res, (y + 1/2) / res) in float32."""
+    sc = Scene(prob, segs_per_cubic)
+    q = np.asarray(params, np.float32).reshape(-1, 4).copy()
+    _, _, covc = sc.render(q.astype(np.float64).reshape(-1), res, opts)
+    D2, axis = medial_axis(covc)
+    cand = np.flatnonzero(axis.reshape(-1))
+    if len(cand) == 0:
+        return q, D2, axis
+    n = len(q)
+    rbin = np.array([sc.bin_radius(e) for e in range(n)], np.float32)
+    r = (rbin * q[:, 3]) * np.float32(res)
+    cx, cy = cand % res, cand // res
+    d2c = D2.reshape(-1)[cand]
+    clear = np.full(len(cand), np.finfo(np.float32).max, np.float32)
+    placed = np.zeros(n, bool)
+    for _ in range(n):
+        free = np.flatnonzero(~placed)
+        e = free[np.lexsort((free, -r[free].astype(np.float64)))[0]]
+        ok = np.flatnonzero(clear >= r[e])
+        if len(ok):
+            c = ok[np.lexsort((cand[ok], -d2c[ok]))[0]]
+        else:
+            c = np.lexsort((cand, -clear.astype(np.float64)))[0]
+        x, y = cx[c], cy[c]
+        q[e, 0] = (np.float32(x) + np.float32(0.5)) / np.float32(res)
+        q[e, 1] = (np.float32(y) + np.float32(0.5)) / np.float32(res)
+        dist = np.sqrt(((cx - x) ** 2 + (cy - y) ** 2).astype(np.float32)) - r[e]
+        clear = np.minimum(clear, dist)
+        placed[e] = True
+    return q, D2, axis

@@ -673,3 +673,88 @@ def test_adam_points_matches_torch(oracle_mod):
         opt.step()
         p, m, v = oracle_mod.adam_points(p, m, v, gk, k + 1)
     np.testing.assert_allclose(p, tp.detach().numpy(), rtol=0, atol=1e-15)
+
+
+# ---- skeleton-based initialisation (Sec. 4.1) -----------------------------------------------------
+def test_medial_width_matches_scipy_edt(oracle_mod):
+    nd = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(11)
+    for R in (17, 40):
+        cov = (rng.uniform(size=(R, R)) < 0.8).astype(np.float64)
+        D2, _ = oracle_mod.medial_axis(cov)
+        # scipy measures to the nearest zero of its input: pad the image with one outside ring
+        padded = np.zeros((R + 2, R + 2))
+        padded[1:-1, 1:-1] = cov >= 0.5
+        ref = nd.distance_transform_edt(padded)[1:-1, 1:-1]
+        np.testing.assert_array_equal(D2, np.rint(ref ** 2).astype(np.int64))
+
+
+def test_medial_axis_closed_forms(oracle_mod):
+    # a horizontal strip of odd height: the centre row is the ridge away from the ends, and only it
+    R = 64
+    cov = np.zeros((R, R))
+    cov[20:31, 4:60] = 1.0  # 11 rows: centre row 25
+    D2, axis = oracle_mod.medial_axis(cov)
+    assert axis[25, 12:52].all()
+    assert not axis[20:25, 12:52].any() and not axis[26:31, 12:52].any()
+    assert (D2[25, 12:52] == 36).all()  # 6 rows to the outside rows 19 and 31
+    # a square: the ridge is its two diagonals (and the centre has the largest width)
+    cov = np.zeros((R, R))
+    cov[10:41, 10:41] = 1.0  # 31 x 31, centre (25, 25)
+    D2, axis = oracle_mod.medial_axis(cov)
+    assert D2.max() == D2[25, 25] == 16 ** 2
+    for k in range(-12, 13):
+        assert axis[25 + k, 25 + k] and axis[25 + k, 25 - k]
+    assert not axis[25, 18] and not axis[18, 25]
+
+
+def _place_brute(D2, axis, r, res):
+    """The placement rule with explicit loops: largest radius first (lower index on ties); among the
+    axis pixels with clearance >= r the largest D2 (lower pixel index on ties), else the largest
+    clearance; clearances in float32."""
+    cands = [(int(i), int(D2.reshape(-1)[i])) for i in np.flatnonzero(axis.reshape(-1))]
+    clear = {i: np.float32(np.finfo(np.float32).max) for i, _ in cands}
+    todo = list(range(len(r)))
+    out = {}
+    while todo:
+        e = todo[0]
+        for f in todo:
+            if r[f] > r[e]:
+                e = f
+        todo.remove(e)
+        best = None
+        for i, w in cands:
+            if clear[i] >= r[e] and (best is None or w > best[1] or (w == best[1] and i < best[0])):
+                best = (i, w)
+        if best is None:
+            for i, _ in cands:
+                if best is None or clear[i] > clear[best[0]] or (clear[i] == clear[best[0]] and i < best[0]):
+                    best = (i, 0)
+        c = best[0]
+        out[e] = c
+        for i, _ in cands:
+            d = np.float32(np.sqrt(np.float32((i % res - c % res) ** 2 + (i // res - c // res) ** 2)))
+            clear[i] = min(clear[i], np.float32(d - r[e]))
+    return out
+
+
+def test_mat_placement_brute_force(oracle_mod):
+    R = 48
+    rng = W.PCG32(5)
+    els = [(1, W.regular_polygon(0.03 + 0.05 * rng.uniform(), 8), 0.0) for _ in range(7)]
+    params = [(0.5, 0.5, 0.0, 1.0)] * 7
+    prob = W.make_problem(els, W.star_container(rng, r_in=0.2, r_out=0.45), params, R)
+    o = oracle_mod.options()
+    q, D2, axis = oracle_mod.mat_init(prob, prob["params0"], R, o)
+    sc = oracle_mod.Scene(prob)
+    r = (np.array([sc.bin_radius(e) for e in range(7)], np.float32) * np.float32(1.0)) * np.float32(R)
+    ref = _place_brute(D2, axis, r, R)
+    for e, c in ref.items():
+        assert q[e, 0] == np.float32((np.float32(c % R) + np.float32(0.5)) / np.float32(R))
+        assert q[e, 1] == np.float32((np.float32(c // R) + np.float32(0.5)) / np.float32(R))
+    # the largest element sits at the widest pixel of the container
+    e0 = int(np.argmax(r))
+    c0 = ref[e0]
+    assert D2.reshape(-1)[c0] == D2.max()
+    # rotation and scale are untouched
+    assert np.array_equal(q[:, 2:], np.asarray(prob["params0"], np.float32).reshape(-1, 4)[:, 2:])
