@@ -277,6 +277,10 @@ def cpu_per_config():
     g, _ = O.control_grad(fp, fp["params0"], 256, O.options(**W.FIT_LOSS))
     O.adam_points(np.asarray(fp["pts"]).reshape(-1, 2), 0.0, 0.0, g, 1)
     out["fit20_star_256"] = time.perf_counter() - t0
+    # skeleton-based initialisation of the 1024^2 workload (one call, s)
+    t0 = time.perf_counter()
+    O.mat_init(_workload(), _workload()["params0"], 1024, O.options())
+    out["mat_init_mixed1000_1024"] = time.perf_counter() - t0
     prev = O.set_threads(1)
     try:
         out["mixed1000_annulus_1024_1core"] = per_iter(_workload(), 1024, dict(pad_px=2.0))
@@ -346,6 +350,26 @@ def outline_fitting(steps, flush, torch):
         out[name] = steps / sum(_time_steps(col, steps, flush, torch))
         col.close()
     return out
+
+
+def mat_initialisation(torch):
+    """Skeleton-based initialisation (Sec. 4.1) of the 1000-element workload at its 1024^2 level:
+    medial width, ridge axis and greedy placement (collage_mat_init), milliseconds per call."""
+    from paper_2406_04008_gb300.collage import Collage
+    col = Collage(_workload(), level_res=[1024], tile=8)
+    col.mat_init()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record(stream)
+    for _ in range(reps):
+        col.mat_init()
+    b.record(stream)
+    b.synchronize()
+    col.close()
+    return {"workload": "mixed1000_annulus_1024: medial axis of the annulus at 1024^2, 1000 elements "
+                        "placed", "ms": a.elapsed_time(b) / reps}
 
 
 def open_packing(steps, flush, torch):
@@ -495,6 +519,7 @@ def main():
         extra["open5000"] = open_packing(10, flush, torch)
         extra["schedule_mixed1000"] = schedule_time(torch)
         extra["fit20"] = outline_fitting(50, flush, torch)
+        extra["mat_init"] = mat_initialisation(torch)
 
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)

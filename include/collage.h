@@ -192,6 +192,24 @@ collage_status collage_get_controls(collage_t h, void* stream, float* d_pts);
 collage_status collage_set_controls(collage_t h, void* stream, const float* d_pts);
 collage_status collage_get_control_grad(collage_t h, void* stream, float* d_dpts);
 
+/* Skeleton-based initial positions (Sec. 4.1, Initialization): the medial axis of each problem's
+ * container at the current level and its medial width, then the elements placed along the axis,
+ * larger ones where the width is larger.  On the container raster (inside: coverage >= 1/2; the
+ * pixels one step beyond the image are outside), D2(p) is the exact squared distance in pixels
+ * from an inside pixel centre to the nearest outside pixel centre; the axis is the ridge of D2: the
+ * inside pixels that are a maximum of D2 along one of the four lines through them (horizontal,
+ * vertical, the two diagonals; >= both line neighbours and > one, neighbours beyond the image 0).  The elements, in decreasing
+ * radius r = bin radius x s x res (pixels; ties: lower index), each take the axis pixel of largest
+ * D2 (ties: lower pixel index) whose clearance min_j (|p - c_j| - r_j) over the elements already
+ * placed is >= r, else the axis pixel of largest clearance (float32, fixed operation order); an
+ * element's translation becomes that pixel's centre, its rotation and scale stay.  A pending Adam
+ * step is applied first; the Adam state is kept.  A problem without inside pixels keeps its
+ * params.  Optional outputs (device, [total_pixels] at the current level, NULL to skip):
+ *   d_axis   int32 1 on the medial axis, else 0
+ *   d_width  float32 medial width sqrt(D2) in pixels (0 outside the container)
+ * Allocates scratch (16 B per pixel) on first use; asynchronous. */
+collage_status collage_mat_init(collage_t h, void* stream, int* d_axis, float* d_width);
+
 /* Checkpoint: d_state [12*n_elems] = params, Adam m, Adam v (device); *h_step and *h_level are
  * the Adam step count and the level.  set_state restores all of it (and sets the level). */
 collage_status collage_get_state(collage_t h, void* stream, float* d_state, int* h_step,

@@ -69,6 +69,7 @@ SIGNATURES = {
     "collage_get_loss": (C.c_int, [_vp, _vp, _vp]),
     "collage_get_params": (C.c_int, [_vp, _vp, _vp]),
     "collage_set_params": (C.c_int, [_vp, _vp, _vp]),
+    "collage_mat_init": (C.c_int, [_vp, _vp, _vp, _vp]),
     "collage_get_controls": (C.c_int, [_vp, _vp, _vp]),
     "collage_set_controls": (C.c_int, [_vp, _vp, _vp]),
     "collage_get_control_grad": (C.c_int, [_vp, _vp, _vp]),

@@ -110,6 +110,20 @@ class Collage:
         p = params.detach().reshape(-1).contiguous().float()
         self._check(self.lib.collage_set_params(self.h, _stream(), _dptr(p)))
 
+    # skeleton-based initialisation ------------------------------------------------------------
+    def mat_init(self, want_maps: bool = False):
+        """Place the elements along the container's medial axis (collage_mat_init); with want_maps,
+        also return the axis mask (int32) and the medial width (float32) of every pixel."""
+        axis = width = None
+        if want_maps:
+            n = self.info()["total_pixels"]
+            axis = torch.empty(n, device="cuda", dtype=torch.int32)
+            width = torch.empty(n, device="cuda", dtype=torch.float32)
+        self._check(self.lib.collage_mat_init(
+            self.h, _stream(), None if axis is None else C.c_void_p(axis.data_ptr()),
+            None if width is None else _dptr(width)))
+        return axis, width
+
     # outline points (fit_controls) ------------------------------------------------------------
     def get_controls(self) -> torch.Tensor:
         t = torch.empty(self.n_pts * 2, device="cuda", dtype=torch.float32)

@@ -65,6 +65,9 @@ struct collage_s {
   uint8_t* met_obj = nullptr;
   int* met_gcol = nullptr;
   unsigned long long* met_cnt = nullptr;  // [5 * P]: 4 counts, then the distance sums
+  // skeleton-based initialisation scratch (allocated by collage_mat_init)
+  unsigned char* mat_buf = nullptr;
+  size_t mat_bytes = 0;
   size_t met_pix = 0;
   std::string err;
   std::vector<void*> owned;      // fixed-size allocations
@@ -132,6 +135,7 @@ collage_s::~collage_s() {
   if (met_obj) cudaFree(met_obj);
   if (met_gcol) cudaFree(met_gcol);
   if (met_cnt) cudaFree(met_cnt);
+  if (mat_buf) cudaFree(mat_buf);
   if (ev_fork) cudaEventDestroy(ev_fork);
   if (ev_join) cudaEventDestroy(ev_join);
   if (h_ctl) cudaFreeHost(h_ctl);
@@ -1063,6 +1067,35 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   collage_status st = setup_level(h, h->level);
   if (st) return st;
   if (h_best_ms) *h_best_ms = best;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_mat_init(collage_t h, void* stream, int* d_axis, float* d_width) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t np = (size_t)h->d.total_pix, al = 256;
+  auto up = [&](size_t b) { return (b + al - 1) / al * al; };
+  // gcol, D2, candidates, clearances (4 B per pixel each), placed flags, candidate counts
+  const size_t need = 4 * up(4 * np) + up((size_t)h->N) + up(sizeof(int) * (size_t)h->P);
+  if (need > h->mat_bytes) {
+    CK(h, cudaDeviceSynchronize());
+    if (h->mat_buf) cudaFree(h->mat_buf);
+    h->mat_buf = nullptr;
+    h->mat_bytes = 0;
+    CK(h, cudaMalloc(&h->mat_buf, need));
+    h->mat_bytes = need;
+  }
+  unsigned char* b = h->mat_buf;
+  int* gcol = reinterpret_cast<int*>(b);
+  unsigned* d2 = reinterpret_cast<unsigned*>(b + up(4 * np));
+  int* cand = reinterpret_cast<int*>(b + 2 * up(4 * np));
+  float* clear = reinterpret_cast<float*>(b + 3 * up(4 * np));
+  uint8_t* placed = b + 4 * up(4 * np);
+  int* n_cand = reinterpret_cast<int*>(b + 4 * up(4 * np) + up((size_t)h->N));
+  CK(h, launch_adam_flush(h->d, s));  // a pending step belongs to the old params
+  int max_res = 1;
+  for (int p = 0; p < h->P; ++p) max_res = std::max(max_res, h->res[p]);
+  CK(h, launch_mat_init(h->d, s, max_res, gcol, d2, cand, n_cand, clear, placed, d_axis, d_width));
   return COLLAGE_OK;
 }
 

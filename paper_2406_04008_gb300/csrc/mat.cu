@@ -1,0 +1,210 @@
+// Skeleton-based initialisation (Sec. 4.1): the medial axis of the container and its medial width
+// (distance to the nearest boundary point), then the elements placed along the axis, larger ones
+// where the width is larger.
+//
+// On the container raster of the current level (inside: coverage >= 1/2; the pixels one step beyond
+// the image count as outside):
+//  - D2(p): the squared distance, in pixels, from an inside pixel centre to the nearest outside pixel
+//    centre (exact integers: a column pass, then per row the minimum over columns k of
+//    (j - k)^2 + g(k)^2);
+//  - the medial axis: the ridge of D2, the inside pixels that are a maximum of D2 along one of the
+//    four lines through them (horizontal, vertical, the two diagonals): D2 >= both line neighbours
+//    and > at least one (neighbours beyond the image count 0);
+//  - placement, per problem: the elements in decreasing radius r = rbin s res (pixels; ties: lower
+//    index first) each take the axis pixel of largest D2 (ties: lower pixel index) whose clearance
+//    min_j (|p - c_j| - r_j) over the elements placed so far is >= r; if no axis pixel has that
+//    clearance, the one of largest clearance.  Clearances are float32 with a fixed operation order,
+//    so every decision is reproducible.  The element's translation becomes its pixel centre;
+//    rotation and scale are kept.
+#include <cfloat>
+
+#include "collage.h"
+#include "internal.h"
+
+namespace collage {
+
+constexpr int kMatWarps = 4;
+constexpr int kPlaceThreads = 1024;
+
+__device__ __forceinline__ bool inside_px(const Dev& d, long long pix) { return d.covc[pix] >= 0.5f; }
+
+// Column pass: rows to the nearest outside pixel of the same column (rows -1 and res are outside).
+__global__ void k_mat_cols(Dev d, int* gcol, int max_res) {
+  const int p = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int res = d.prob_res[p];
+  if (k >= res || k >= max_res) return;
+  const long long pb = d.prob_pix_base[p];
+  int last = -1;
+  for (int i = 0; i < res; ++i) {
+    const long long pix = pb + (long long)i * res + k;
+    if (!inside_px(d, pix)) last = i;
+    gcol[pix] = i - last;
+  }
+  last = res;
+  for (int i = res - 1; i >= 0; --i) {
+    const long long pix = pb + (long long)i * res + k;
+    if (!inside_px(d, pix)) last = i;
+    if (last - i < gcol[pix]) gcol[pix] = last - i;
+  }
+}
+
+// Row pass, one row per warp: D2 = min over the columns k in [-1, res] of (j - k)^2 + g(k)^2, with
+// g = 0 in the two columns beyond the image; 0 for outside pixels.
+__global__ void __launch_bounds__(kMatWarps * 32) k_mat_rows(Dev d, const int* gcol, unsigned* d2,
+                                                             int max_res) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p = blockIdx.y, i = blockIdx.x * kMatWarps + wid;
+  const int res = d.prob_res[p];
+  if (i >= res || i >= max_res) return;
+  const long long rowb = d.prob_pix_base[p] + (long long)i * res;
+  for (int j = lane; j < res; j += 32) {
+    if (!inside_px(d, rowb + j)) {
+      d2[rowb + j] = 0u;
+      continue;
+    }
+    long long best = (long long)(j + 1) * (j + 1);
+    const long long right = (long long)(res - j) * (res - j);
+    if (right < best) best = right;
+    for (int k = 0; k < res; ++k) {
+      const long long g = gcol[rowb + k], dj = j - k;
+      const long long v = dj * dj + g * g;
+      best = v < best ? v : best;
+    }
+    d2[rowb + j] = (unsigned)best;
+  }
+}
+
+// Medial axis test per pixel; the axis pixels are appended to their problem's candidate list
+// (in no particular order: the placement orders them by key).
+__global__ void k_mat_axis(Dev d, const unsigned* d2, int* cand, int* n_cand, int* axis_out,
+                           float* width_out) {
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= d.total_pix) return;
+  int p = 0, lo = 0, hi = d.n_probs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.prob_pix_base[mid] <= pix) lo = mid;
+    else hi = mid - 1;
+  }
+  p = lo;
+  const long long pb = d.prob_pix_base[p];
+  const int res = d.prob_res[p];
+  const int local = (int)(pix - pb), y = local / res, x = local % res;
+  const unsigned a = d2[pix];
+  auto at = [&](int xx, int yy) -> unsigned {
+    return xx < 0 || yy < 0 || xx >= res || yy >= res ? 0u : d2[pb + (long long)yy * res + xx];
+  };
+  bool axis = false;
+  if (a > 0) {
+    const int dirs[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+    for (int k = 0; k < 4 && !axis; ++k) {
+      const unsigned u = at(x + dirs[k][0], y + dirs[k][1]), v = at(x - dirs[k][0], y - dirs[k][1]);
+      axis = a >= u && a >= v && (a > u || a > v);
+    }
+  }
+  if (axis) cand[pb + atomicAdd(&n_cand[p], 1)] = local;
+  if (axis_out) axis_out[pix] = axis ? 1 : 0;
+  if (width_out) width_out[pix] = a > 0 ? sqrtf((float)a) : 0.0f;
+}
+
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, unsigned long long* s) {
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  __syncthreads();  // the previous reduction's readers are done
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = s[threadIdx.x];
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (threadIdx.x == 0) s[0] = v;
+  }
+  __syncthreads();
+  return s[0];
+}
+
+// A float's bits as an unsigned key with the float's order (negative values included).
+__device__ __forceinline__ unsigned ordered(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Greedy placement, one block per problem.  clear[] holds each candidate's clearance, placed[] marks
+// the problem's placed elements.
+__global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, const int* cand, const int* n_cand,
+                                                             const unsigned* d2, float* clear,
+                                                             uint8_t* placed) {
+  __shared__ unsigned long long s_red[kPlaceThreads / 32];
+  const int p = blockIdx.x;
+  const int res = d.prob_res[p], nc = n_cand[p];
+  const long long pb = d.prob_pix_base[p];
+  const int e0 = d.prob_elem_base[p], e1 = d.prob_elem_base[p + 1];
+  if (nc == 0) return;  // no inside pixel: the params stay
+  const float fres = (float)res;
+  for (int c = threadIdx.x; c < nc; c += kPlaceThreads) clear[pb + c] = FLT_MAX;
+  for (int e = e0 + (int)threadIdx.x; e < e1; e += kPlaceThreads) placed[e] = 0;
+  __syncthreads();
+  for (int step = e0; step < e1; ++step) {
+    // the largest element not yet placed (radius bits, then the lower index)
+    unsigned long long ek = 0;
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += kPlaceThreads) {
+      if (placed[e]) continue;
+      const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
+      const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | (0xffffffffu - (unsigned)e);
+      ek = k > ek ? k : ek;
+    }
+    ek = block_max(ek, s_red);
+    const int e = (int)(0xffffffffu - (unsigned)(ek & 0xffffffffu));
+    const float r = __uint_as_float((unsigned)(ek >> 32));
+    // the widest axis pixel with clearance >= r (key: D2, then the lower pixel index)
+    unsigned long long ck = 0, fk = 0;
+    for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
+      const unsigned idx = (unsigned)cand[pb + c];
+      const unsigned long long low = 0xffffffffu - idx;
+      const float cl = clear[pb + c];
+      if (cl >= r) {
+        const unsigned long long k = ((unsigned long long)d2[pb + idx] << 32) | low;
+        ck = k > ck ? k : ck;
+      }
+      const unsigned long long kf = ((unsigned long long)ordered(cl) << 32) | low;
+      fk = kf > fk ? kf : fk;
+    }
+    ck = block_max(ck, s_red);
+    if (ck == 0) ck = block_max(fk, s_red);  // none has room: the largest clearance
+    const int idx = (int)(0xffffffffu - (unsigned)(ck & 0xffffffffu));
+    const int x = idx % res, y = idx / res;
+    if (threadIdx.x == 0) {
+      placed[e] = 1;
+      float4 q = d.q[e];
+      q.x = __fdiv_rn(__fadd_rn((float)x, 0.5f), fres);
+      q.y = __fdiv_rn(__fadd_rn((float)y, 0.5f), fres);
+      d.q[e] = q;
+    }
+    for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
+      const int j = cand[pb + c], dx = j % res - x, dy = j / res - y;
+      const float dist = __fsub_rn(sqrtf(__int2float_rn(dx * dx + dy * dy)), r);
+      if (dist < clear[pb + c]) clear[pb + c] = dist;
+    }
+    __syncthreads();  // placed[] and the clearances are complete before the next choice
+  }
+}
+
+cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol, unsigned* d2,
+                            int* cand, int* n_cand, float* clear, uint8_t* placed, int* axis_out,
+                            float* width_out) {
+  cudaError_t e = cudaMemsetAsync(n_cand, 0, sizeof(int) * d.n_probs, s);
+  if (e != cudaSuccess) return e;
+  k_mat_cols<<<dim3((max_res + 127) / 128, d.n_probs), 128, 0, s>>>(d, gcol, max_res);
+  k_mat_rows<<<dim3((max_res + kMatWarps - 1) / kMatWarps, d.n_probs), kMatWarps * 32, 0, s>>>(
+      d, gcol, d2, max_res);
+  const long long np = d.total_pix;
+  k_mat_axis<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(d, d2, cand, n_cand, axis_out, width_out);
+  k_mat_place<<<d.n_probs, kPlaceThreads, 0, s>>>(d, cand, n_cand, d2, clear, placed);
+  return cudaGetLastError();
+}
+
+}  // namespace collage

@@ -1,0 +1,65 @@
+"""Skeleton-based initialisation (Sec. 4.1) through the C ABI against the FP64 oracle: the medial
+width, the ridge axis and the placements are integer or float32 decisions taken the same way on both
+sides, so they are compared exactly."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2406_04008_gb300 import workloads as W
+from tests import _util as U
+
+pytestmark = pytest.mark.gpu
+
+# the inside test is coverage >= 1/2; a pixel whose coverage lies this close to 1/2 could fall
+# either way between FP32 and FP64, so the cases are checked to have none
+AMBIGUOUS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    from paper_2406_04008_gb300 import build
+    build.build()
+    from paper_2406_04008_gb300.collage import Collage
+    assert torch.cuda.is_available()
+    return oracle_mod, Collage
+
+
+def _check(env, probs, grids, **gpu):
+    O, Collage = env
+    g, o = U.paired()
+    g.update(gpu)
+    col = Collage(probs, **g)
+    axis, width = col.mat_init(want_maps=True)
+    q = col.get_params().cpu().numpy()
+    axis, width = axis.cpu().numpy(), width.cpu().numpy()
+    col.close()
+    pix = e0 = 0
+    for prob, R in zip(probs, grids):
+        _, _, covc = O.Scene(prob).render(prob["params0"].astype(np.float64), R, o)
+        assert np.abs(covc - 0.5).min() > AMBIGUOUS
+        qr, D2, ax = O.mat_init(prob, prob["params0"], R, o)
+        n = len(prob["kind"])
+        assert np.array_equal(axis[pix:pix + R * R].reshape(R, R), ax.astype(np.int32))
+        assert np.array_equal(width[pix:pix + R * R].reshape(R, R), np.sqrt(D2.astype(np.float32)))
+        assert np.array_equal(q[e0:e0 + n], qr)
+        pix += R * R
+        e0 += n
+
+
+def test_mat_init_mixed_annulus(env):
+    _check(env, [W.config_problem(3, n_elems=120, grid=256)], [256], level_res=[256], tile=8)
+
+
+def test_mat_init_open_rect_ragged(env):
+    # the open top: the rows above the image count as outside
+    _check(env, [W.config_problem(5, n_elems=150, grid=240)], [240], level_res=[240], tile=16)
+
+
+def test_mat_init_batch(env):
+    probs = [W.config_problem(4, i) for i in range(3)]
+    _check(env, probs, [int(p["grid"]) for p in probs], n_levels=1, level_res=[1], tile=8)
+
+
+def test_mat_init_headline_size(env):
+    # the 1000-element workload's container at its 1024^2 level, in the benchmark's configuration
+    _check(env, [W.config_problem(3)], [1024], level_res=[1024], tile=8, persistent=1, use_graphs=1)
