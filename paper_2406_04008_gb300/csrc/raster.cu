@@ -72,7 +72,6 @@ __device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, floa
 
 constexpr int kSegCap = 1024;   // container segments staged per chunk
 constexpr int kNearCap = 64;    // near segments staged per chunk of one (tile, element) pair
-constexpr int kStageSegs = 128; // outlines up to this many segments are staged whole per pair
 constexpr int kRowCross = 16;   // crossings listed per pixel row of a pair
 constexpr int kPairWarps = 4;   // pairs per block of the per-pair adjoint (one per warp)
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
@@ -121,9 +120,6 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d
   __shared__ float2 s_seg2[kNearCap];
   __shared__ float s_slope[kNearCap];
   __shared__ int s_idx[kNearCap];
-  __shared__ float4 s_allA[kStageSegs];   // the whole outline (when it has <= kStageSegs segments)
-  __shared__ float2 s_allB[kStageSegs];
-  __shared__ float s_allS[kStageSegs];
   __shared__ int s_back[T];
   __shared__ float s_rx[T][kRowCross];  // per pixel row: x of its crossings with near segments
   __shared__ signed char s_rd[T][kRowCross];  // and their direction
@@ -171,22 +167,14 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d
       bj[k] = -1;
       wn[k] = 0;
     }
-    // a short outline is loaded once by the whole block (one round trip) and both the compaction
-    // and the backdrop read it from shared memory; a long one is read from global memory
-    const bool staged = ns <= kStageSegs;
-    const float4* SA = staged ? s_allA : d.segA + v0;
-    const float2* SB = staged ? s_allB : d.segB + v0;
-    const float* SS = staged ? s_allS : d.segS + v0;
+    // the compaction (warp 0) and the backdrop (the other warps) read the outline from global
+    // memory side by side: the second reader finds it in L1, and no block-wide staging round and
+    // barrier precede them
+    const float4* SA = d.segA + v0;
+    const float2* SB = d.segB + v0;
+    const float* SS = d.segS + v0;
     for (int base = 0;; base += kNearCap) {
       __syncthreads();  // the previous users of the shared lists are done
-      if (base == 0 && staged) {
-        for (int j = threadIdx.x; j < ns; j += NT) {
-          s_allA[j] = d.segA[v0 + j];
-          s_allB[j] = d.segB[v0 + j];
-          s_allS[j] = d.segS[v0 + j];
-        }
-        __syncthreads();
-      }
       if (wid == 0) {
         // ordered compaction of the near segments with positions in [base, base + kNearCap)
         int cnt = 0;

@@ -111,3 +111,19 @@ def test_fit_adam_steps(env, deterministic):
     U.check_terms(now, ref, grid, (o.alpha, o.beta, o.gamma, o.delta), use_u=False)
     assert ref[0] < 0.5 * t0[0], (t0[0], ref[0], terms[0])
     col.close()
+
+
+def test_fit_step_host_moves_points_not_transforms(env):
+    # the host-buffer step in fitting mode: the transforms it returns are the fixed ones, the points
+    # move, and the loss it returns is the iteration's
+    O, Collage = env
+    prob, kw, grid, tile = _case("star20_128")
+    g, o = U.paired(**kw)
+    col = Collage(prob, level_res=[grid], tile=tile, fit_controls=1, **g)
+    p0 = np.asarray(prob["params0"], np.float32)
+    for _ in range(3):
+        pout, lout = col.step_host(1, params_in=p0)
+        assert np.array_equal(pout, p0)
+    assert not np.array_equal(col.get_controls().cpu().numpy(), _pts(prob))
+    assert np.array_equal(lout, col.loss().cpu().numpy().reshape(-1))
+    col.close()

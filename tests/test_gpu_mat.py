@@ -63,3 +63,18 @@ def test_mat_init_batch(env):
 def test_mat_init_headline_size(env):
     # the 1000-element workload's container at its 1024^2 level, in the benchmark's configuration
     _check(env, [W.config_problem(3)], [1024], level_res=[1024], tile=8, persistent=1, use_graphs=1)
+
+
+def test_mat_init_empty_container_keeps_params(env):
+    # a container smaller than a pixel has no inside pixel at 64^2: nothing moves, no axis
+    O, Collage = env
+    rng = W.PCG32(3)
+    els = [(1, W.regular_polygon(0.05, 6), 0.0), (0, W.blob_controls(rng, 0.04), 0.0)]
+    params = [(0.3, 0.4, 0.5, 1.0), (0.6, 0.7, 1.0, 1.2)]
+    prob = W.make_problem(els, [W.regular_polygon(0.002, 8) + (0.5, 0.5)], params, 64)
+    g, o = U.paired()
+    col = Collage(prob, level_res=[64], tile=8, **g)
+    axis, width = col.mat_init(want_maps=True)
+    assert not axis.any().item() and not width.any().item()
+    assert np.array_equal(col.get_params().cpu().numpy().reshape(-1), prob["params0"])
+    col.close()
