@@ -364,17 +364,25 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(Dev d) {
   }
 }
 
-// Deterministic mode: each element sums its (tile, element) partials over its tile rectangle in
-// row-major order (a tile's list is ordered by element id, so the pair is found by bisection).
-__device__ __forceinline__ void grad_reduce_one(const Dev& d, int g) {
-  const int4 rc = d.rect[g];
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (rc.z >= rc.x && rc.w >= rc.y) {
-    const int p = d.elem_prob[g];
-    const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
-    for (int ty = rc.y; ty <= rc.w; ++ty)
-      for (int tx = rc.x; tx <= rc.z; ++tx) {
-        const uint2 rg = d.range[tb + ty * ntx + tx];
+// Deterministic mode: each element sums its (tile, element) partials over its tile rectangle, one
+// warp per element: lane l takes the tiles l, l + 32, ... of the rectangle in row-major order (a
+// tile's list is ordered by element id, so the pair is found by bisection) and the 32 lane sums are
+// added by a fixed shuffle tree; the order of every addition is fixed, so the result is bitwise
+// reproducible.
+constexpr int kReduceWarps = 8;
+__global__ void __launch_bounds__(kReduceWarps * 32) k_grad_reduce(Dev d, int mark) {
+  pdl_enter();
+  const int lane = threadIdx.x & 31;
+  const int g = blockIdx.x * kReduceWarps + (threadIdx.x >> 5);
+  if (g < d.n_elems && !(*d.status & kStatusOverflow)) {
+    const int4 rc = d.rect[g];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rc.z >= rc.x && rc.w >= rc.y) {
+      const int p = d.elem_prob[g];
+      const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
+      const int w = rc.z - rc.x + 1, n = w * (rc.w - rc.y + 1);
+      for (int i = lane; i < n; i += 32) {
+        const uint2 rg = d.range[tb + (rc.y + i / w) * ntx + rc.x + i % w];
         unsigned lo = rg.x, hi = rg.y;  // first entry >= g
         while (lo < hi) {
           const unsigned mid = (lo + hi) >> 1;
@@ -389,14 +397,15 @@ __device__ __forceinline__ void grad_reduce_one(const Dev& d, int g) {
           acc.w += v.w;
         }
       }
+    }
+    for (int o = 16; o; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+      acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    }
+    if (lane == 0) d.dq[g] = acc;
   }
-  d.dq[g] = acc;
-}
-
-__global__ void k_grad_reduce(Dev d, int mark) {
-  pdl_enter();
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < d.n_elems && !(*d.status & kStatusOverflow)) grad_reduce_one(d, g);
   if (mark) mark_step_if_last(d);
 }
 
@@ -497,7 +506,8 @@ cudaError_t launch_loss(const Dev& d, cudaStream_t s) {
 }
 
 cudaError_t launch_grad_reduce(const Dev& d, cudaStream_t s, bool mark_step) {
-  return klaunch(d.pdl, k_grad_reduce, (d.n_elems + 255) / 256, 256, 0, s, d, mark_step ? 1 : 0);
+  return klaunch(d.pdl, k_grad_reduce, (d.n_elems + kReduceWarps - 1) / kReduceWarps, kReduceWarps * 32, 0,
+                 s, d, mark_step ? 1 : 0);
 }
 
 cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s, float* out) {
