@@ -380,6 +380,7 @@ static collage_status setup_level(collage_t h, int level) {
     CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
     CK(h, dmalloc(h->level_bufs, d.range, nt));
     CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
+    CK(h, dmalloc(h->level_bufs, d.scan_part, (size_t)scan_rounds((int)nt)));
     CK(h, dmalloc(h->level_bufs, d.lossA, nt));
     CK(h, dmalloc(h->level_bufs, d.lossU, nd));
     CK(h, dmalloc(h->level_bufs, d.dtile_flags, nd));
@@ -1154,7 +1155,8 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   // transform (with the previous Adam step), tile scan, emit, pair distances, composite,
   // (2 dilation), raster bwd, (gradient reduce), loss
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 5 + (dil ? 2 : 0) + 1 + (h->d.deterministic ? 1 : 0) + 1 + (h->d.fit ? 1 : 0);
+  out->kernels_per_iter = 5 + (scan_rounds(h->d.total_tiles) > 1 ? 2 : 0) + (dil ? 2 : 0) + 1 +
+                         (h->d.deterministic ? 1 : 0) + 1 + (h->d.fit ? 1 : 0);
   return COLLAGE_OK;
 }
 

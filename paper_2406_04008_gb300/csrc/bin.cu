@@ -181,38 +181,108 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     atomicAdd(&d.tile_cnt[tb + (r.y + i / w) * ntx + r.x + i % w], 1);
 }
 
-// Exclusive scan of the per-tile counts into [begin, end) ranges: one block, rounds of 16384
-// tiles; each thread loads 16 consecutive counts with vector loads, scans them in registers, the
-// block scans the per-thread totals, and the thread writes its 16 ranges with vector stores.  The
-// total is the pair count; above the capacity the overflow bit is latched.
+// Exclusive scan of the per-tile counts into [begin, end) ranges, in rounds of 16384 tiles: each
+// thread loads 16 consecutive counts with vector loads, scans them in registers, the block scans
+// the per-thread totals, and the thread writes its 16 ranges with vector stores.  The total is the
+// pair count; above the capacity the overflow bit is latched.  Up to one round the scan is one
+// block; beyond that the rounds run as separate blocks (ranges relative to their round), one block
+// scans the round totals into offsets, and a third kernel adds each round's offset.
 constexpr int kScanThreads = 1024, kScanPer = 16, kScanRound = kScanThreads * kScanPer;
+
+// The round of counts from `base`, its ranges written from `carry`; returns the round's total.
+__device__ __forceinline__ int scan_round(const Dev& d, int base, int carry, int* wsum) {
+  const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int i0 = base + t * kScanPer;
+  const bool full = i0 + kScanPer <= n;
+  int v[kScanPer];
+  if (full) {
+    const int4* src = reinterpret_cast<const int4*>(d.tile_cnt + i0);
+#pragma unroll
+    for (int q = 0; q < kScanPer / 4; ++q) {
+      const int4 a = src[q];
+      v[4 * q] = a.x;
+      v[4 * q + 1] = a.y;
+      v[4 * q + 2] = a.z;
+      v[4 * q + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) v[i] = i0 + i < n ? d.tile_cnt[i0 + i] : 0;
+  }
+  int s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) s += v[i];
+  int x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int ws = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ws, o);
+      if (lane >= o) ws += y;
+    }
+    wsum[lane] = ws;  // inclusive
+  }
+  __syncthreads();
+  int run = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
+  const int round_total = wsum[31];
+  unsigned st[kScanPer + 1];
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    st[i] = (unsigned)run;
+    run += v[i];
+  }
+  st[kScanPer] = (unsigned)run;
+  if (full) {
+    uint4* dst = reinterpret_cast<uint4*>(d.range + i0);
+#pragma unroll
+    for (int q = 0; q < kScanPer / 2; ++q)
+      dst[q] = make_uint4(st[2 * q], st[2 * q + 1], st[2 * q + 1], st[2 * q + 2]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i)
+      if (i0 + i < n) d.range[i0 + i] = make_uint2(st[i], st[i + 1]);
+  }
+  __syncthreads();  // wsum is reused by the next round
+  return round_total;
+}
+
+// The pair count, the overflow bit, and the per-iteration counters cleared.
+__device__ __forceinline__ void scan_finish(const Dev& d, int total) {
+  *d.total_pairs = total;
+  if (total > d.cap) atomicOr(d.status, kStatusOverflow);
+  *d.pending = 0;  // every transform block has applied the pending Adam step
+  for (int i = 0; i < 8; ++i) d.work[i] = 0;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
   pdl_enter();
   __shared__ int wsum[32];
-  const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
   int carry = 0;
-  for (int base = 0; base < n; base += kScanRound) {
-    const int i0 = base + t * kScanPer;
-    const bool full = i0 + kScanPer <= n;
-    int v[kScanPer];
-    if (full) {
-      const int4* src = reinterpret_cast<const int4*>(d.tile_cnt + i0);
-#pragma unroll
-      for (int q = 0; q < kScanPer / 4; ++q) {
-        const int4 a = src[q];
-        v[4 * q] = a.x;
-        v[4 * q + 1] = a.y;
-        v[4 * q + 2] = a.z;
-        v[4 * q + 3] = a.w;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < kScanPer; ++i) v[i] = i0 + i < n ? d.tile_cnt[i0 + i] : 0;
-    }
-    int s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i) s += v[i];
-    int x = s;
+  for (int base = 0; base < d.total_tiles; base += kScanRound) carry += scan_round(d, base, carry, wsum);
+  if (threadIdx.x == 0) scan_finish(d, carry);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_rounds(Dev d) {
+  pdl_enter();
+  __shared__ int wsum[32];
+  const int total = scan_round(d, blockIdx.x * kScanRound, 0, wsum);
+  if (threadIdx.x == 0) d.scan_part[blockIdx.x] = total;
+}
+
+// One block: the round totals into exclusive offsets (in place), then the scan's finish.
+__global__ void __launch_bounds__(kScanThreads) k_scan_offsets(Dev d, int rounds) {
+  pdl_enter();
+  __shared__ int wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int carry = 0;
+  for (int base = 0; base < rounds; base += kScanThreads) {
+    const int v = base + t < rounds ? d.scan_part[base + t] : 0;
+    int x = v;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -225,36 +295,25 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
         const int y = __shfl_up_sync(0xffffffffu, ws, o);
         if (lane >= o) ws += y;
       }
-      wsum[lane] = ws;  // inclusive
+      wsum[lane] = ws;
     }
     __syncthreads();
-    int run = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
-    const int round_total = wsum[31];
-    unsigned st[kScanPer + 1];
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-      st[i] = (unsigned)run;
-      run += v[i];
-    }
-    st[kScanPer] = (unsigned)run;
-    if (full) {
-      uint4* dst = reinterpret_cast<uint4*>(d.range + i0);
-#pragma unroll
-      for (int q = 0; q < kScanPer / 2; ++q)
-        dst[q] = make_uint4(st[2 * q], st[2 * q + 1], st[2 * q + 1], st[2 * q + 2]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kScanPer; ++i)
-        if (i0 + i < n) d.range[i0 + i] = make_uint2(st[i], st[i + 1]);
-    }
-    carry += round_total;
-    __syncthreads();  // wsum is reused by the next round
+    if (base + t < rounds) d.scan_part[base + t] = carry + x - v + (w > 0 ? wsum[w - 1] : 0);
+    carry += wsum[31];
+    __syncthreads();
   }
-  if (t == 0) {
-    *d.total_pairs = carry;
-    if (carry > d.cap) atomicOr(d.status, kStatusOverflow);
-    *d.pending = 0;  // every transform block has applied the pending Adam step
-    for (int i = 0; i < 8; ++i) d.work[i] = 0;
+  if (t == 0) scan_finish(d, carry);
+}
+
+// Each round's ranges moved by the round's offset.
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(Dev d) {
+  pdl_enter();
+  if (blockIdx.x == 0) return;  // the first round starts at 0
+  const unsigned off = (unsigned)d.scan_part[blockIdx.x];
+  const int i0 = blockIdx.x * kScanRound + threadIdx.x * kScanPer;
+  for (int i = i0; i < i0 + kScanPer && i < d.total_tiles; ++i) {
+    const uint2 r = d.range[i];
+    d.range[i] = make_uint2(r.x + off, r.y + off);
   }
 }
 
@@ -386,8 +445,15 @@ cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad) {
 }
 
 cudaError_t launch_scan(const Dev& d, cudaStream_t s) {
-  return klaunch(d.pdl, k_tile_scan, 1, kScanThreads, 0, s, d);
+  const int rounds = (d.total_tiles + kScanRound - 1) / kScanRound;
+  if (rounds <= 1 || !d.scan_part) return klaunch(d.pdl, k_tile_scan, 1, kScanThreads, 0, s, d);
+  cudaError_t e = klaunch(d.pdl, k_scan_rounds, rounds, kScanThreads, 0, s, d);
+  if (e == cudaSuccess) e = klaunch(d.pdl, k_scan_offsets, 1, kScanThreads, 0, s, d, rounds);
+  if (e == cudaSuccess) e = klaunch(d.pdl, k_scan_add, rounds, kScanThreads, 0, s, d);
+  return e;
 }
+
+int scan_rounds(int total_tiles) { return (total_tiles + kScanRound - 1) / kScanRound; }
 
 cudaError_t launch_bin(const Dev& d, cudaStream_t s) {
   return klaunch(d.pdl, k_emit, d.n_elems, kEmitThreads, 0, s, d);

@@ -79,6 +79,7 @@ struct Dev {
   float4* bbox;                 // [n] outline box relative to the translation, grown by the margin
   int4* rect;                   // [n] tile rectangle (tx0, ty0, tx1, ty1), empty if tx1 < tx0
   int* tile_cnt;                // [total_tiles] counting-sort counts (zero between iterations)
+  int* scan_part;               // [scan rounds] round totals, then offsets (levels above one round)
   int* total_pairs;             // [1]
   int cap;                      // pair capacity
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
@@ -217,6 +218,7 @@ __device__ __forceinline__ void mark_step_if_last(const Dev& d) {
 // ---- launchers (each enqueues on `s`, returns the launch error) ----
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
 cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
+int scan_rounds(int total_tiles);                                 // rounds (blocks) of the scan
 cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit pairs into tile ranges
 cudaError_t launch_container(const Dev& d, cudaStream_t s);
 // part 1: per-pair signed distances; part 2: per-tile composite and loss partials; 3: both
