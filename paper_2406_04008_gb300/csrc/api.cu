@@ -55,6 +55,8 @@ struct collage_s {
   int* h_ctl = nullptr;      // pinned mirror
   float* d_stage = nullptr;  // device: params, loss terms and control words gathered for one copy
   float* h_stage = nullptr;  // pinned: their host copy ([4n | 5 n_probs | 4], see k_adam_flush)
+  float* h_stage_dev = nullptr;  // h_stage mapped into the device's address space (or null): the
+                                 // gathering kernel then writes the host copy itself
   bool ctl_current = false;  // h_ctl[1] (step count) and h_ctl[3] (pending) are the device's:
                              // no step was enqueued since the last read
   cudaStream_t cap_stream = nullptr;
@@ -743,7 +745,11 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.prob_pix_base = h->d_prob_pix_base;
   CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
   CKC(dmalloc(h->owned, h->d_stage, stage_floats(h)));
-  CKC(cudaMallocHost(&h->h_stage, sizeof(float) * stage_floats(h)));
+  CKC(cudaHostAlloc(&h->h_stage, sizeof(float) * stage_floats(h), cudaHostAllocMapped));
+  if (cudaHostGetDevicePointer(&h->h_stage_dev, h->h_stage, 0) != cudaSuccess) {
+    h->h_stage_dev = nullptr;
+    cudaGetLastError();
+  }
   CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CKC(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
   CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -862,8 +868,12 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
   st = enqueue_steps(h, s, n_iters);
   if (st) return st;
   auto copy_out = [&]() -> collage_status {
-    CK(h, launch_adam_flush(h->d, s, h->d_stage));
-    CK(h, cudaMemcpyAsync(h->h_stage, h->d_stage, sizeof(float) * stage_floats(h), cudaMemcpyDeviceToHost, s));
+    if (h->h_stage_dev) {
+      CK(h, launch_adam_flush(h->d, s, h->h_stage_dev));
+    } else {
+      CK(h, launch_adam_flush(h->d, s, h->d_stage));
+      CK(h, cudaMemcpyAsync(h->h_stage, h->d_stage, sizeof(float) * stage_floats(h), cudaMemcpyDeviceToHost, s));
+    }
     CK(h, cudaStreamSynchronize(s));
     const float* tail = h->h_stage + 4 * (size_t)h->N;
     if (h_params_out) std::memcpy(h_params_out, h->h_stage, sizeof(float4) * h->N);
