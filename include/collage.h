@@ -169,9 +169,10 @@ collage_status collage_run_schedule(collage_t h, void* stream);
 /* Host-buffer form of collage_step for callers without device memory: copies h_params_in
  * [4*n_elems] (NULL = keep) to the device, runs n_iters iterations, copies the params to
  * h_params_out [4*n_elems] and the last loss terms to h_loss_out [n_probs*5] (either NULL = skip)
- * and synchronises.  Pinned host memory is faster but not required.  Unless a bin overflow has to
- * be recovered (as collage_step does), the copies, the iterations and the status check share one
- * host round trip. */
+ * and synchronises.  Pinned host memory is faster but not required; the outputs are gathered by
+ * one kernel into a mapped (page-locked) staging buffer of the handle.  Unless a bin overflow has
+ * to be recovered (as collage_step does), the transfers, the iterations and the status check share
+ * one host round trip. */
 collage_status collage_step_host(collage_t h, void* stream, int n_iters, const float* h_params_in,
                                  float* h_params_out, float* h_loss_out);
 
