@@ -133,6 +133,9 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d
   // shared counter as blocks finish (pair costs vary by two orders of magnitude); s_next is
   // double-buffered so that thread 0's next write never meets a read of the previous value
   __shared__ int s_next[2];
+  constexpr int kLiveBatch = 8;
+  __shared__ int4 s_live[kLiveBatch];
+  int n_live = 0;  // thread 0's count of buffered live records
   for (int i = blockIdx.x, it = 0; i < n_near; ++it) {
     if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
     const int4 rec = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
@@ -304,10 +307,23 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d
     }
     live = __syncthreads_or(live);
     if (threadIdx.x == 0) {
-      if (live) d.live_list[atomicAdd(&d.work[1], 1)] = rec;
-      else if (d.deterministic) d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (live) {
+        // live pairs are appended kLiveBatch at a time: one atomic per batch
+        s_live[n_live++] = rec;
+        if (n_live == kLiveBatch) {
+          const int at = atomicAdd(&d.work[1], kLiveBatch);
+          for (int q = 0; q < kLiveBatch; ++q) d.live_list[at + q] = s_live[q];
+          n_live = 0;
+        }
+      } else if (d.deterministic) {
+        d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     i = s_next[it & 1];
+  }
+  if (threadIdx.x == 0 && n_live > 0) {
+    const int at = atomicAdd(&d.work[1], n_live);
+    for (int q = 0; q < n_live; ++q) d.live_list[at + q] = s_live[q];
   }
 }
 
