@@ -202,12 +202,34 @@ def run_reference(args):
 
 
 def run_profile(args):
-    """A fixed launch sequence for ncu: level 1024^2, W eager warm-up iterations, N eager ones."""
+    """A fixed launch sequence for ncu: level 1024^2, W eager warm-up iterations, N eager ones.
+    --profile-workload fit20: the outline fitting of one 20-cubic star at 256^2 instead;
+    mat_init: N skeleton-based initialisations of the 1024^2 workload."""
     import torch
 
     from paper_2406_04008_gb300 import build
     build.build()
     from paper_2406_04008_gb300.collage import Collage
+    if args.profile_workload == "fit20":
+        from paper_2406_04008_gb300 import workloads as W
+        kw = dict(W.FIT_LOSS)
+        kw["delta_down"] = kw.pop("delta")
+        col = Collage(W.fit_problem(0), fit_controls=1, n_levels=1, level_res=[256], level_iters=[50],
+                      n_dilations=0, use_graphs=0, persistent=1, tile=args.tile, **kw)
+        col.step(args.warmup)
+        col.step(args.profile_iters)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_iters": args.profile_iters, "info": col.info()}))
+        col.close()
+        return
+    if args.profile_workload == "mat_init":
+        col = Collage(_workload(), level_res=[1024], tile=args.tile)
+        for _ in range(args.warmup + args.profile_iters):
+            col.mat_init()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_iters": args.profile_iters, "info": col.info()}))
+        col.close()
+        return
     col = Collage(_workload(), **_opts(use_graphs=0, persistent=1, tile=args.tile))
     col.set_level(3)
     col.step(args.warmup)
@@ -417,6 +439,8 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="for ncu: W warm-up then N eager iterations of the 1024^2 step, no timing")
     ap.add_argument("--tile", type=int, default=16, help="raster tile of --profile-iters")
+    ap.add_argument("--profile-workload", default="mixed1000", choices=["mixed1000", "fit20", "mat_init"],
+                    help="what --profile-iters runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -23,17 +23,36 @@ __device__ __forceinline__ void bernstein(int j, int spc, double (&b)[4]) {
   b[3] = __dmul_rn(__dmul_rn(t, t), t);
 }
 
+constexpr int kBernMax = 256;  // samples per curve whose weights are tabled in shared memory
+
 // mode 0: dv -> dctrl, dv cleared; 1: the same, then an Adam step on the points (step *d.step,
 // the update adam_update makes, without a clamp) and the flattening; 2: the flattening only.
 __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
   pdl_enter();
   __shared__ double s_r[kCtrlThreads / 32];
+  __shared__ double s_w[kBernMax][4];  // the Bernstein weights of the samples, formed once
   if (mode != 2 && (*d.status & (kStatusOverflow | kStatusBadParam))) return;  // a void iteration
   const int g = blockIdx.x;
   const int c0 = d.elem_coff[g], np = d.elem_coff[g + 1] - c0;
   const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
   const bool cubic = d.elem_cubic[g] != 0;
   const int spc = d.spc, ncurve = np / 3;
+  const bool table = cubic && spc <= kBernMax;
+  if (table) {
+    for (int j = threadIdx.x; j < spc; j += kCtrlThreads) {
+      double b[4];
+      bernstein(j, spc, b);
+      for (int r = 0; r < 4; ++r) s_w[j][r] = b[r];
+    }
+    __syncthreads();
+  }
+  // weight r of sample j (from the table when there is one)
+  auto weight = [&](int j, int r) -> double {
+    if (table) return s_w[j][r];
+    double b[4];
+    bernstein(j, spc, b);
+    return b[r];
+  };
   if (mode != 2) {
     // point k of a cubic path is entry k % 3 of curve k / 3; an anchor (k % 3 = 0) is also entry 3
     // of the previous curve.  A fixed order over the samples: the sums are reproducible given dv.
@@ -46,10 +65,8 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
         gk = d.dv[v0 + k];
       } else {
         const int c = k / 3, r = k % 3;
-        double b[4];
         for (int j = 0; j < spc; ++j) {
-          bernstein(j, spc, b);
-          const float w = (float)b[r];
+          const float w = (float)weight(j, r);
           const float2 gv = d.dv[v0 + c * spc + j];
           gk.x = fmaf(w, gv.x, gk.x);
           gk.y = fmaf(w, gv.y, gk.y);
@@ -57,8 +74,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
         if (r == 0) {
           const int cp = c == 0 ? ncurve - 1 : c - 1;
           for (int j = 0; j < spc; ++j) {
-            bernstein(j, spc, b);
-            const float w = (float)b[3];
+            const float w = (float)weight(j, 3);
             const float2 gv = d.dv[v0 + cp * spc + j];
             gk.x = fmaf(w, gv.x, gk.x);
             gk.y = fmaf(w, gv.y, gk.y);
@@ -91,13 +107,12 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
       continue;
     }
     const int c = i / spc, j = i % spc;
-    double b[4];
-    bernstein(j, spc, b);
     double x = 0.0, y = 0.0;
     for (int r = 0; r < 4; ++r) {
       const float2 p = d.ctrl[c0 + (3 * c + r) % np];
-      x = __dadd_rn(x, __dmul_rn(b[r], (double)p.x));
-      y = __dadd_rn(y, __dmul_rn(b[r], (double)p.y));
+      const double w = weight(j, r);
+      x = __dadd_rn(x, __dmul_rn(w, (double)p.x));
+      y = __dadd_rn(y, __dmul_rn(w, (double)p.y));
     }
     d.vloc[v0 + i] = make_float2(__double2float_rn(x), __double2float_rn(y));
   }
