@@ -1086,8 +1086,8 @@ extern "C" collage_status collage_mat_init(collage_t h, void* stream, int* d_axi
   cudaStream_t s = (cudaStream_t)stream;
   const size_t np = (size_t)h->d.total_pix, al = 256;
   auto up = [&](size_t b) { return (b + al - 1) / al * al; };
-  // gcol, D2, candidates, clearances (4 B per pixel each), placed flags, candidate counts
-  const size_t need = 4 * up(4 * np) + up((size_t)h->N) + up(sizeof(int) * (size_t)h->P);
+  // gcol, D2, candidates, clearances (4 B per pixel each), placement order, candidate counts
+  const size_t need = 4 * up(4 * np) + up(sizeof(int) * (size_t)h->N) + up(sizeof(int) * (size_t)h->P);
   if (need > h->mat_bytes) {
     CK(h, cudaDeviceSynchronize());
     if (h->mat_buf) cudaFree(h->mat_buf);
@@ -1101,12 +1101,12 @@ extern "C" collage_status collage_mat_init(collage_t h, void* stream, int* d_axi
   unsigned* d2 = reinterpret_cast<unsigned*>(b + up(4 * np));
   int* cand = reinterpret_cast<int*>(b + 2 * up(4 * np));
   float* clear = reinterpret_cast<float*>(b + 3 * up(4 * np));
-  uint8_t* placed = b + 4 * up(4 * np);
-  int* n_cand = reinterpret_cast<int*>(b + 4 * up(4 * np) + up((size_t)h->N));
+  int* order = reinterpret_cast<int*>(b + 4 * up(4 * np));
+  int* n_cand = reinterpret_cast<int*>(b + 4 * up(4 * np) + up(sizeof(int) * (size_t)h->N));
   CK(h, launch_adam_flush(h->d, s));  // a pending step belongs to the old params
   int max_res = 1;
   for (int p = 0; p < h->P; ++p) max_res = std::max(max_res, h->res[p]);
-  CK(h, launch_mat_init(h->d, s, max_res, gcol, d2, cand, n_cand, clear, placed, d_axis, d_width));
+  CK(h, launch_mat_init(h->d, s, max_res, gcol, d2, cand, n_cand, clear, order, d_axis, d_width));
   return COLLAGE_OK;
 }
 

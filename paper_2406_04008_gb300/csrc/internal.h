@@ -238,7 +238,7 @@ cudaError_t launch_adam_flush(const Dev& d, cudaStream_t s, float* out = nullptr
 cudaError_t launch_ctrl_step(const Dev& d, cudaStream_t s, int mode);
 // skeleton-based initialisation: distance transform, medial axis, greedy placement into d.q
 cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol, unsigned* d2,
-                            int* cand, int* n_cand, float* clear, uint8_t* placed, int* axis_out,
+                            int* cand, int* n_cand, float* clear, int* order, int* axis_out,
                             float* width_out);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);

@@ -133,41 +133,84 @@ __device__ __forceinline__ unsigned ordered(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Greedy placement, one block per problem.  clear[] holds each candidate's clearance, placed[] marks
-// the problem's placed elements.
-__global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, const int* cand, const int* n_cand,
-                                                             const unsigned* d2, float* clear,
-                                                             uint8_t* placed) {
+// Greedy placement, one block per problem.  First every axis pixel's D2 and packed coordinates are
+// gathered into per-candidate arrays (cand and gxy), and the elements are ranked by radius (ties:
+// lower index) into order[]; then each step is one pass over the candidates: the clearances take the
+// previous element's disk into account and the next element's choice is reduced over the block.
+constexpr int kPlaceRankMax = 4096;  // elements ranked in shared memory (more: a reduction per step)
+
+__device__ __forceinline__ unsigned long long elem_key(const Dev& d, int e, float fres) {
+  const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
+  return ((unsigned long long)__float_as_uint(r) << 32) | (0xffffffffu - (unsigned)e);
+}
+
+__global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, const int* n_cand,
+                                                             const unsigned* d2, float* clear, int* gxy,
+                                                             int* order) {
   __shared__ unsigned long long s_red[kPlaceThreads / 32];
+  __shared__ unsigned long long s_key[kPlaceRankMax];
   const int p = blockIdx.x;
   const int res = d.prob_res[p], nc = n_cand[p];
   const long long pb = d.prob_pix_base[p];
-  const int e0 = d.prob_elem_base[p], e1 = d.prob_elem_base[p + 1];
+  const int e0 = d.prob_elem_base[p], e1 = d.prob_elem_base[p + 1], ne = e1 - e0;
   if (nc == 0) return;  // no inside pixel: the params stay
   const float fres = (float)res;
-  for (int c = threadIdx.x; c < nc; c += kPlaceThreads) clear[pb + c] = FLT_MAX;
-  for (int e = e0 + (int)threadIdx.x; e < e1; e += kPlaceThreads) placed[e] = 0;
-  __syncthreads();
-  for (int step = e0; step < e1; ++step) {
-    // the largest element not yet placed (radius bits, then the lower index)
-    unsigned long long ek = 0;
-    for (int e = e0 + (int)threadIdx.x; e < e1; e += kPlaceThreads) {
-      if (placed[e]) continue;
-      const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
-      const unsigned long long k = ((unsigned long long)__float_as_uint(r) << 32) | (0xffffffffu - (unsigned)e);
-      ek = k > ek ? k : ek;
+  // per candidate: D2 (in place of the pixel index) and x | y << 16, the clearance
+  for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
+    const int idx = cand[pb + c];
+    cand[pb + c] = (int)d2[pb + idx];
+    gxy[pb + c] = (idx % res) | ((idx / res) << 16);
+    clear[pb + c] = FLT_MAX;
+  }
+  // the elements in placement order: decreasing key (radius bits, then the lower index)
+  const bool ranked = ne <= kPlaceRankMax;
+  if (ranked) {
+    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) s_key[i] = elem_key(d, e0 + i, fres);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
+      const unsigned long long k = s_key[i];
+      int rank = 0;
+      for (int j = 0; j < ne; ++j) rank += s_key[j] > k ? 1 : 0;
+      order[e0 + rank] = e0 + i;
     }
-    ek = block_max(ek, s_red);
-    const int e = (int)(0xffffffffu - (unsigned)(ek & 0xffffffffu));
-    const float r = __uint_as_float((unsigned)(ek >> 32));
-    // the widest axis pixel with clearance >= r (key: D2, then the lower pixel index)
+  } else {
+    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) order[e0 + i] = 0;  // 0: not placed yet
+  }
+  __syncthreads();
+  int px = 0, py = 0;  // the previous element's pixel and radius (none before the first step)
+  float pr = -1.0f;
+  for (int step = 0; step < ne; ++step) {
+    int e;
+    if (ranked) {
+      e = order[e0 + step];
+    } else {  // the largest element not yet placed, by a reduction
+      unsigned long long ek = 0;
+      for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
+        if (order[e0 + i]) continue;
+        const unsigned long long k = elem_key(d, e0 + i, fres);
+        ek = k > ek ? k : ek;
+      }
+      ek = block_max(ek, s_red);
+      e = (int)(0xffffffffu - (unsigned)(ek & 0xffffffffu));
+    }
+    const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
+    // one pass: the previous element's disk into the clearances, then the widest axis pixel with
+    // clearance >= r (key: D2, then the lower pixel index), and the largest clearance as fallback
     unsigned long long ck = 0, fk = 0;
     for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
-      const unsigned idx = (unsigned)cand[pb + c];
-      const unsigned long long low = 0xffffffffu - idx;
-      const float cl = clear[pb + c];
+      const int xy = gxy[pb + c], x = xy & 0xffff, y = xy >> 16;
+      float cl = clear[pb + c];
+      if (pr >= 0.0f) {
+        const int dx = x - px, dy = y - py;
+        const float dist = __fsub_rn(sqrtf(__int2float_rn(dx * dx + dy * dy)), pr);
+        if (dist < cl) {
+          cl = dist;
+          clear[pb + c] = cl;
+        }
+      }
+      const unsigned long long low = 0xffffffffu - (unsigned)(y * res + x);
       if (cl >= r) {
-        const unsigned long long k = ((unsigned long long)d2[pb + idx] << 32) | low;
+        const unsigned long long k = ((unsigned long long)(unsigned)cand[pb + c] << 32) | low;
         ck = k > ck ? k : ck;
       }
       const unsigned long long kf = ((unsigned long long)ordered(cl) << 32) | low;
@@ -176,25 +219,22 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, const int* c
     ck = block_max(ck, s_red);
     if (ck == 0) ck = block_max(fk, s_red);  // none has room: the largest clearance
     const int idx = (int)(0xffffffffu - (unsigned)(ck & 0xffffffffu));
-    const int x = idx % res, y = idx / res;
+    px = idx % res;
+    py = idx / res;
+    pr = r;
     if (threadIdx.x == 0) {
-      placed[e] = 1;
+      if (!ranked) order[e] = 1;
       float4 q = d.q[e];
-      q.x = __fdiv_rn(__fadd_rn((float)x, 0.5f), fres);
-      q.y = __fdiv_rn(__fadd_rn((float)y, 0.5f), fres);
+      q.x = __fdiv_rn(__fadd_rn((float)px, 0.5f), fres);
+      q.y = __fdiv_rn(__fadd_rn((float)py, 0.5f), fres);
       d.q[e] = q;
     }
-    for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
-      const int j = cand[pb + c], dx = j % res - x, dy = j / res - y;
-      const float dist = __fsub_rn(sqrtf(__int2float_rn(dx * dx + dy * dy)), r);
-      if (dist < clear[pb + c]) clear[pb + c] = dist;
-    }
-    __syncthreads();  // placed[] and the clearances are complete before the next choice
+    __syncthreads();  // the choice is complete before the next pass (the unranked flags too)
   }
 }
 
 cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol, unsigned* d2,
-                            int* cand, int* n_cand, float* clear, uint8_t* placed, int* axis_out,
+                            int* cand, int* n_cand, float* clear, int* order, int* axis_out,
                             float* width_out) {
   cudaError_t e = cudaMemsetAsync(n_cand, 0, sizeof(int) * d.n_probs, s);
   if (e != cudaSuccess) return e;
@@ -203,7 +243,8 @@ cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol
       d, gcol, d2, max_res);
   const long long np = d.total_pix;
   k_mat_axis<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(d, d2, cand, n_cand, axis_out, width_out);
-  k_mat_place<<<d.n_probs, kPlaceThreads, 0, s>>>(d, cand, n_cand, d2, clear, placed);
+  // gcol is free after the row pass: it holds the candidates' coordinates
+  k_mat_place<<<d.n_probs, kPlaceThreads, 0, s>>>(d, cand, n_cand, d2, clear, gcol, order);
   return cudaGetLastError();
 }
 

@@ -78,3 +78,15 @@ def test_mat_init_empty_container_keeps_params(env):
     assert not axis.any().item() and not width.any().item()
     assert np.array_equal(col.get_params().cpu().numpy().reshape(-1), prob["params0"])
     col.close()
+
+
+def test_mat_init_more_elements_than_ranked(env):
+    # past 4096 elements the placement takes the largest remaining element by a reduction per step
+    # instead of a precomputed order: the same rule, the same result
+    rng = W.PCG32(8)
+    els, params = [], []
+    for _ in range(4200):
+        els.append((1, W.regular_polygon(0.002 + 0.004 * rng.uniform(), 5), 0.0))
+        params.append((0.5, 0.5, 0.0, 0.6 + 0.8 * rng.uniform()))
+    prob = W.make_problem(els, W.annulus_container(), params, 256)
+    _check(env, [prob], [256], level_res=[256], tile=16)
