@@ -34,17 +34,38 @@ __global__ void k_mat_cols(Dev d, int* gcol, int max_res) {
   const int res = d.prob_res[p];
   if (k >= res || k >= max_res) return;
   const long long pb = d.prob_pix_base[p];
+  // rows in groups of 8 whose coverages are read together (the loads are independent; only the
+  // running index of the last outside pixel carries from row to row)
+  constexpr int G = 8;
   int last = -1;
-  for (int i = 0; i < res; ++i) {
-    const long long pix = pb + (long long)i * res + k;
-    if (!inside_px(d, pix)) last = i;
-    gcol[pix] = i - last;
+  for (int i0 = 0; i0 < res; i0 += G) {
+    bool out[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) out[u] = i0 + u < res && !inside_px(d, pb + (long long)(i0 + u) * res + k);
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      if (i0 + u >= res) break;
+      if (out[u]) last = i0 + u;
+      gcol[pb + (long long)(i0 + u) * res + k] = i0 + u - last;
+    }
   }
   last = res;
-  for (int i = res - 1; i >= 0; --i) {
-    const long long pix = pb + (long long)i * res + k;
-    if (!inside_px(d, pix)) last = i;
-    if (last - i < gcol[pix]) gcol[pix] = last - i;
+  for (int i1 = res - 1; i1 >= 0; i1 -= G) {
+    bool out[G];
+    int g[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int i = i1 - u;
+      out[u] = i >= 0 && !inside_px(d, pb + (long long)i * res + k);
+      g[u] = i >= 0 ? gcol[pb + (long long)i * res + k] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int i = i1 - u;
+      if (i < 0) break;
+      if (out[u]) last = i;
+      if (last - i < g[u]) gcol[pb + (long long)i * res + k] = last - i;
+    }
   }
 }
 
