@@ -23,7 +23,8 @@ __device__ __forceinline__ void bernstein(int j, int spc, double (&b)[4]) {
   b[3] = __dmul_rn(__dmul_rn(t, t), t);
 }
 
-constexpr int kBernMax = 256;  // samples per curve whose weights are tabled in shared memory
+constexpr int kBernMax = 256;   // samples per curve whose weights are tabled in shared memory
+constexpr int kStageDv = 2048;  // vertex gradients of an element staged in shared memory
 
 // mode 0: dv -> dctrl, dv cleared; 1: the same, then an Adam step on the points (step *d.step,
 // the update adam_update makes, without a clamp) and the flattening; 2: the flattening only.
@@ -31,6 +32,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
   pdl_enter();
   __shared__ double s_r[kCtrlThreads / 32];
   __shared__ double s_w[kBernMax][4];  // the Bernstein weights of the samples, formed once
+  __shared__ float2 s_dv[kStageDv];    // the element's vertex gradients, read once
   if (mode != 2 && (*d.status & (kStatusOverflow | kStatusBadParam))) return;  // a void iteration
   const int g = blockIdx.x;
   const int c0 = d.elem_coff[g], np = d.elem_coff[g + 1] - c0;
@@ -54,6 +56,16 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
     return b[r];
   };
   if (mode != 2) {
+    // the vertex gradients are read (and cleared for the next pass) once, coalesced
+    const bool staged = nv <= kStageDv;
+    if (staged) {
+      for (int i = threadIdx.x; i < nv; i += kCtrlThreads) {
+        s_dv[i] = d.dv[v0 + i];
+        d.dv[v0 + i] = make_float2(0.0f, 0.0f);
+      }
+      __syncthreads();
+    }
+    const float2* dv = staged ? s_dv : d.dv + v0;
     // point k of a cubic path is entry k % 3 of curve k / 3; an anchor (k % 3 = 0) is also entry 3
     // of the previous curve.  A fixed order over the samples: the sums are reproducible given dv.
     const int t = *d.step;
@@ -62,12 +74,12 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
     for (int k = threadIdx.x; k < np; k += kCtrlThreads) {
       float2 gk = make_float2(0.0f, 0.0f);
       if (!cubic) {
-        gk = d.dv[v0 + k];
+        gk = dv[k];
       } else {
         const int c = k / 3, r = k % 3;
         for (int j = 0; j < spc; ++j) {
           const float w = (float)weight(j, r);
-          const float2 gv = d.dv[v0 + c * spc + j];
+          const float2 gv = dv[c * spc + j];
           gk.x = fmaf(w, gv.x, gk.x);
           gk.y = fmaf(w, gv.y, gk.y);
         }
@@ -75,7 +87,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
           const int cp = c == 0 ? ncurve - 1 : c - 1;
           for (int j = 0; j < spc; ++j) {
             const float w = (float)weight(j, 3);
-            const float2 gv = d.dv[v0 + cp * spc + j];
+            const float2 gv = dv[cp * spc + j];
             gk.x = fmaf(w, gv.x, gk.x);
             gk.y = fmaf(w, gv.y, gk.y);
           }
@@ -95,8 +107,10 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
         d.ctrl_v[c0 + k] = v;
       }
     }
-    __syncthreads();  // every read of dv is done
-    for (int i = threadIdx.x; i < nv; i += kCtrlThreads) d.dv[v0 + i] = make_float2(0.0f, 0.0f);
+    if (!staged) {
+      __syncthreads();  // every read of dv is done
+      for (int i = threadIdx.x; i < nv; i += kCtrlThreads) d.dv[v0 + i] = make_float2(0.0f, 0.0f);
+    }
     if (mode == 0) return;
     __syncthreads();  // the new points are visible to the block
   }
