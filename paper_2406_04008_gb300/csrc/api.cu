@@ -623,6 +623,8 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   Dev& d = h->d;
   d.n_elems = h->N;
   d.n_probs = h->P;
+  d.max_segs = 0;
+  for (int e = 0; e < h->N; ++e) d.max_segs = std::max(d.max_segs, h->elem_voff[e + 1] - h->elem_voff[e]);
   d.tile = h->opt.tile;
   d.deterministic = o.deterministic ? 1 : 0;
   d.pdl = o.overlap_launches ? 1 : 0;

@@ -330,7 +330,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(Dev d) {
 // Then one thread per tile: the (tile, element) pair takes a slot of its tile's range by counting
 // the tile back down (so the counts are zero again for the next iteration, also after an
 // overflow), and near pairs are appended to the distance kernel's list (one atomic per warp).
-constexpr int kEmitThreads = 128, kEmitChunkRows = 32, kEmitMaxW = 64;
+// 128 threads per element; 256 when an element has more than 128 segments (outlines of many
+// curves, as in outline fitting), where one thread per segment is what the classification needs.
+constexpr int kEmitChunkRows = 32, kEmitMaxW = 64;
+template <int kEmitThreads>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
   pdl_enter();
   __shared__ int s_near[kEmitChunkRows * kEmitMaxW];  // segments marking the tile near
@@ -456,7 +459,8 @@ cudaError_t launch_scan(const Dev& d, cudaStream_t s) {
 int scan_rounds(int total_tiles) { return (total_tiles + kScanRound - 1) / kScanRound; }
 
 cudaError_t launch_bin(const Dev& d, cudaStream_t s) {
-  return klaunch(d.pdl, k_emit, d.n_elems, kEmitThreads, 0, s, d);
+  if (d.max_segs > 128) return klaunch(d.pdl, k_emit<256>, d.n_elems, 256, 0, s, d);
+  return klaunch(d.pdl, k_emit<128>, d.n_elems, 128, 0, s, d);
 }
 
 }  // namespace collage

@@ -44,6 +44,7 @@ struct LossParams {
 struct Dev {
   // ---- problem (fixed at create) ----
   int n_elems, n_probs;
+  int max_segs;                 // the most segments of any element
   const int* elem_prob;
   const int* elem_voff;         // [n+1]
   const uint8_t* elem_closed;
