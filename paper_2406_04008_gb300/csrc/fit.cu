@@ -13,14 +13,14 @@ namespace collage {
 constexpr int kCtrlThreads = 128;
 
 // Bernstein weights of sample j of a curve sampled spc times (t = j / spc, u = 1 - t; u^3, 3u^2 t,
-// 3u t^2, t^3), in double with explicit round-to-nearest operations in the order the host's
-// flattening uses, so that vertices flattened here equal the host's bit for bit.
-__device__ __forceinline__ void bernstein(int j, int spc, double (&b)[4]) {
-  const double t = __ddiv_rn((double)j, (double)spc), u = __dsub_rn(1.0, t);
-  b[0] = __dmul_rn(__dmul_rn(u, u), u);
-  b[1] = __dmul_rn(__dmul_rn(__dmul_rn(3.0, u), u), t);
-  b[2] = __dmul_rn(__dmul_rn(__dmul_rn(3.0, u), t), t);
-  b[3] = __dmul_rn(__dmul_rn(t, t), t);
+// 3u t^2, t^3), in float: FP64 instructions are slow and long-latency on this part, and the
+// vertices are float either way (within an ulp or two of the host's double flattening).
+__device__ __forceinline__ void bernstein(int j, int spc, float (&b)[4]) {
+  const float t = (float)j / (float)spc, u = 1.0f - t;
+  b[0] = u * u * u;
+  b[1] = 3.0f * u * u * t;
+  b[2] = 3.0f * u * t * t;
+  b[3] = t * t * t;
 }
 
 constexpr int kBernMax = 256;   // samples per curve whose weights are tabled in shared memory
@@ -30,8 +30,8 @@ constexpr int kStageDv = 2048;  // vertex gradients of an element staged in shar
 // the update adam_update makes, without a clamp) and the flattening; 2: the flattening only.
 __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
   pdl_enter();
-  __shared__ double s_r[kCtrlThreads / 32];
-  __shared__ double s_w[kBernMax][4];  // the Bernstein weights of the samples, formed once
+  __shared__ float s_r[kCtrlThreads / 32];
+  __shared__ float s_w[kBernMax][4];  // the Bernstein weights of the samples, formed once
   __shared__ float2 s_dv[kStageDv];    // the element's vertex gradients, read once
   if (mode != 2 && (*d.status & (kStatusOverflow | kStatusBadParam))) return;  // a void iteration
   const int g = blockIdx.x;
@@ -42,16 +42,16 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
   const bool table = cubic && spc <= kBernMax;
   if (table) {
     for (int j = threadIdx.x; j < spc; j += kCtrlThreads) {
-      double b[4];
+      float b[4];
       bernstein(j, spc, b);
       for (int r = 0; r < 4; ++r) s_w[j][r] = b[r];
     }
     __syncthreads();
   }
   // weight r of sample j (from the table when there is one)
-  auto weight = [&](int j, int r) -> double {
+  auto weight = [&](int j, int r) -> float {
     if (table) return s_w[j][r];
-    double b[4];
+    float b[4];
     bernstein(j, spc, b);
     return b[r];
   };
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
       } else {
         const int c = k / 3, r = k % 3;
         for (int j = 0; j < spc; ++j) {
-          const float w = (float)weight(j, r);
+          const float w = weight(j, r);
           const float2 gv = dv[c * spc + j];
           gk.x = fmaf(w, gv.x, gk.x);
           gk.y = fmaf(w, gv.y, gk.y);
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
         if (r == 0) {
           const int cp = c == 0 ? ncurve - 1 : c - 1;
           for (int j = 0; j < spc; ++j) {
-            const float w = (float)weight(j, 3);
+            const float w = weight(j, 3);
             const float2 gv = dv[cp * spc + j];
             gk.x = fmaf(w, gv.x, gk.x);
             gk.y = fmaf(w, gv.y, gk.y);
@@ -114,35 +114,35 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
     if (mode == 0) return;
     __syncthreads();  // the new points are visible to the block
   }
-  // the flattening, as the host forms it at create time
+  // the flattening (the same sampling as the host's at create time)
   for (int i = threadIdx.x; i < nv; i += kCtrlThreads) {
     if (!cubic) {
       d.vloc[v0 + i] = d.ctrl[c0 + i];
       continue;
     }
     const int c = i / spc, j = i % spc;
-    double x = 0.0, y = 0.0;
+    float x = 0.0f, y = 0.0f;
     for (int r = 0; r < 4; ++r) {
       const float2 p = d.ctrl[c0 + (3 * c + r) % np];
-      const double w = weight(j, r);
-      x = __dadd_rn(x, __dmul_rn(w, (double)p.x));
-      y = __dadd_rn(y, __dmul_rn(w, (double)p.y));
+      const float w = weight(j, r);
+      x = fmaf(w, p.x, x);
+      y = fmaf(w, p.y, y);
     }
-    d.vloc[v0 + i] = make_float2(__double2float_rn(x), __double2float_rn(y));
+    d.vloc[v0 + i] = make_float2(x, y);
   }
-  // bin radius: the largest |point| (the curve stays in the convex hull of its control points)
-  double rmax = 0.0;
+  // bin radius: the largest |point| (the curve stays in the convex hull of its control points;
+  // the tile rectangle adds a pixel of slack beyond it)
+  float rmax = 0.0f;
   for (int k = threadIdx.x; k < np; k += kCtrlThreads) {
     const float2 p = d.ctrl[c0 + k];
-    const double x = p.x, y = p.y;
-    rmax = fmax(rmax, sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+    rmax = fmaxf(rmax, sqrtf(fmaf(p.x, p.x, p.y * p.y)));
   }
-  for (int o = 16; o; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  for (int o = 16; o; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
   if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = rmax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kCtrlThreads / 32; ++w) rmax = fmax(rmax, s_r[w]);
-    d.elem_rbin[g] = (float)rmax;
+    for (int w = 1; w < kCtrlThreads / 32; ++w) rmax = fmaxf(rmax, s_r[w]);
+    d.elem_rbin[g] = rmax;
   }
 }
 
