@@ -154,11 +154,16 @@ __device__ __forceinline__ unsigned ordered(float f) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Greedy placement, one block per problem.  First every axis pixel's D2 and packed coordinates are
-// gathered into per-candidate arrays (cand and gxy), and the elements are ranked by radius (ties:
-// lower index) into order[]; then each step is one pass over the candidates: the clearances take the
-// previous element's disk into account and the next element's choice is reduced over the block.
-constexpr int kPlaceRankMax = 4096;  // elements ranked in shared memory (more: a reduction per step)
+// Greedy placement, one block per problem.  First the elements are ranked by radius (ties: lower
+// index) into order[]; then every axis pixel's D2, packed coordinates and clearance are gathered
+// into per-candidate arrays, in dynamic shared memory when they fit there (else in cand, gxy and
+// clear); then each step is one pass over the candidates: the clearances take the previous
+// element's disk into account and the next element's choice is reduced over the block.
+constexpr int kPlaceRankMax = 4096;                // elements ranked in shared memory (more: a
+                                                   // reduction per step)
+constexpr int kPlaceSmem = 224 * 1024;             // dynamic shared memory of the placement
+constexpr int kPlaceSmemCands = kPlaceSmem / 12;   // candidates it holds (D2, coordinates, clearance)
+static_assert(kPlaceSmem >= kPlaceRankMax * 8, "the ranking keys share the candidates' space");
 
 __device__ __forceinline__ unsigned long long elem_key(const Dev& d, int e, float fres) {
   const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
@@ -168,24 +173,18 @@ __device__ __forceinline__ unsigned long long elem_key(const Dev& d, int e, floa
 __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, const int* n_cand,
                                                              const unsigned* d2, float* clear, int* gxy,
                                                              int* order) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ unsigned long long s_red[kPlaceThreads / 32];
-  __shared__ unsigned long long s_key[kPlaceRankMax];
   const int p = blockIdx.x;
   const int res = d.prob_res[p], nc = n_cand[p];
   const long long pb = d.prob_pix_base[p];
   const int e0 = d.prob_elem_base[p], e1 = d.prob_elem_base[p + 1], ne = e1 - e0;
   if (nc == 0) return;  // no inside pixel: the params stay
   const float fres = (float)res;
-  // per candidate: D2 (in place of the pixel index) and x | y << 16, the clearance
-  for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
-    const int idx = cand[pb + c];
-    cand[pb + c] = (int)d2[pb + idx];
-    gxy[pb + c] = (idx % res) | ((idx / res) << 16);
-    clear[pb + c] = FLT_MAX;
-  }
   // the elements in placement order: decreasing key (radius bits, then the lower index)
   const bool ranked = ne <= kPlaceRankMax;
   if (ranked) {
+    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_dyn);
     for (int i = threadIdx.x; i < ne; i += kPlaceThreads) s_key[i] = elem_key(d, e0 + i, fres);
     __syncthreads();
     for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
@@ -196,6 +195,19 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, c
     }
   } else {
     for (int i = threadIdx.x; i < ne; i += kPlaceThreads) order[e0 + i] = 0;  // 0: not placed yet
+  }
+  __syncthreads();  // the keys' space is free
+  // per candidate: D2, x | y << 16, the clearance
+  const bool in_smem = nc <= kPlaceSmemCands;
+  unsigned* cd2 = in_smem ? reinterpret_cast<unsigned*>(s_dyn) : reinterpret_cast<unsigned*>(cand + pb);
+  int* cxy = in_smem ? reinterpret_cast<int*>(s_dyn + 4 * kPlaceSmemCands) : gxy + pb;
+  float* ccl = in_smem ? reinterpret_cast<float*>(s_dyn + 8 * kPlaceSmemCands) : clear + pb;
+  for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
+    const int idx = cand[pb + c];
+    const unsigned w = d2[pb + idx];
+    cd2[c] = w;
+    cxy[c] = (idx % res) | ((idx / res) << 16);
+    ccl[c] = FLT_MAX;
   }
   __syncthreads();
   int px = 0, py = 0;  // the previous element's pixel and radius (none before the first step)
@@ -219,19 +231,19 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, c
     // clearance >= r (key: D2, then the lower pixel index), and the largest clearance as fallback
     unsigned long long ck = 0, fk = 0;
     for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
-      const int xy = gxy[pb + c], x = xy & 0xffff, y = xy >> 16;
-      float cl = clear[pb + c];
+      const int xy = cxy[c], x = xy & 0xffff, y = xy >> 16;
+      float cl = ccl[c];
       if (pr >= 0.0f) {
         const int dx = x - px, dy = y - py;
         const float dist = __fsub_rn(sqrtf(__int2float_rn(dx * dx + dy * dy)), pr);
         if (dist < cl) {
           cl = dist;
-          clear[pb + c] = cl;
+          ccl[c] = cl;
         }
       }
       const unsigned long long low = 0xffffffffu - (unsigned)(y * res + x);
       if (cl >= r) {
-        const unsigned long long k = ((unsigned long long)(unsigned)cand[pb + c] << 32) | low;
+        const unsigned long long k = ((unsigned long long)cd2[c] << 32) | low;
         ck = k > ck ? k : ck;
       }
       const unsigned long long kf = ((unsigned long long)ordered(cl) << 32) | low;
@@ -264,8 +276,11 @@ cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol
       d, gcol, d2, max_res);
   const long long np = d.total_pix;
   k_mat_axis<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(d, d2, cand, n_cand, axis_out, width_out);
-  // gcol is free after the row pass: it holds the candidates' coordinates
-  k_mat_place<<<d.n_probs, kPlaceThreads, 0, s>>>(d, cand, n_cand, d2, clear, gcol, order);
+  // gcol is free after the row pass: it holds the candidates' coordinates when they do not fit in
+  // shared memory
+  e = cudaFuncSetAttribute(k_mat_place, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaceSmem);
+  if (e != cudaSuccess) return e;
+  k_mat_place<<<d.n_probs, kPlaceThreads, kPlaceSmem, s>>>(d, cand, n_cand, d2, clear, gcol, order);
   return cudaGetLastError();
 }
 
