@@ -371,6 +371,60 @@ static double box_sum(const double* img, int R, int i, int j, int r) {
   return s;
 }
 
+/* Eq. 7 over one R x R image, in the reading of the header: for k = 0..K-1 the box of width
+ * 5 + 6k px, B_k = its zero-padded sum of the occupancy O, D_k = min(1, B_k), and
+ *   L_u = sum_k w_k sum_p M(p) (1 - O(p)) (1 - D_k(p)),
+ * with M the container coverage.  Its derivative in O(q), by the chain rule through the min
+ * (one-sided at the kink: d min(1, B)/dB = 0 at B = 1):
+ *   dL_u/dO(q) = sum_k w_k [ -M(q)(1 - D_k(q)) - sum_{p in box_k(q)} M(p)(1 - O(p)) 1[B_k(p) < 1] ]
+ * (the box is symmetric, so q in box_k(p) is p in box_k(q)).  gou may be NULL. */
+void ora_uniform_term(int R, int K, const double* w, const double* occ, const double* covc,
+                      double* Lu, double* gou) {
+  const long NP = (long)R * R;
+  double* bsum = (double*)malloc(sizeof(double) * NP * (K > 0 ? K : 1));
+  double* rowsum = (double*)malloc(sizeof(double) * (R > 0 ? R : 1));
+  double total = 0.0;
+  for (int k = 0; k < K; ++k) {
+    int r = (5 + 6 * k - 1) / 2;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < R; ++i) {
+      rowsum[i] = 0.0;
+      for (int j = 0; j < R; ++j) {
+        long p = (long)i * R + j;
+        double B = box_sum(occ, R, i, j, r);
+        bsum[k * NP + p] = B;
+        double D = B < 1.0 ? B : 1.0;
+        rowsum[i] += covc[p] * (1.0 - occ[p]) * (1.0 - D);
+      }
+    }
+    double lk = 0.0; /* rows summed in order: the result does not depend on the thread count */
+    for (int i = 0; i < R; ++i) lk += rowsum[i];
+    total += w[k] * lk;
+  }
+  free(rowsum);
+  *Lu = total;
+  if (gou) {
+    double* G = (double*)malloc(sizeof(double) * (NP > 0 ? NP : 1));
+    for (long p = 0; p < NP; ++p) gou[p] = 0.0;
+    for (int k = 0; k < K; ++k) {
+      int r = (5 + 6 * k - 1) / 2;
+      for (long p = 0; p < NP; ++p) {
+        double B = bsum[k * NP + p];
+        G[p] = B < 1.0 ? covc[p] * (1.0 - occ[p]) : 0.0;
+      }
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < R; ++i)
+        for (int j = 0; j < R; ++j) {
+          long p = (long)i * R + j;
+          double B = bsum[k * NP + p], D = B < 1.0 ? B : 1.0;
+          gou[p] += w[k] * (-covc[p] * (1.0 - D) - box_sum(G, R, i, j, r));
+        }
+    }
+    free(G);
+  }
+  free(bsum);
+}
+
 /* ---------------------------------------------------------------------------------------------
  * Loss (Eqs. 5-8) and gradient
  * ------------------------------------------------------------------------------------------- */
@@ -411,27 +465,9 @@ void ora_eval(const ora_scene* sc, const double* params, int R, const ora_opts* 
   Lo *= inv_wh;
   Ld *= inv_wh;
 
-  int K = o->n_dil;
-  double* bsum = (double*)malloc(sizeof(double) * NP * (K > 0 ? K : 1));
-  double* rowsum = (double*)malloc(sizeof(double) * R);
-  for (int k = 0; k < K; ++k) {
-    int r = (5 + 6 * k - 1) / 2;
-#pragma omp parallel for schedule(static)
-    for (int i = 0; i < R; ++i) {
-      rowsum[i] = 0.0;
-      for (int j = 0; j < R; ++j) {
-        long p = (long)i * R + j;
-        double B = box_sum(occ, R, i, j, r);
-        bsum[k * NP + p] = B;
-        double D = B < 1.0 ? B : 1.0;
-        rowsum[i] += covc[p] * (1.0 - occ[p]) * (1.0 - D);
-      }
-    }
-    double lk = 0.0; /* rows summed in order: the result does not depend on the thread count */
-    for (int i = 0; i < R; ++i) lk += rowsum[i];
-    Lu += o->dil_weight[k] * lk;
-  }
-  free(rowsum);
+  const int want_grad = grad_a || grad_b || grad_v;
+  double* gou = want_grad ? (double*)calloc(NP, sizeof(double)) : NULL;
+  ora_uniform_term(R, o->n_dil, o->dil_weight, occ, covc, &Lu, gou);
   double L = o->alpha * Lc + o->beta * Lo + o->gamma * Lu + o->delta * Ld;
   if (terms) {
     terms[0] = Lc;
@@ -441,24 +477,7 @@ void ora_eval(const ora_scene* sc, const double* params, int R, const ora_opts* 
     terms[4] = L;
   }
 
-  if (grad_a || grad_b || grad_v) {
-    /* dL_u/dO(q) = sum_k w_k [ -M(q)(1 - D_k(q)) - sum_{p in win_k(q)} M(p)(1 - O(p)) 1[B_k(p) < 1] ] */
-    double* gou = (double*)calloc(NP, sizeof(double));
-    double* G = (double*)malloc(sizeof(double) * NP);
-    for (int k = 0; k < K; ++k) {
-      int r = (5 + 6 * k - 1) / 2;
-      for (long p = 0; p < NP; ++p) {
-        double B = bsum[k * NP + p];
-        G[p] = B < 1.0 ? covc[p] * (1.0 - occ[p]) : 0.0;
-      }
-#pragma omp parallel for schedule(static)
-      for (int i = 0; i < R; ++i)
-        for (int j = 0; j < R; ++j) {
-          long p = (long)i * R + j;
-          double B = bsum[k * NP + p], D = B < 1.0 ? B : 1.0;
-          gou[p] += o->dil_weight[k] * (-covc[p] * (1.0 - D) - box_sum(G, R, i, j, r));
-        }
-    }
+  if (want_grad) {
     /* Per-pixel adjoints of Ihat and A_tau */
     double* gI = (double*)malloc(sizeof(double) * NP);
     double* gA = (double*)malloc(sizeof(double) * NP);
@@ -600,10 +619,8 @@ void ora_eval(const ora_scene* sc, const double* params, int R, const ora_opts* 
     free(acc_b);
     free(gI);
     free(gA);
-    free(gou);
-    free(G);
   }
-  free(bsum);
+  free(gou);
   free(covc);
   free(ihat);
   free(atau);

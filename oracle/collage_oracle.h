@@ -74,6 +74,12 @@ void ora_render(const ora_scene* sc, const double* params, int res, const ora_op
 void ora_eval(const ora_scene* sc, const double* params, int res, const ora_opts* o,
               double* terms, double* grad_a, double* grad_b, double* grad_v);
 
+/* The even-distribution term of Eq. 7 alone, on one res x res image: occ = O = 1 - Ihat and covc
+ * the container coverage (row-major, res*res each), K kernels of widths 5 + 6k px with weights
+ * w[K].  *Lu receives L_u; gou (may be NULL) receives dL_u/dO per pixel.  ora_eval uses it. */
+void ora_uniform_term(int res, int K, const double* w, const double* occ, const double* covc,
+                      double* Lu, double* gou);
+
 /* One Adam step (bias-corrected, step >= 1) on params[4n]; entries whose trainable flag is 0 are
  * left unchanged, s is clamped to [s_min, s_max] after the step. */
 void ora_adam(int n, double* p, double* m, double* v, const double* g, int step, double lr,

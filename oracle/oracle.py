@@ -90,6 +90,7 @@ def _load():
     lib.ora_pair_work.restype = C.c_double
     lib.ora_pair_work.argtypes = [vp, _dp, C.c_int, opt]
     lib.ora_metrics.argtypes = [vp, _dp, C.c_int, opt, _dp]
+    lib.ora_uniform_term.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double), dpn]
     lib.ora_set_threads.restype = C.c_int
     lib.ora_set_threads.argtypes = [C.c_int]
     _lib = lib
@@ -202,6 +203,23 @@ class Scene:
 
     def pair_work(self, params, res, opts):
         return self.lib.ora_pair_work(self.h, _d(params), res, C.byref(opts))
+
+
+def uniform_term(occ, covc, weights, grad=True):
+    """The even-distribution term of Eq. 7 on one square image: (L_u, dL_u/dO [R, R] or None).
+    occ = O = 1 - Ihat and covc = the container coverage M, both [R, R]; weights[K] are the weights
+    of the K box kernels of widths 5 + 6k px."""
+    lib = _load()
+    occ = np.ascontiguousarray(occ, np.float64)
+    covc = np.ascontiguousarray(covc, np.float64)
+    R = occ.shape[0]
+    assert occ.shape == (R, R) and covc.shape == (R, R)
+    w = np.zeros(8)
+    w[:len(weights)] = weights
+    lu = C.c_double()
+    gou = np.zeros((R, R)) if grad else None
+    lib.ora_uniform_term(R, len(weights), w, occ.reshape(-1), covc.reshape(-1), C.byref(lu), _ptr(gou))
+    return lu.value, gou
 
 
 def set_threads(n: int) -> int:

@@ -295,6 +295,54 @@ def test_distribution_term_integer_case(oracle_mod):
     assert out["terms"][2] == ref and ref > 0
 
 
+def test_distribution_gradient_central_differences(oracle_mod):
+    # dL_u/dO of Eq. 7 (the adjoint the allocation-free call and the raster adjoint consume)
+    # against central differences of L_u in every pixel of a 14 x 14 image.  L_u is a polynomial
+    # of degree 2 in each O(q) away from the kinks of min(1, B_k), so the differences are exact up
+    # to rounding; pixels whose windows hold a box sum within 4h of 1 are skipped.  Occupancies are
+    # small (mostly B_k < 1) with a dense patch (B_k > 1 there), so both branches of the min occur.
+    rng = np.random.default_rng(11)
+    R, h = 14, 1e-6
+    occ = rng.uniform(0.0, 0.03, (R, R))
+    occ[2:6, 8:12] = rng.uniform(0.3, 1.0, (4, 4))
+    cov = np.clip(rng.uniform(-0.3, 1.3, (R, R)), 0.0, 1.0)
+    wts = (1.0, 2.5, 4.0)
+    lu, gou = oracle_mod.uniform_term(occ, cov, wts)
+
+    def box(img, r):
+        p = np.pad(img, r)
+        return np.array([[p[i:i + 2 * r + 1, j:j + 2 * r + 1].sum() for j in range(R)] for i in range(R)])
+
+    B = [box(occ, 2 + 3 * k) for k in range(len(wts))]
+    assert any((b > 1).any() for b in B) and any((b < 1).any() for b in B)
+    checked = 0
+    for i in range(R):
+        for j in range(R):
+            near_kink = any(np.abs(B[k][max(i - r, 0):i + r + 1, max(j - r, 0):j + r + 1] - 1).min() < 4 * h
+                            for k, r in enumerate(2 + 3 * k for k in range(len(wts))))
+            if near_kink:
+                continue
+            a, b = occ.copy(), occ.copy()
+            a[i, j] += h
+            b[i, j] -= h
+            fd = (oracle_mod.uniform_term(a, cov, wts, grad=False)[0] -
+                  oracle_mod.uniform_term(b, cov, wts, grad=False)[0]) / (2 * h)
+            assert abs(fd - gou[i, j]) <= 1e-6 * max(1.0, abs(gou[i, j])), (i, j, fd, gou[i, j])
+            checked += 1
+    assert checked > R * R // 2
+
+
+def test_distribution_term_alone_equals_full_evaluation(oracle_mod):
+    # the standalone Eq. 7 entry gives the L_u of the full loss evaluation on the same render
+    prob = W.config_problem(1, n_elems=10, grid=64)
+    sc = oracle_mod.Scene(prob)
+    o = oracle_mod.options(n_dil=3, dil_weight=(1.0, 2.0, 3.0))
+    q = prob["params0"].astype(np.float64)
+    ihat, _, cov = sc.render(q, 64, o)
+    lu, _ = oracle_mod.uniform_term(1.0 - ihat, cov, (1.0, 2.0, 3.0), grad=False)
+    assert lu == sc.eval(q, 64, o, grad=False)["terms"][2] and lu > 0
+
+
 def _rot_problem(prob, params):
     """The same scene rotated by 90 degrees about (1/2, 1/2): (x, y) -> (1 - y, x)."""
     q = params.reshape(-1, 4).copy()
