@@ -66,17 +66,55 @@ def _raster_src_sha1():
         return hashlib.sha1(f.read()).hexdigest()
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml): SM clock, its maximum and
+    the active clock-event reasons of one GPU, found by the UUID torch reports."""
+    SM = 1  # NVML_CLOCK_SM
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, uuid, index):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = C.c_void_p()
+        ok = False
+        if uuid:
+            ok = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), C.byref(self.h)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(index, C.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        f = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = f or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        C = self.C
+        clk, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, C.byref(clk)) != 0:
+            return None
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, C.byref(mx))
+        self.reasons_fn(self.h, C.byref(rs))
+        return float(clk.value), float(mx.value), [n for b, n in self.BITS.items() if rs.value & b]
+
+
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    """SM clock and throttle reasons while the timed region runs: nvidia-smi every 50 ms (as the
+    profiling recipe does) and NVML every millisecond (a timed region of a few milliseconds falls
+    between nvidia-smi samples)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, uuid=None):
         self.index = index
+        self.uuid = uuid
         self.proc = None
         self.lines = []
+        self.fast = []
+        self.stop = threading.Event()
+        self.nvml = None
 
     def __enter__(self):
         try:
@@ -92,13 +130,27 @@ class ClockSampler:
             self.lines.clear()
         except OSError:
             self.proc = None
+        try:
+            self.nvml = _Nvml(self.uuid, self.index)
+            self.ft = threading.Thread(target=self._poll, daemon=True)
+            self.ft.start()
+        except (OSError, AttributeError):
+            self.nvml = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def _poll(self):
+        while not self.stop.is_set():
+            s = self.nvml.sample()
+            if s:
+                self.fast.append(s)
+            time.sleep(0.001)
+
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
@@ -109,6 +161,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        n_smi = 0
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
@@ -118,13 +171,26 @@ class ClockSampler:
                 mx.append(float(f[2]))
             except ValueError:
                 continue
+            n_smi += 1
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        for c, m, rs in self.fast:
+            sm.append(c)
+            mx.append(m)
+            reasons.update(rs)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_nvidia_smi": n_smi, "samples_nvml": len(self.fast)}
+
+
+def _config(world):
+    """The workload's description, the same on both arms."""
+    return {"workload": WORKLOAD, "grid": 1024, "elements": 1000,
+            "path": "graph-captured persistent autotuned",
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "parallelism": f"replicas x{world}"}
 
 
 def _workload(rank=0):
@@ -175,8 +241,9 @@ def run_reference(args):
     o = O.options(pad_px=2.0)
     q = prob["params0"].astype(np.float64)
     m, v = np.zeros_like(q), np.zeros_like(q)
-    # one oracle iteration takes seconds: the sample is capped so that the run ends in minutes
-    warm, steps = min(args.warmup, 1), min(args.steps, 20)
+    # one oracle iteration takes ~0.4 s on 16 cores: the sample is capped so that the run ends in
+    # well under a minute
+    warm, steps = min(args.warmup, 10), min(args.steps, 20)
     for i in range(warm):
         g = sc.eval(q, 1024, o)["grad_a"]
         q, m, v = O.adam(q, m, v, g, i + 1)
@@ -191,7 +258,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": steps, "warmup": warm,
            "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "grid": 1024, "elements": 1000},
+           "config": _config(args.gpus),
            "cpu_baseline": {"value": val, "unit": "iters/s", "cores": cores, "kind": "oracle",
                             "sample": f"{steps} full FP64 oracle iterations (forward, "
                                       "gradient, Adam) of the 1024^2 workload (at most 20 of "
@@ -479,18 +546,29 @@ def main():
     info = col.info()
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except (AttributeError, RuntimeError):
+        uuid = None
+    with ClockSampler(local, uuid) as clk:
         t_wall0 = time.perf_counter()
         times = _time_steps(col, args.steps, flush, torch)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     barrier()
+    # the statistic: the median step time (p10 / p90 and the mean beside it), max over ranks
+    med = statistics.median(times)
     total = sum(times)
     if world > 1:
-        t = torch.tensor([total], device="cuda")
+        t = torch.tensor([med, total], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = world * args.steps / total
+        med, total = float(t[0].item()), float(t[1].item())
+    value = world / med
+    qs = statistics.quantiles(times, n=10) if len(times) >= 2 else [times[0]] * 9
+    spread = {"statistic": "median of per-step CUDA-event times, max over ranks",
+              "p10_ms": 1e3 * qs[0], "median_ms": 1e3 * med, "p90_ms": 1e3 * qs[-1],
+              "mean_ms": 1e3 * total / len(times), "mean_value": world * len(times) / total}
 
     # ---- end to end through the host-buffer entry point ----
     p0 = np.ascontiguousarray(prob["params0"], np.float32)
@@ -530,7 +608,7 @@ def main():
     torch.cuda.synchronize()
     ptimes = _time_steps(plain, min(args.steps, 50), flush, torch)
     plain.close()
-    plain_value = len(ptimes) / sum(ptimes)
+    plain_value = 1.0 / statistics.median(ptimes)
 
     if rank != 0:
         if world > 1:
@@ -569,12 +647,11 @@ def main():
                 "work": f"{pairs:.4g} pixel-segment pairs x {FLOP_PER_PAIR} flop",
                 "launch_ms": stages["raster_fwd"]}
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * med,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "grid": 1024, "elements": 1000, "tile": tile,
-                      "path": "graph-captured persistent autotuned", "l2": "flushed between steps "
-                      f"({L2_FLUSH_BYTES >> 20} MiB write)", "parallelism": f"replicas x{world}"},
+           "config": _config(world),
+           "tile": tile, "step_time": spread,
            "plain": {"value": plain_value, "unit": "iters/s",
                      "path": "eager launches, one block per tile, 16 px tiles",
                      "speedup": value / world / plain_value},

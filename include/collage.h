@@ -116,6 +116,15 @@ typedef struct {
   int pair_capacity;         /* (tile, element) pairs the bin buffers hold */
   int last_pairs;            /* pairs binned by the last iteration (after a sync) */
   int kernels_per_iter;      /* kernel launches of one collage_step iteration */
+  /* How often the rarely taken kernel paths ran since collage_create (cumulative): */
+  long long path_row_fallback; /* pixel rows of a (tile, element) pair that cross the outline
+                                  more than 16 times, whose winding number is then taken over
+                                  every segment of the outline */
+  long long path_long_near;    /* pairs with more than 64 segments near the tile (the distance
+                                  loop runs over the near segments in chunks of 64) */
+  long long path_wide_tile;    /* tiles listing more than 32 elements (the composite ranks the
+                                  list in global memory instead of by warp shuffles) */
+  long long path_ring_chunk;   /* container chunks after the first 1024 segments of a ring */
 } collage_info;
 
 /* Fills *opt with the defaults listed above (one level of 1024, 50 iterations). */
@@ -242,12 +251,12 @@ collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float
  * h_best_ms receives its iteration time (may be NULL).  Params are restored afterwards. */
 collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
 
-/* The even-distribution term (Eq. 7 as collage_loss_backward evaluates it) of one res x res image,
- * and its gradient with respect to the occupancy O = 1 - d_ihat, computed without allocating any
- * device memory.  The paper has no counterpart to this call; it exists for callers that cannot
+/* The even-distribution term of one res x res image, as collage_loss_backward evaluates it, and
+ * its gradient with respect to the occupancy O = 1 - d_ihat, computed without allocating any
+ * device memory.  The paper has no counterpart to this call.  It exists for callers that cannot
  * call cudaMalloc: code whose device memory is owned by another allocator (a framework's caching
- * allocator, a fixed arena) and real-time loops where cudaMalloc / cudaFree, which can synchronise
- * the device, are not acceptable.
+ * allocator, a fixed arena), which a cudaMalloc behind its back would bypass, and real-time loops
+ * where cudaMalloc / cudaFree, which can synchronise the device, are not acceptable.
  *   d_ihat [res*res]    items rendered black on white (the d_img_bw of collage_render), row-major
  *   d_cov  [res*res]    container coverage M_C (1 inside, 0 outside, anti-aliased at the edge)
  *   h_dil_weight [n_dilations]  host weights of the kernels of widths 5 + 6k pixels, 1..8 kernels
@@ -257,8 +266,8 @@ collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
  * 5 MiB, held by every GPU that loads the library until the process exits).  res*res above that
  * maximum, res < 1, n_dilations outside 1..8 or a NULL pointer return COLLAGE_ERR_INVALID_ARG
  * before any device work; CUDA failures return COLLAGE_ERR_CUDA.  The first call on a device looks
- * up the array's device address (once per device, with that device current); make that first
- * call before any stream capture.  All calls share the one array and it keeps the last call's
+ * up the array's device address and sets the dilation kernels' shared-memory limit (once per
+ * device, with that device current); make that first call before any stream capture.  All calls share the one array and it keeps the last call's
  * contents, so calls that overlap on the GPU (different streams, threads or devices sharing a
  * context) race: serialise them.  Asynchronous on `stream`; inputs must stay valid until it runs. */
 #define COLLAGE_NOALLOC_MAX_PIXELS (1024 * 1024)
@@ -284,6 +293,7 @@ collage_status collage_metrics(collage_t h, void* stream, double* h_metrics);
  * INVALID_ARG for NULL, CUDA on a launch or event failure.  Synchronises `stream`. */
 collage_status collage_fp32_peak(void* stream, float* h_tflops);
 
+/* Sizes of the current level and the path counters above.  Synchronises the device. */
 collage_status collage_get_info(collage_t h, collage_info* out);
 /* Waits for the stream and returns any latched device error. */
 collage_status collage_sync(collage_t h, void* stream);

@@ -48,7 +48,9 @@ class collage_options(C.Structure):
 class collage_info(C.Structure):
     _fields_ = [("n_probs", C.c_int), ("n_elems", C.c_int), ("level", C.c_int),
                 ("n_levels", C.c_int), ("tile", C.c_int), ("total_pixels", C.c_longlong),
-                ("pair_capacity", C.c_int), ("last_pairs", C.c_int), ("kernels_per_iter", C.c_int)]
+                ("pair_capacity", C.c_int), ("last_pairs", C.c_int), ("kernels_per_iter", C.c_int),
+                ("path_row_fallback", C.c_longlong), ("path_long_near", C.c_longlong),
+                ("path_wide_tile", C.c_longlong), ("path_ring_chunk", C.c_longlong)]
 
 
 # name -> (restype, argtypes), the C ABI of include/collage.h

@@ -728,6 +728,8 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   CKC(cudaMemset(d.dq, 0, sizeof(float4) * h->N));
   CKC(dmalloc(h->owned, d.loss_terms, 5 * h->P));
   CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
+  CKC(dmalloc(h->owned, d.paths, 4));
+  CKC(cudaMemset(d.paths, 0, sizeof(unsigned long long) * 4));
   CKC(dmalloc(h->owned, h->ctl, 12));
   CKC(cudaMemset(h->ctl, 0, sizeof(int) * 12));
   d.status = h->ctl;
@@ -1169,6 +1171,13 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
   out->kernels_per_iter = 5 + (scan_rounds(h->d.total_tiles) > 1 ? 2 : 0) + (dil ? 2 : 0) + 1 +
                          (h->d.deterministic ? 1 : 0) + 1 + (h->d.fit ? 1 : 0);
+  unsigned long long paths[4] = {0, 0, 0, 0};
+  CK(h, cudaDeviceSynchronize());
+  CK(h, cudaMemcpy(paths, h->d.paths, sizeof(paths), cudaMemcpyDeviceToHost));
+  out->path_row_fallback = (long long)paths[0];
+  out->path_long_near = (long long)paths[1];
+  out->path_wide_tile = (long long)paths[2];
+  out->path_ring_chunk = (long long)paths[3];
   return COLLAGE_OK;
 }
 

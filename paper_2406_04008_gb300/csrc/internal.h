@@ -121,6 +121,12 @@ struct Dev {
                                 //   finished, [4] light near pairs (back of near_list), [5] blocks
                                 //   of the Adam flush that have finished (its last block resets
                                 //   it), [6..7] spare
+  unsigned long long* paths;    // [4] cumulative counts of the rarely taken kernel paths (since
+                                //   create): [0] pixel rows of a near pair whose crossings
+                                //   overflow the per-row list (winding over every segment),
+                                //   [1] near pairs with more near segments than one staged chunk,
+                                //   [2] tiles listing more than 32 pairs (ranked in global
+                                //   memory), [3] container ring chunks after a ring's first
   LossParams L;
   int deterministic;
   int pdl;                      // launch the iteration's kernels with programmatic serialisation

@@ -81,12 +81,15 @@ extern "C" collage_status collage_uniform_term_noalloc(void* stream, int res, in
   if (e != cudaSuccess || dev < 0 || dev >= 128) return COLLAGE_ERR_CUDA;
   unsigned char* base = nullptr;
   {
-    // once per device, with that device current: the device address of the scratch array
+    // once per device, with that device current: the device address of the scratch array, and
+    // the dynamic shared-memory limit of every dilation kernel (a per-device function attribute;
+    // each kernel's limit is a constant of its kernel count, so no later call changes it)
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_ptr[dev]) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return COLLAGE_ERR_CUDA;
+      if (prepare_dilate(kMaxDil) != cudaSuccess) return COLLAGE_ERR_CUDA;
       g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
     }
     base = g_scratch_ptr[dev];
@@ -110,9 +113,6 @@ extern "C" collage_status collage_uniform_term_noalloc(void* stream, int res, in
   d.L.n_dil = n_dilations;
   d.L.gamma = 1.0f;
   for (int k = 0; k < kMaxDil; ++k) d.L.dil_w[k] = k < n_dilations ? h_dil_weight[k] : 0.0f;
-  // the dilation kernels' dynamic shared-memory limit is per function and a handle's level setup
-  // may have lowered it, so raise it to the largest size on every call (no allocation involved)
-  if (prepare_dilate(kMaxDil) != cudaSuccess) return COLLAGE_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_noalloc_setup<<<1, 1, 0, s>>>(res);
   if ((e = cudaGetLastError()) == cudaSuccess) e = launch_dilate(d, s, false);

@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d
       if (total_near <= base + kNearCap) break;
     }
     if (closed) __syncthreads();  // the row crossing lists are complete
+    if (d.paths) {
+      if (closed && threadIdx.x < T && s_rc[threadIdx.x] > kRowCross) atomicAdd(&d.paths[0], 1ull);
+      if (threadIdx.x == 0 && s_near > kNearCap) atomicAdd(&d.paths[1], 1ull);
+    }
     float2* sv = d.saved + (size_t)slot * NP;
     bool live = false;
 #pragma unroll
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
         d.pair_slot[rg.x + r] = (int)rg.x + lane;
       }
     } else {
+      if (lane == 0 && d.paths) atomicAdd(&d.paths[2], 1ull);
       for (int i = lane; i < m; i += 32) {
         const int vi = d.pair_elem[rg.x + i];
         int r = 0;
@@ -624,6 +629,7 @@ __global__ void __launch_bounds__(NT) k_container(Dev d) {
       const int b0 = d.ring_off[r], nv = d.ring_off[r + 1] - b0;
       for (int c0 = 0; c0 < nv; c0 += kSegCap) {
         const int cn = min(kSegCap, nv - c0);
+        if (c0 > 0 && threadIdx.x == 0 && d.paths) atomicAdd(&d.paths[3], 1ull);
         __syncthreads();
         for (int j = threadIdx.x; j < cn; j += NT) {
           const int ai = b0 + c0 + j, bi = b0 + (c0 + j + 1) % nv;

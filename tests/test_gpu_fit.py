@@ -20,15 +20,64 @@ def env(oracle_mod):
     return oracle_mod, Collage
 
 
+def _generic(prob, grid, k=0):
+    """The fitting workload's circle starts centred on the grid, so its flattening is symmetric
+    about the grid diagonals: a pixel centre on a diagonal is exactly equidistant from the two
+    segments meeting at the vertex there, where the gradient is set-valued (reading A15: any
+    choice is a valid one-sided derivative, and float rounding decides which side a kernel takes).
+    The parity cases move the (fixed) transform by a fraction of a pixel and rotate it slightly, so
+    that no pixel sits on such a tie; _assert_tie_free checks it."""
+    q = np.asarray(prob["params0"], np.float64).reshape(-1, 4).copy()
+    q[:, 0] += (0.29 + 0.07 * k) / grid
+    q[:, 1] += (0.41 - 0.05 * k) / grid
+    q[:, 2] += 0.0137 * (1 + k)
+    out = dict(prob)
+    out["params0"] = q.astype(np.float32).reshape(-1)
+    return out
+
+
 def _case(name):
     """(problem, loss kwargs, grid, tile)"""
     if name == "star20_128":
-        return W.fit_problem(0, n_cubics=20, grid=128), dict(W.FIT_LOSS), 128, 8
+        return _generic(W.fit_problem(0, n_cubics=20, grid=128), 128, 5), dict(W.FIT_LOSS), 128, 8
     if name == "star20_200_t16":  # ragged: 200 is no multiple of the 16-px tile
-        return W.fit_problem(1, n_cubics=20, grid=200), dict(W.FIT_LOSS), 200, 16
+        return _generic(W.fit_problem(1, n_cubics=20, grid=200), 200, 0), dict(W.FIT_LOSS), 200, 16
     if name == "mixed60_full":  # every element kind, the full loss of Eq. 8 with padding and force
         return W.config_problem(3, n_elems=60, grid=192), dict(pad_px=2.0, delta=100.0), 192, 8
     raise KeyError(name)
+
+
+TIE_PX = 1e-5  # the device's distances are good to ~1e-6 px
+
+
+def _assert_tie_free(O, prob, R, o):
+    """No pixel whose coverage carries a gradient (|sd| < rho + pad (+ hw), in px) has two closest
+    segments, with different closest points, whose distances differ by less than TIE_PX."""
+    sc = O.Scene(prob)
+    q = np.asarray(prob["params0"], np.float64)
+    kind = np.asarray(prob["kind"])
+    hw = np.asarray(prob["hw"], np.float64)
+    ys, xs = np.mgrid[0:R, 0:R]
+    P = np.stack([(xs.ravel() + 0.5), (ys.ravel() + 0.5)], 1)  # px
+    for e in range(len(kind)):
+        v = sc.world_vertices(q, e) * R
+        a = v if kind[e] != 2 else v[:-1]
+        b = np.roll(v, -1, 0) if kind[e] != 2 else v[1:]
+        lo, hi = v.min(0) - 4 - hw[e] * R, v.max(0) + 4 + hw[e] * R
+        sel = np.all((P >= lo) & (P <= hi), 1)
+        p = P[sel]
+        ab = b - a
+        t = np.clip(((p[:, None, :] - a[None]) * ab[None]).sum(2) / np.maximum((ab * ab).sum(1), 1e-300), 0, 1)
+        cp = a[None] + t[:, :, None] * ab[None]
+        d = np.hypot(*(p[:, None, :] - cp).transpose(2, 0, 1))
+        j = d.argmin(1)
+        d1 = d[np.arange(len(p)), j]
+        sd = d1 if kind[e] == 2 else d1  # |sd| for closed kinds; hw - d for strokes
+        band = (np.abs(hw[e] * R - d1) if kind[e] == 2 else d1) < o.rho_px + o.pad_px
+        same = np.hypot(*(cp - cp[np.arange(len(p)), j][:, None, :]).transpose(2, 0, 1)) < 1e-6
+        d2 = np.where(same, np.inf, d).min(1)
+        ties = band & (d2 - d1 < TIE_PX)
+        assert not ties.any(), (e, p[ties][:4], (d2 - d1)[ties][:4], sd[ties][:4])
 
 
 def _point_err(g, gr):
@@ -37,54 +86,16 @@ def _point_err(g, gr):
     return np.abs(g - gr) / np.maximum(np.abs(gr), floor)
 
 
-def _point_bound(O, prob, R, o, ref):
-    """The bound for the point gradients: the gradient bound plus twice what moving every float32
-    vertex by one ulp does to the oracle's point gradients.  A point's gradient sums few pixels and
-    can react to geometry at that scale by several 1e-3 (measured with the oracle: 7.6e-3 for 8
-    cubics at 128^2); the device's vertex transform (float-float) differs from the oracle's (double)
-    at that scale, so a bound below this reaction would test rounding, not the method."""
-    moved, _ = _ref_grad(O, prob, R, o, nudge=True)
-    return U.GRAD_RTOL + 2.0 * _point_err(moved, ref).max()
-
-
 def _pts(prob):
     return np.asarray(prob["pts"], np.float32).reshape(-1, 2)
 
 
-def _ref_grad(O, prob, R, o, spc=16, nudge=False):
-    """The oracle's dL/d(points) for the outlines as the device holds them: the flattened vertices
-    are float32 (one rounding of the double flattening), so every cubic path enters the oracle as
-    the polygon of its rounded vertices, and the vertex gradients go back to the control points by
-    the Bernstein weights.  A point's gradient sums few pixels: that rounding alone moves it by up
-    to ~4e-3 of its size (the oracle on rounded against unrounded vertices), more than the bound."""
-    sc = O.Scene(prob, spc)
-    kind = np.asarray(prob["kind"])
-    off = np.asarray(prob["pt_off"])
-    pts, koff, kk = [], [0], []
-    rng = np.random.default_rng(0)
-    for e in range(len(kind)):
-        v = sc.local_vertices(e).astype(np.float32) if kind[e] == 0 else \
-            np.asarray(prob["pts"], np.float32).reshape(-1, 2)[off[e]:off[e + 1]]
-        if nudge:  # every coordinate moved to a float32 neighbour, up or down at random
-            v = np.nextafter(v, np.where(rng.uniform(size=v.shape) < 0.5, -np.inf, np.inf).astype(np.float32))
-        pts.append(v)
-        koff.append(koff[-1] + len(v))
-        kk.append(1 if kind[e] == 0 else kind[e])
-    flat = dict(prob, kind=np.array(kk, np.int32), pt_off=np.array(koff, np.int32),
-                pts=np.concatenate(pts).reshape(-1))
-    gv, terms = O.control_grad(flat, prob["params0"], R, o, spc)
-    w = O.bernstein_weights(spc)
-    out = np.zeros((int(off[-1]), 2))
-    for e in range(len(kind)):
-        ge = gv[koff[e]:koff[e + 1]]
-        if kind[e] != 0:
-            out[off[e]:off[e + 1]] = ge
-            continue
-        npt = int(off[e + 1] - off[e])
-        for c in range(npt // 3):
-            for r in range(4):
-                out[off[e] + (3 * c + r) % npt] += w[:, r] @ ge[c * spc:(c + 1) * spc]
-    return out, terms
+def _ref_grad(O, prob, R, o, spc=16, tie_free=True):
+    """The oracle's dL/d(points) at the problem's control points (FP64 flattening, Sec. 3), after
+    checking (tie_free) that the case has no closest-segment near-tie."""
+    if tie_free:
+        _assert_tie_free(O, prob, R, o)
+    return O.control_grad(prob, prob["params0"], R, o, spc)
 
 
 @pytest.mark.parametrize("name", ["star20_128", "star20_200_t16", "mixed60_full"])
@@ -95,11 +106,14 @@ def test_fit_terms_and_point_gradient_match_oracle(env, name):
     col = Collage(prob, level_res=[grid], tile=tile, fit_controls=1, **g)
     terms, _ = col.loss_backward()
     dp = col.control_grad().cpu().numpy()
-    ref, rterms = _ref_grad(O, prob, grid, o)
+    # the 60-element case holds near-ties inside its small blobs (128 segments of ~0.1 px: an
+    # interior pixel has many nearly equal distances) where the two candidates' normals differ
+    # by 0.05 rad; the star fits are tie-free
+    ref, rterms = _ref_grad(O, prob, grid, o, tie_free=name != "mixed60_full")
     U.check_terms(terms.cpu().numpy()[0], rterms, grid, (o.alpha, o.beta, o.gamma, o.delta),
                   use_u=o.gamma != 0)
     err = _point_err(dp, ref)
-    assert err.max() <= _point_bound(O, prob, grid, o, ref), (err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert err.max() <= U.GRAD_RTOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
     # the points themselves are untouched by a backward pass
     assert np.array_equal(col.get_controls().cpu().numpy(), _pts(prob))
     col.close()
@@ -178,8 +192,9 @@ def test_fit_step_host_moves_points_not_transforms(env):
 def test_fit_batch_of_uneven_problems(env):
     # three outlines on different grids in one handle: every problem's points and their gradient
     O, Collage = env
-    probs = [W.fit_problem(2, n_cubics=12, grid=96), W.fit_problem(3, n_cubics=20, grid=160),
-             W.fit_problem(4, n_cubics=8, grid=128)]
+    probs = [_generic(W.fit_problem(2, n_cubics=12, grid=96), 96, 1),
+             _generic(W.fit_problem(3, n_cubics=20, grid=160), 160, 0),
+             _generic(W.fit_problem(4, n_cubics=8, grid=128), 128, 0)]
     g, o = U.paired(**W.FIT_LOSS)
     col = Collage(probs, n_levels=1, level_res=[1], tile=8, fit_controls=1, **g)
     terms, _ = col.loss_backward()
@@ -191,7 +206,7 @@ def test_fit_batch_of_uneven_problems(env):
         U.check_terms(terms.cpu().numpy()[i], rterms, R, (o.alpha, o.beta, o.gamma, o.delta), use_u=False)
         n = len(ref)
         err = _point_err(dp[k:k + n], ref)
-        assert err.max() <= _point_bound(O, prob, R, o, ref), (i, err.max())
+        assert err.max() <= U.GRAD_RTOL, (i, err.max())
         k += n
     assert k == len(dp)
     col.close()
