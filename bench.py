@@ -480,18 +480,42 @@ def open_packing(steps, flush, torch):
 
 
 def schedule_time(torch):
-    """Wall time of the whole 128 -> 256 -> 512 -> 1024 schedule (300/200/100/50 iterations)."""
+    """The whole 128 -> 256 -> 512 -> 1024 schedule (300/200/100/50 iterations) as one captured
+    graph (collage_run_schedule): wall time of a run with the graph cached, of the first run (which
+    probes every level and captures), and each level's device time on its own (CUDA events around
+    the level's iterations on its one-iteration graph)."""
     from paper_2406_04008_gb300.collage import Collage
+    levels, iters = [128, 256, 512, 1024], [300, 200, 100, 50]
     col = Collage(_workload(), **_opts(use_graphs=1, persistent=1, tile=8))
-    col.step(1)
-    col.set_level(0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    col.run_schedule()
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    per_level = []
+    for lv, n in enumerate(iters):
+        col.set_level(lv)
+        col.step(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        col.step_async(n)
+        b.record(stream)
+        b.synchronize()
+        col.sync()
+        ms = a.elapsed_time(b)
+        per_level.append({"res": levels[lv], "iterations": n, "device_ms": ms, "us_per_iter": 1e3 * ms / n})
+    walls = []
+    for _ in range(3):
+        col.set_level(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        col.run_schedule()
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
     col.close()
-    return {"iterations": 650, "seconds": dt, "levels": "128/256/512/1024 x 300/200/100/50"}
+    dev = sum(x["device_ms"] for x in per_level) / 1e3
+    return {"iterations": sum(iters), "levels": "128/256/512/1024 x 300/200/100/50",
+            "path": "one CUDA graph: per level the level switch and a device-decided WHILE loop",
+            "seconds": statistics.median(walls[1:]), "first_run_seconds": walls[0],
+            "sum_level_device_seconds": dev, "wall_over_device": statistics.median(walls[1:]) / dev,
+            "per_level": per_level}
 
 
 def main():

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcollage.so")
-SOURCES = ["api.cu", "bin.cu", "raster.cu", "loss.cu", "fit.cu", "mat.cu", "metrics.cu", "noalloc.cu", "peak.cu"]
+SOURCES = ["api.cu", "bin.cu", "raster.cu", "loss.cu", "fit.cu", "mat.cu", "metrics.cu", "noalloc.cu", "peak.cu", "sched.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -36,8 +36,22 @@ struct collage_s {
   bool has_trainable = false;
   // level state
   int level = -1;
-  std::vector<int> res, ntx, tile_base, dtile_base;
+  std::vector<int> res, ntx, tile_base, dtile_base;  // host copies of the current level's tables
   std::vector<long long> pix_base;
+  // every level's tables for the raster tile lv_tile: host copies and device arrays
+  struct LevelTab {
+    std::vector<int> res, ntx, tile_base, dtile_base;
+    std::vector<long long> pix_base;
+    int total_tiles = 0, total_dtiles = 0;
+    long long total_pix = 0;
+    int* d_res = nullptr;
+    int* d_ntx = nullptr;
+    int* d_tile_base = nullptr;
+    int* d_dtile_base = nullptr;
+    long long* d_pix_base = nullptr;
+  };
+  std::vector<LevelTab> lv;
+  int lv_tile = 0;
   int pair_grid = 0;  // grid of the per-pair distance kernel
   int bwd_grid = 0;   // grid of the per-pair adjoint
   int tile_grid = 0;  // grid of the per-tile composite
@@ -45,13 +59,8 @@ struct collage_s {
   // device memory
   Dev d{};
   size_t pix_cap = 0, tile_cap = 0, dtile_cap = 0, pair_cap = 0, saved_tile = 0;
-  // per-level arrays (device), sized P / P+1
-  int* d_prob_res = nullptr;
-  int* d_prob_ntx = nullptr;
-  int* d_prob_tile_base = nullptr;
-  int* d_prob_dtile_base = nullptr;
-  long long* d_prob_pix_base = nullptr;
-  int* ctl = nullptr;        // device: status, step, total_pairs, pending, 4 work counters
+  int* ctl = nullptr;        // device: status, step, total_pairs, pending, 8 work counters,
+                             //   schedule base step, 3 spare
   int* h_ctl = nullptr;      // pinned mirror
   float* d_stage = nullptr;  // device: params, loss terms and control words gathered for one copy
   float* h_stage = nullptr;  // pinned: their host copy ([4n | 5 n_probs | 4], see k_adam_flush)
@@ -61,8 +70,11 @@ struct collage_s {
                              // no step was enqueued since the last read
   cudaStream_t cap_stream = nullptr;
   cudaStream_t aux_stream = nullptr;  // side branch of an iteration (the loss assembly)
+  cudaStream_t body_stream = nullptr;  // captures the loop bodies of the schedule graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;  // one iteration at the current level
+  cudaGraphExec_t sched = nullptr;  // the schedule from level sched_start to the last
+  int sched_start = -1;
   // quality-metric scratch (allocated by collage_metrics)
   uint8_t* met_obj = nullptr;
   int* met_gcol = nullptr;
@@ -123,16 +135,27 @@ void free_list(std::vector<void*>& list) {
 
 bool is_finite_f(float x) { return std::isfinite(x); }
 
-void drop_graph(collage_t h) {
+// The one-iteration graph holds the current level's tables; the schedule graph holds every level's
+// but the pair buffers, tile size and grids of its capture.
+void drop_iter_graph(collage_t h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+}
+
+void drop_graph(collage_t h) {
+  drop_iter_graph(h);
+  if (h->sched) cudaGraphExecDestroy(h->sched);
+  h->sched = nullptr;
+  h->sched_start = -1;
 }
 
 }  // namespace
 
 collage_s::~collage_s() {
   if (graph) cudaGraphExecDestroy(graph);
+  if (sched) cudaGraphExecDestroy(sched);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (body_stream) cudaStreamDestroy(body_stream);
   if (aux_stream) cudaStreamDestroy(aux_stream);
   if (met_obj) cudaFree(met_obj);
   if (met_gcol) cudaFree(met_gcol);
@@ -344,72 +367,127 @@ static collage_status read_ctl(collage_t h, cudaStream_t s) {
   return COLLAGE_OK;
 }
 
-static collage_status setup_level(collage_t h, int level) {
+// Per-pixel, per-tile and per-dilation-tile buffers for the largest level (regrown if needed).
+static collage_status ensure_level_bufs(collage_t h, size_t np, size_t nt, size_t nd) {
+  if (np <= h->pix_cap && nt <= h->tile_cap && nd <= h->dtile_cap) return COLLAGE_OK;
   drop_graph(h);
-  const collage_options& o = h->opt;
+  CK(h, cudaDeviceSynchronize());
+  free_list(h->level_bufs);
+  h->pix_cap = h->tile_cap = h->dtile_cap = 0;
   Dev& d = h->d;
-  const int T = d.tile;
-  const long long last = o.level_res[o.n_levels - 1];
-  h->res.assign(h->P, 0);
-  h->ntx.assign(h->P, 0);
-  h->tile_base.assign(h->P + 1, 0);
-  h->dtile_base.assign(h->P + 1, 0);
-  h->pix_base.assign(h->P + 1, 0);
-  for (int p = 0; p < h->P; ++p) {
-    const long long g = h->prob_grid[p];
-    const int r = (int)(g * o.level_res[level] / last);
-    h->res[p] = r;
-    h->ntx[p] = (r + T - 1) / T;
-    h->tile_base[p + 1] = h->tile_base[p] + h->ntx[p] * h->ntx[p];
-    const int nd = (r + 31) / 32;
-    h->dtile_base[p + 1] = h->dtile_base[p] + nd * nd;
-    h->pix_base[p + 1] = h->pix_base[p] + (long long)r * r;
+  CK(h, dmalloc(h->level_bufs, d.covc, np));
+  CK(h, dmalloc(h->level_bufs, d.img_I, np));
+  CK(h, dmalloc(h->level_bufs, d.img_Pt, np));
+  CK(h, dmalloc(h->level_bufs, d.gOu, np));
+  CK(h, dmalloc(h->level_bufs, d.dil_m, np));
+  CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
+  CK(h, dmalloc(h->level_bufs, d.range, nt));
+  CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
+  CK(h, cudaMemset(d.tile_cnt, 0, sizeof(int) * nt));
+  CK(h, dmalloc(h->level_bufs, d.scan_part, (size_t)scan_rounds((int)nt)));
+  CK(h, dmalloc(h->level_bufs, d.lossA, nt));
+  CK(h, dmalloc(h->level_bufs, d.lossU, nd));
+  CK(h, dmalloc(h->level_bufs, d.dtile_flags, nd));
+  CK(h, dmalloc(h->level_bufs, d.dtile_list, 2 * nd));
+  CK(h, dmalloc(h->level_bufs, d.dtile_n, 2));
+  h->pix_cap = np;
+  h->tile_cap = nt;
+  h->dtile_cap = nd;
+  return COLLAGE_OK;
+}
+
+// Every level's tables for the current raster tile: per problem the resolution, tiles per side and
+// the base offsets of its tiles, dilation tiles and pixels; uploaded once, selected per level.
+static collage_status build_levels(collage_t h) {
+  const collage_options& o = h->opt;
+  const int T = h->d.tile, L = o.n_levels, P = h->P;
+  const long long last = o.level_res[L - 1];
+  h->lv.resize(L);
+  size_t np = 0, nt = 0, nd = 0;
+  for (int l = 0; l < L; ++l) {
+    collage_s::LevelTab& t = h->lv[l];
+    t.res.assign(P, 0);
+    t.ntx.assign(P, 0);
+    t.tile_base.assign(P + 1, 0);
+    t.dtile_base.assign(P + 1, 0);
+    t.pix_base.assign(P + 1, 0);
+    for (int p = 0; p < P; ++p) {
+      const int r = (int)((long long)h->prob_grid[p] * o.level_res[l] / last);
+      t.res[p] = r;
+      t.ntx[p] = (r + T - 1) / T;
+      t.tile_base[p + 1] = t.tile_base[p] + t.ntx[p] * t.ntx[p];
+      const int ndt = (r + 31) / 32;
+      t.dtile_base[p + 1] = t.dtile_base[p] + ndt * ndt;
+      t.pix_base[p + 1] = t.pix_base[p] + (long long)r * r;
+    }
+    t.total_tiles = t.tile_base[P];
+    t.total_dtiles = t.dtile_base[P];
+    t.total_pix = t.pix_base[P];
+    np = std::max(np, (size_t)t.total_pix);
+    nt = std::max(nt, (size_t)t.total_tiles);
+    nd = std::max(nd, (size_t)t.total_dtiles);
+    if (!t.d_res) {
+      CK(h, dmalloc(h->owned, t.d_res, P));
+      CK(h, dmalloc(h->owned, t.d_ntx, P));
+      CK(h, dmalloc(h->owned, t.d_tile_base, P + 1));
+      CK(h, dmalloc(h->owned, t.d_dtile_base, P + 1));
+      CK(h, dmalloc(h->owned, t.d_pix_base, P + 1));
+    }
+    CK(h, cudaMemcpy(t.d_res, t.res.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(t.d_ntx, t.ntx.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(t.d_tile_base, t.tile_base.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(t.d_dtile_base, t.dtile_base.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(t.d_pix_base, t.pix_base.data(), sizeof(long long) * (P + 1), cudaMemcpyHostToDevice));
   }
-  d.total_tiles = h->tile_base[h->P];
-  d.total_dtiles = h->dtile_base[h->P];
-  d.total_pix = h->pix_base[h->P];
-  if ((size_t)d.total_pix > h->pix_cap || (size_t)d.total_tiles > h->tile_cap ||
-      (size_t)d.total_dtiles > h->dtile_cap) {
-    // regrow every level-sized buffer
-    CK(h, cudaDeviceSynchronize());
-    free_list(h->level_bufs);
-    const size_t np = (size_t)d.total_pix, nt = (size_t)d.total_tiles, nd = (size_t)d.total_dtiles;
-    CK(h, dmalloc(h->level_bufs, d.covc, np));
-    CK(h, dmalloc(h->level_bufs, d.img_I, np));
-    CK(h, dmalloc(h->level_bufs, d.img_Pt, np));
-    CK(h, dmalloc(h->level_bufs, d.gOu, np));
-    CK(h, dmalloc(h->level_bufs, d.dil_m, np));
-    CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
-    CK(h, dmalloc(h->level_bufs, d.range, nt));
-    CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
-    CK(h, dmalloc(h->level_bufs, d.scan_part, (size_t)scan_rounds((int)nt)));
-    CK(h, dmalloc(h->level_bufs, d.lossA, nt));
-    CK(h, dmalloc(h->level_bufs, d.lossU, nd));
-    CK(h, dmalloc(h->level_bufs, d.dtile_flags, nd));
-    CK(h, dmalloc(h->level_bufs, d.dtile_list, 2 * nd));
-    CK(h, dmalloc(h->level_bufs, d.dtile_n, 2));
-    h->pix_cap = np;
-    h->tile_cap = nt;
-    h->dtile_cap = nd;
+  drop_graph(h);
+  collage_status st = ensure_level_bufs(h, np, nt, nd);
+  if (st) return st;
+  h->lv_tile = T;
+  return COLLAGE_OK;
+}
+
+// Points the device view at level `level`'s tables (no device work unless the tile changed).
+static collage_status apply_level(collage_t h, int level) {
+  if (h->lv_tile != h->d.tile) {
+    collage_status st = build_levels(h);
+    if (st) return st;
   }
-  CK(h, cudaMemcpy(h->d_prob_res, h->res.data(), sizeof(int) * h->P, cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(h->d_prob_ntx, h->ntx.data(), sizeof(int) * h->P, cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(h->d_prob_tile_base, h->tile_base.data(), sizeof(int) * (h->P + 1), cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(h->d_prob_dtile_base, h->dtile_base.data(), sizeof(int) * (h->P + 1), cudaMemcpyHostToDevice));
-  CK(h, cudaMemcpy(h->d_prob_pix_base, h->pix_base.data(), sizeof(long long) * (h->P + 1), cudaMemcpyHostToDevice));
-  CK(h, prepare_dilate(o.n_dilations));
-  cudaStream_t s = h->cap_stream;
-  CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));  // clear latched status
-  CK(h, launch_container(d, s));
-  // the distribution term's kernels visit only the tiles listed by the flags; every other tile
-  // keeps the zeros written here for the whole level
-  CK(h, cudaMemsetAsync(d.dtile_n, 0, 2 * sizeof(int), s));
-  CK(h, cudaMemsetAsync(d.gOu, 0, sizeof(float) * (size_t)d.total_pix, s));
-  CK(h, cudaMemsetAsync(d.dil_m, 0, sizeof(float) * (size_t)d.total_pix, s));
-  CK(h, cudaMemsetAsync(d.dil_mask, 0, (size_t)d.total_pix, s));
-  CK(h, cudaMemsetAsync(d.lossU, 0, sizeof(float) * (size_t)d.total_dtiles, s));
-  CK(h, launch_dtile_flags(d, s));
-  // size the pair buffers from the current params: count with an unbounded capacity
+  const collage_s::LevelTab& t = h->lv[level];
+  Dev& d = h->d;
+  d.prob_res = t.d_res;
+  d.prob_ntx = t.d_ntx;
+  d.prob_tile_base = t.d_tile_base;
+  d.prob_dtile_base = t.d_dtile_base;
+  d.prob_pix_base = t.d_pix_base;
+  d.total_tiles = t.total_tiles;
+  d.total_dtiles = t.total_dtiles;
+  d.total_pix = t.total_pix;
+  h->res = t.res;
+  h->ntx = t.ntx;
+  h->tile_base = t.tile_base;
+  h->dtile_base = t.dtile_base;
+  h->pix_base = t.pix_base;
+  return COLLAGE_OK;
+}
+
+// The level switch on the device (capturable): the container raster of the level, and the
+// distribution term's tile lists with the zeros that the tiles off those lists keep.
+static cudaError_t enqueue_level_switch(const Dev& d, cudaStream_t s) {
+  cudaError_t e = launch_container(d, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.dtile_n, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.gOu, 0, sizeof(float) * (size_t)d.total_pix, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.dil_m, 0, sizeof(float) * (size_t)d.total_pix, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.dil_mask, 0, (size_t)d.total_pix, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.lossU, 0, sizeof(float) * (size_t)d.total_dtiles, s);
+  if (e == cudaSuccess) e = launch_dtile_flags(d, s);
+  return e;
+}
+
+// Pairs that binning the current params at the selected level produces: the transform and the
+// tile scan with an unbounded capacity, read back (synchronises the stream).  The tile counts are
+// left at zero.  A pending Adam step is applied on the way, as the next iteration would.
+static collage_status probe_pairs(collage_t h, cudaStream_t s, size_t* need) {
+  Dev& d = h->d;
   CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
   Dev probe = d;
   probe.cap = 0x7fffffff;
@@ -421,8 +499,26 @@ static collage_status setup_level(collage_t h, int level) {
   CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
   CK(h, cudaStreamSynchronize(s));
   if (h->h_ctl[0] & kStatusBadParam) return fail(h, COLLAGE_ERR_INVALID_ARG, "params are not finite or s <= 0");
-  const size_t need = (size_t)h->h_ctl[2];
-  st = ensure_pairs(h, std::max<size_t>(need + need / 2 + 256, 1024));
+  *need = (size_t)h->h_ctl[2];
+  return COLLAGE_OK;
+}
+
+static size_t with_slack(size_t need) { return std::max<size_t>(need + need / 2 + 256, 1024); }
+
+static collage_status setup_level(collage_t h, int level) {
+  drop_iter_graph(h);
+  collage_status st = apply_level(h, level);
+  if (st) return st;
+  Dev& d = h->d;
+  CK(h, prepare_dilate(h->opt.n_dilations));
+  cudaStream_t s = h->cap_stream;
+  CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));  // clear latched status
+  CK(h, enqueue_level_switch(d, s));
+  // size the pair buffers from the current params
+  size_t need = 0;
+  st = probe_pairs(h, s, &need);
+  if (st) return st;
+  st = ensure_pairs(h, with_slack(need));
   if (st) return st;
   set_grids(h);
   h->level = level;
@@ -730,23 +826,14 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
   CKC(dmalloc(h->owned, d.paths, 4));
   CKC(cudaMemset(d.paths, 0, sizeof(unsigned long long) * 4));
-  CKC(dmalloc(h->owned, h->ctl, 12));
-  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 12));
+  CKC(dmalloc(h->owned, h->ctl, 16));
+  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 16));
   d.status = h->ctl;
   d.step = h->ctl + 1;
   d.total_pairs = h->ctl + 2;
   d.pending = h->ctl + 3;
   d.work = h->ctl + 4;
-  CKC(dmalloc(h->owned, h->d_prob_res, h->P));
-  CKC(dmalloc(h->owned, h->d_prob_ntx, h->P));
-  CKC(dmalloc(h->owned, h->d_prob_tile_base, h->P + 1));
-  CKC(dmalloc(h->owned, h->d_prob_dtile_base, h->P + 1));
-  CKC(dmalloc(h->owned, h->d_prob_pix_base, h->P + 1));
-  d.prob_res = h->d_prob_res;
-  d.prob_ntx = h->d_prob_ntx;
-  d.prob_tile_base = h->d_prob_tile_base;
-  d.prob_dtile_base = h->d_prob_dtile_base;
-  d.prob_pix_base = h->d_prob_pix_base;
+  d.sched_base = h->ctl + 12;
   CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
   CKC(dmalloc(h->owned, h->d_stage, stage_floats(h)));
   CKC(cudaHostAlloc(&h->h_stage, sizeof(float) * stage_floats(h), cudaHostAllocMapped));
@@ -756,9 +843,12 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   }
   CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CKC(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+  CKC(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
   CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   CKC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
 #undef CKC
+  st = build_levels(h);
+  if (st) return bail(st);
   st = setup_level(h, 0);
   if (st) return bail(st);
   *out = h;
@@ -839,17 +929,155 @@ extern "C" collage_status collage_step_async(collage_t h, void* stream, int n_it
   return enqueue_steps(h, (cudaStream_t)stream, n_iters);
 }
 
-extern "C" collage_status collage_run_schedule(collage_t h, void* stream) {
-  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
-  for (int l = std::max(h->level, 0); l < h->opt.n_levels; ++l) {
+// --------------------------------------------------------------------------------------------
+// The level schedule (Sec. 4.3) as one CUDA graph: per level the level switch, then a WHILE node
+// whose body is one iteration; the loop conditions are set on the device (csrc/sched.cu).
+// --------------------------------------------------------------------------------------------
+static cudaError_t capture_schedule(collage_t h, int start, cudaStream_t s) {
+  const collage_options& o = h->opt;
+  cudaError_t e = launch_sched_begin(h->d, s);
+  int target = 0;
+  for (int l = start; l < o.n_levels && e == cudaSuccess; ++l) {
+    if (apply_level(h, l) != COLLAGE_OK) return cudaErrorInvalidValue;  // tables exist: host only
+    set_grids(h);
+    const Dev& d = h->d;
+    target += o.level_iters[l];
+    e = enqueue_level_switch(d, s);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle cond = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 0, 0);
+    if (e == cudaSuccess) e = launch_sched_cond(d, s, cond, target);
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) break;
+    // the loop body: one iteration, then the condition for the next pass
+    cudaStream_t b = h->body_stream;
+    e = cudaStreamBeginCaptureToGraph(b, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t eb = enqueue_iter(h, b, kStep, nullptr, nullptr);
+    if (eb == cudaSuccess) eb = launch_sched_cond(d, b, cond, target);
+    cudaGraph_t body = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b, &body);
+    e = eb != cudaSuccess ? eb : ee;
+  }
+  return e;
+}
+
+// Capacity for every level of a run from `start` (probed from the current params), then the
+// capture.  Synchronises the device.
+static collage_status build_schedule(collage_t h, int start) {
+  const int cur = h->level;
+  cudaStream_t s = h->cap_stream;
+  CK(h, cudaDeviceSynchronize());
+  size_t need = 0;
+  collage_status st = COLLAGE_OK;
+  for (int l = start; l < h->opt.n_levels && !st; ++l) {
+    st = apply_level(h, l);
+    size_t n = 0;
+    if (!st) st = probe_pairs(h, s, &n);
+    need = std::max(need, n);
+  }
+  collage_status st2 = apply_level(h, cur);
+  if (st) return st;
+  if (st2) return st2;
+  if (with_slack(need) > h->pair_cap) {
+    st = ensure_pairs(h, with_slack(need));
+    if (st) return st;
+  }
+  if (h->sched) cudaGraphExecDestroy(h->sched);
+  h->sched = nullptr;
+  h->sched_start = -1;
+  CK(h, prepare_dilate(h->opt.n_dilations));
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t e = capture_schedule(h, start, s);
+  const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  st = apply_level(h, cur);  // the current level's view again
+  set_grids(h);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, e != cudaSuccess ? e : e2, "schedule capture");
+  }
+  if (st) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&h->sched, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    h->sched = nullptr;
+    return cuda_fail(h, ei, "schedule instantiate");
+  }
+  h->sched_start = start;
+  return COLLAGE_OK;
+}
+
+// The host-driven schedule: level setup on the host, then the level's iterations.
+static collage_status run_schedule_host(collage_t h, void* stream, int level, int done_in_level) {
+  for (int l = level; l < h->opt.n_levels; ++l) {
     if (l != h->level) {
       collage_status st = collage_set_level(h, l);
       if (st) return st;
     }
-    collage_status st = collage_step(h, stream, h->opt.level_iters[l]);
+    collage_status st = collage_step(h, stream, h->opt.level_iters[l] - (l == level ? done_in_level : 0));
     if (st) return st;
   }
   return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_run_schedule(collage_t h, void* stream) {
+  if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
+  const collage_options& o = h->opt;
+  const int L = o.n_levels, start = std::max(h->level, 0);
+  if (!o.use_graphs) return run_schedule_host(h, stream, start, 0);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool over = false;
+  collage_status st = check_and_grow(h, s, &over);  // nothing latched; the step count read
+  if (st) return st;
+  if (!h->sched || h->sched_start != start) {
+    st = build_schedule(h, start);
+    if (st) return st;
+    st = check_and_grow(h, s, &over);
+    if (st) return st;
+  }
+  const int step0 = h->h_ctl[1];
+  CK(h, cudaGraphLaunch(h->sched, s));
+  h->ctl_current = false;
+  st = read_ctl(h, s);
+  if (st) return st;
+  const int done = h->h_ctl[1] - step0;
+  int total = 0;
+  for (int l = start; l < L; ++l) total += o.level_iters[l];
+  // the device now holds the last level that ran (or the last level): the host view follows
+  drop_iter_graph(h);
+  h->level = -1;
+  if (done == total && !(h->h_ctl[0] & (kStatusOverflow | kStatusBadParam | kStatusInternal))) {
+    st = apply_level(h, L - 1);
+    if (st) return st;
+    set_grids(h);
+    h->level = L - 1;
+    return check_and_grow(h, s, &over);  // grows the pair buffers if the last level used > 3/4
+  }
+  // stopped early (a bin overflow, or params became non-finite): resume on the host path from the
+  // iteration that did not complete
+  st = check_and_grow(h, s, &over);
+  if (st) return st;
+  int l = start, acc = 0;
+  while (l < L - 1 && acc + o.level_iters[l] <= done) acc += o.level_iters[l++];
+  return run_schedule_host(h, stream, l, done - acc);
 }
 
 extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_iters,

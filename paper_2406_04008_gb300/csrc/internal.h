@@ -114,6 +114,7 @@ struct Dev {
   int* status;                  // [1]
   int* step;                    // [1] Adam step count (the loss assembly advances it)
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
+  int* sched_base;              // [1] Adam step count when the running schedule graph began
   int* work;                    // [8] per-iteration counters, zeroed by the tile scan:
                                 //   [0] near pairs taken by the distance kernel's blocks,
                                 //   [1] entries of live_list, [2] heavy near pairs (front of
@@ -248,6 +249,10 @@ cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol
                             int* cand, int* n_cand, float* clear, int* order, int* axis_out,
                             float* width_out);
 cudaError_t launch_loss(const Dev& d, cudaStream_t s);
+// the captured level schedule: records the step count at the start of a run; sets a level's loop
+// condition (1 while fewer than `target` iterations of the run are done and nothing latched)
+cudaError_t launch_sched_begin(const Dev& d, cudaStream_t s);
+cudaError_t launch_sched_cond(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle cond, int target);
 cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
 // Resident blocks per SM of the raster kernels, the pairs one adjoint block and the tiles one
 // composite block take at once (the forward distance kernel takes one pair per block).
