@@ -664,7 +664,7 @@ def main():
         traffic = NCU_TRAFFIC["bytes_per_launch"] \
             if NCU_TRAFFIC["raster_src_sha1"] == _raster_src_sha1() else None
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_pair_sd",
+                "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_raster_chunks",
                 "peak_source": "measured: FP32 FMA-chain kernel (collage_fp32_peak), burst",
                 "peak_nominal": fp32_nominal,
                 "peak_nominal_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",

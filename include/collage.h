@@ -120,8 +120,8 @@ typedef struct {
   long long path_row_fallback; /* pixel rows of a (tile, element) pair that cross the outline
                                   more than 16 times, whose winding number is then taken over
                                   every segment of the outline */
-  long long path_long_near;    /* pairs with more than 64 segments near the tile (the distance
-                                  loop runs over the near segments in chunks of 64) */
+  long long path_long_near;    /* emission chunks of outlines of more than 512 segments (not
+                                  staged in shared memory: read from global memory per tile) */
   long long path_wide_tile;    /* tiles listing more than 32 elements (the composite ranks the
                                   list in global memory instead of by warp shuffles) */
   long long path_ring_chunk;   /* container chunks after the first 1024 segments of a ring */
@@ -237,8 +237,8 @@ collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_e
  * (see COLLAGE_STAGE_*); the kernels run on `stream`, timed with events on that stream. */
 #define COLLAGE_N_STAGES 9
 #define COLLAGE_STAGE_TRANSFORM 0 /* previous Adam step, transform, segment records, tile counts */
-#define COLLAGE_STAGE_BIN 1       /* tile-count scan and pair emission */
-#define COLLAGE_STAGE_RASTER_FWD 2 /* signed distances per (tile, element) pair */
+#define COLLAGE_STAGE_BIN 1       /* tile-count scan */
+#define COLLAGE_STAGE_RASTER_FWD 2 /* pair emission, classification and per-pixel signed distances */
 #define COLLAGE_STAGE_COMPOSITE 3 /* per-tile products and loss partials */
 #define COLLAGE_STAGE_DILATE 4    /* distribution term forward and backward */
 #define COLLAGE_STAGE_RASTER_BWD 5

@@ -341,8 +341,6 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   h->pair_cap = 0;
   Dev& d = h->d;
   CK(h, dmalloc(h->pair_bufs, d.pair_elem, cap));
-  CK(h, dmalloc(h->pair_bufs, d.pair_tile, cap));
-  CK(h, dmalloc(h->pair_bufs, d.pair_txy, cap));
   CK(h, dmalloc(h->pair_bufs, d.live_list, cap));
   CK(h, dmalloc(h->pair_bufs, d.near_list, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_cls, cap));
@@ -353,6 +351,7 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   h->pair_cap = cap;
   h->saved_tile = tt;
   d.cap = (int)std::min<size_t>(cap, 0x7fffffff);
+  d.list_cap = d.cap;
   set_grids(h);
   return COLLAGE_OK;
 }
@@ -384,6 +383,8 @@ static collage_status ensure_level_bufs(collage_t h, size_t np, size_t nt, size_
   CK(h, dmalloc(h->level_bufs, d.range, nt));
   CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
   CK(h, cudaMemset(d.tile_cnt, 0, sizeof(int) * nt));
+  CK(h, dmalloc(h->level_bufs, d.tile_fill, nt));
+  CK(h, cudaMemset(d.tile_fill, 0, sizeof(int) * nt));
   CK(h, dmalloc(h->level_bufs, d.scan_part, (size_t)scan_rounds((int)nt)));
   CK(h, dmalloc(h->level_bufs, d.lossA, nt));
   CK(h, dmalloc(h->level_bufs, d.lossU, nd));
@@ -542,7 +543,6 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   STEP_(launch_transform(d, s, bwd && !d.deterministic));
   MARK_(1);
   STEP_(launch_scan(d, s));
-  STEP_(launch_bin(d, s));
   MARK_(2);
   STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 1));
   MARK_(3);
@@ -834,6 +834,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.pending = h->ctl + 3;
   d.work = h->ctl + 4;
   d.sched_base = h->ctl + 12;
+  d.chunk_count = h->ctl + 13;  // [13], [14]
   CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
   CKC(dmalloc(h->owned, h->d_stage, stage_floats(h)));
   CKC(cudaHostAlloc(&h->h_stage, sizeof(float) * stage_floats(h), cudaHostAllocMapped));
@@ -1394,10 +1395,10 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   out->total_pixels = h->d.total_pix;
   out->pair_capacity = h->d.cap;
   out->last_pairs = h->h_ctl ? h->h_ctl[2] : 0;
-  // transform (with the previous Adam step), tile scan, emit, pair distances, composite,
-  // (2 dilation), raster bwd, (gradient reduce), loss
+  // transform (with the previous Adam step), tile scan, emission with signed distances,
+  // composite, (2 dilation), raster bwd, (gradient reduce), loss
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 5 + (scan_rounds(h->d.total_tiles) > 1 ? 2 : 0) + (dil ? 2 : 0) + 1 +
+  out->kernels_per_iter = 4 + (scan_rounds(h->d.total_tiles) > 1 ? 2 : 0) + (dil ? 2 : 0) + 1 +
                          (h->d.deterministic ? 1 : 0) + 1 + (h->d.fit ? 1 : 0);
   unsigned long long paths[4] = {0, 0, 0, 0};
   CK(h, cudaDeviceSynchronize());

@@ -1,11 +1,12 @@
 // Transform (Eq. 2) and tile binning.
 //
 // Binning is a counting sort keyed on the tile: the transform kernel counts, per tile, the elements
-// whose tile rectangle covers it (integer atomics); one prefix scan over the tiles turns the counts
-// into [begin, end) ranges; emission places each (tile, element) pair in its tile's range (and
-// counts the tile back down to zero for the next iteration); the raster kernel then orders each
-// tile's short list by element id before using it, so every tile lists its elements in increasing
-// order whatever the order of the atomics.  The tile rectangle follows a fixed float formula
+// whose tile rectangle covers it (integer atomics), and lists every element's kChunkPx-square
+// chunks of its rectangle; one prefix scan over the tiles turns the counts into [begin, end) ranges (and
+// zeroes the counts for the next iteration); the emission (csrc/raster.cu, per chunk) places each
+// (tile, element) pair in its tile's range; the composite then orders each tile's short list by
+// element id before using it, so every tile lists its elements in increasing order whatever the
+// order of the atomics.  The tile rectangle follows a fixed float formula
 // (bin_rect), so the bins are bit-exact against the oracle's rule.
 #include <cfloat>
 
@@ -171,6 +172,22 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     d.rect[g] = r;
     s_rect = r;
     if (zero_grad) d.dq[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the emission's work: the rectangle in chunks of kChunkPx / T tiles a side; chunks whose
+    // segments x tiles exceed kHeavyChunk are listed from the front, the others from the back, so
+    // that the emission takes the costliest first and none trails at the end
+    if (r.z >= r.x && r.w >= r.y) {
+      const int cw = kChunkPx / d.tile, nx = (r.z - r.x) / cw + 1, ny = (r.w - r.y) / cw + 1;
+      const int tiles = min(r.z - r.x + 1, cw) * min(r.w - r.y + 1, cw);
+      const bool heavy = nv * tiles > kHeavyChunk;
+      const int base = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);
+      // (heavy + light chunks beyond the list mean more pairs than the capacity too: the iteration
+      // overflows and the list is not read; every write stays inside it)
+      if (base + nx * ny <= d.list_cap)
+        for (int c = 0; c < nx * ny; ++c) {
+          const int at = heavy ? base + c : d.list_cap - 1 - (base + c);
+          d.near_list[at] = make_int4(g, (r.x + (c % nx) * cw) | ((r.y + (c / nx) * cw) << 16), p, 0);
+        }
+    }
   }
   __syncthreads();
   const int4 r = s_rect;
@@ -195,8 +212,9 @@ __device__ __forceinline__ int scan_round(const Dev& d, int base, int carry, int
   const int i0 = base + t * kScanPer;
   const bool full = i0 + kScanPer <= n;
   int v[kScanPer];
+  // the counts are read once and zeroed for the next iteration's transform
   if (full) {
-    const int4* src = reinterpret_cast<const int4*>(d.tile_cnt + i0);
+    int4* src = reinterpret_cast<int4*>(d.tile_cnt + i0);
 #pragma unroll
     for (int q = 0; q < kScanPer / 4; ++q) {
       const int4 a = src[q];
@@ -205,9 +223,14 @@ __device__ __forceinline__ int scan_round(const Dev& d, int base, int carry, int
       v[4 * q + 2] = a.z;
       v[4 * q + 3] = a.w;
     }
+#pragma unroll
+    for (int q = 0; q < kScanPer / 4; ++q) src[q] = make_int4(0, 0, 0, 0);
   } else {
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) v[i] = i0 + i < n ? d.tile_cnt[i0 + i] : 0;
+    for (int i = 0; i < kScanPer; ++i) {
+      v[i] = i0 + i < n ? d.tile_cnt[i0 + i] : 0;
+      if (i0 + i < n) d.tile_cnt[i0 + i] = 0;
+    }
   }
   int s = 0;
 #pragma unroll
@@ -257,6 +280,9 @@ __device__ __forceinline__ void scan_finish(const Dev& d, int total) {
   if (total > d.cap) atomicOr(d.status, kStatusOverflow);
   *d.pending = 0;  // every transform block has applied the pending Adam step
   for (int i = 0; i < 8; ++i) d.work[i] = 0;
+  d.work[6] = d.chunk_count[0];  // the emission's work list is complete: heavy chunks from the
+  d.work[7] = d.chunk_count[1];  //   front, light ones from the back
+  d.chunk_count[0] = d.chunk_count[1] = 0;
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
@@ -317,132 +343,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(Dev d) {
   }
 }
 
-// Emission, one block per element.  Classification of the element's tiles first, in work
-// proportional to its segments rather than segments x tiles:
-//  - near: every segment marks the tiles whose pixel-centre box, grown by the coverage margin,
-//    its own box meets (computed with 0.05 px of slack, so the mark is a superset of the
-//    distance kernel's near test: a tile it leaves unmarked has no segment within the margin);
-//  - inside / outside for the other tiles: the winding number at a tile's first pixel, from the
-//    crossings of that pixel row with the segments (half-open test).  A crossing at x counts for
-//    the tiles whose first pixel lies left of x; it is added to the last such tile of the row and
-//    a suffix sum along the row spreads it.  For a tile that is not near, every crossing is
-//    farther than the margin from its pixel, so the comparison is well conditioned.
-// Then one thread per tile: the (tile, element) pair takes a slot of its tile's range by counting
-// the tile back down (so the counts are zero again for the next iteration, also after an
-// overflow), and near pairs are appended to the distance kernel's list (one atomic per warp).
-// 128 threads per element; 256 when an element has more than 128 segments (outlines of many
-// curves, as in outline fitting), where one thread per segment is what the classification needs.
-constexpr int kEmitChunkRows = 32, kEmitMaxW = 64;
-template <int kEmitThreads>
-__global__ void __launch_bounds__(kEmitThreads) k_emit(Dev d) {
-  pdl_enter();
-  __shared__ int s_near[kEmitChunkRows * kEmitMaxW];  // segments marking the tile near
-  __shared__ int s_wind[kEmitChunkRows * kEmitMaxW];
-  const int g = blockIdx.x;
-  const int lane = threadIdx.x & 31;
-  const int4 r = d.rect[g];
-  if (r.z < r.x || r.w < r.y) return;
-  const int w = r.z - r.x + 1, hgt = r.w - r.y + 1;
-  const int p = d.elem_prob[g];
-  const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p], T = d.tile;
-  const bool ovf = (*d.status & kStatusOverflow) != 0;  // slots are void: only count back down
-  const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
-  const bool closed = d.elem_closed[g] != 0;
-  const int ns = ovf ? 0 : (closed ? nv : nv - 1);
-  const float4 tp = d.tpx[g];
-  const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)d.prob_res[p];
-  const float mrg = d.L.rho_px + d.L.pad_px + hwpx;
-  const float fT = (float)T, tpx = tp.x + tp.z, tpy = tp.y + tp.w;
-  // rectangles wider than kEmitMaxW tiles are classified in column strips
-  for (int cx0 = 0; cx0 < w; cx0 += kEmitMaxW) {
-    const int cw = min(kEmitMaxW, w - cx0);
-    for (int cy0 = 0; cy0 < hgt; cy0 += kEmitChunkRows) {
-      const int ch = min(kEmitChunkRows, hgt - cy0), cn = cw * ch;
-      const int tx_lo = r.x + cx0, ty_lo = r.y + cy0;  // chunk origin in tiles
-      __syncthreads();  // the previous chunk's readers are done
-      for (int i = threadIdx.x; i < cn; i += kEmitThreads) {
-        s_near[i] = 0;
-        s_wind[i] = 0;
-      }
-      __syncthreads();
-      for (int j = threadIdx.x; j < ns; j += kEmitThreads) {
-        const float4 sa = d.segA[v0 + j];
-        const float2 sb = d.segB[v0 + j];
-        const float bx = sa.x + sa.z;
-        // near: tiles whose grown pixel-centre box meets the segment's box (in pixels)
-        const float x0 = fminf(sa.x, bx) + tpx, x1 = fmaxf(sa.x, bx) + tpx;
-        const float y0 = fminf(sa.y, sb.x) + tpy, y1 = fmaxf(sa.y, sb.x) + tpy;
-        const float m = mrg + 0.06f;
-        const int ax = max((int)floorf((x0 - m - (fT - 0.5f)) / fT) + 1, tx_lo);
-        const int bxt = min((int)floorf((x1 + m - 0.5f) / fT), tx_lo + cw - 1);
-        const int ay = max((int)floorf((y0 - m - (fT - 0.5f)) / fT) + 1, ty_lo);
-        const int byt = min((int)floorf((y1 + m - 0.5f) / fT), ty_lo + ch - 1);
-        for (int ty = ay; ty <= byt; ++ty)
-          for (int tx = ax; tx <= bxt; ++tx) atomicAdd(&s_near[(ty - ty_lo) * cw + (tx - tx_lo)], 1);
-        // crossings of the tiles' first pixel rows
-        if (closed) {
-          for (int ty = ty_lo; ty < ty_lo + ch; ++ty) {
-            const float py = ((float)(ty * T) + 0.5f - tp.y) - tp.w;
-            const bool a_le = py - sa.y >= 0.0f, b_le = py - sb.x >= 0.0f;
-            if (a_le == b_le) continue;
-            const float xc = sa.x + sa.z * ((py - sa.y) / sa.w);  // element frame
-            // last tile whose first pixel lies left of xc
-            int tx = (int)floorf((xc + tpx - 0.5f) / fT);
-            if (tx < tx_lo) continue;
-            tx = min(tx, tx_lo + cw - 1);
-            atomicAdd(&s_wind[(ty - ty_lo) * cw + (tx - tx_lo)], a_le ? 1 : -1);
-          }
-        }
-      }
-      __syncthreads();
-      if (closed && !ovf)  // suffix sums along each row (crossings right of the strip included)
-        for (int row = threadIdx.x; row < ch; row += kEmitThreads) {
-          int acc = 0;
-          for (int c = cw - 1; c >= 0; --c) {
-            acc += s_wind[row * cw + c];
-            s_wind[row * cw + c] = acc;
-          }
-        }
-      __syncthreads();
-      for (int i0 = 0; i0 < cn; i0 += kEmitThreads) {  // warp-uniform trip count
-        const int i = i0 + threadIdx.x;
-        int pos = -1;
-        uint8_t cls = kPairOut;
-        if (i < cn) {
-          const int t = tb + (ty_lo + i / cw) * ntx + tx_lo + i % cw;
-          const int slot = atomicSub(&d.tile_cnt[t], 1) - 1;
-          const unsigned u = d.range[t].x + (unsigned)slot;
-          if (!ovf && u < (unsigned)d.cap) {
-            pos = (int)u;
-            cls = s_near[i] ? kPairNear : (closed && s_wind[i] != 0 ? kPairIn : kPairOut);
-            d.pair_elem[pos] = g;
-            d.pair_tile[pos] = t;
-            d.pair_txy[pos] = (tx_lo + i % cw) | ((ty_lo + i / cw) << 16);
-            d.pair_cls[pos] = cls;
-            if (cls != kPairNear && d.deterministic) d.partial[pos] = make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-        }
-        // near pairs with many segments near the tile go to the front of the list (taken first,
-        // so that the costliest pairs do not trail), the others to the back
-        const bool near = pos >= 0 && cls == kPairNear;
-        const bool heavy = near && s_near[i] > kHeavyNear;
-        const unsigned bh = __ballot_sync(0xffffffffu, heavy), bl = __ballot_sync(0xffffffffu, near && !heavy);
-        int hb = 0, lb = 0;
-        if (lane == 0 && bh) hb = atomicAdd(&d.work[2], __popc(bh));
-        if (lane == 0 && bl) lb = atomicAdd(&d.work[4], __popc(bl));
-        hb = __shfl_sync(0xffffffffu, hb, 0);
-        lb = __shfl_sync(0xffffffffu, lb, 0);
-        const unsigned below = (1u << lane) - 1u;
-        if (near) {
-          const int4 rec = make_int4(pos, g, (tx_lo + i % cw) | ((ty_lo + i / cw) << 16), p);
-          if (heavy) d.near_list[hb + __popc(bh & below)] = rec;
-          else d.near_list[d.cap - 1 - (lb + __popc(bl & below))] = rec;
-        }
-      }
-    }
-  }
-}
-
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad) {
   return klaunch(d.pdl, k_transform, d.n_elems, kTfThreads, 0, s, d, zero_grad ? 1 : 0);
 }
@@ -457,10 +357,5 @@ cudaError_t launch_scan(const Dev& d, cudaStream_t s) {
 }
 
 int scan_rounds(int total_tiles) { return (total_tiles + kScanRound - 1) / kScanRound; }
-
-cudaError_t launch_bin(const Dev& d, cudaStream_t s) {
-  if (d.max_segs > 128) return klaunch(d.pdl, k_emit<256>, d.n_elems, 256, 0, s, d);
-  return klaunch(d.pdl, k_emit<128>, d.n_elems, 128, 0, s, d);
-}
 
 }  // namespace collage

@@ -18,6 +18,8 @@
 namespace collage {
 
 constexpr int kMaxDil = 8;
+constexpr int kChunkPx = 64;            // side, in pixels, of the emission's chunks of an element
+constexpr int kHeavyChunk = 1024;       // segments x tiles above which a chunk is taken first
 constexpr int kStatusOverflow = 1;      // device status bits
 constexpr int kStatusBadParam = 2;
 constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bug)
@@ -29,7 +31,6 @@ constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bu
 constexpr uint8_t kPairOut = 0;   // not near, outside the outline: c = c^pad = 0
 constexpr uint8_t kPairIn = 1;    // not near, inside: c = c^pad = 1
 constexpr uint8_t kPairNear = 2;  // per-pixel signed distances (the distance kernel)
-constexpr int kHeavyNear = 24;    // a near pair with more segments near its tile is taken first
 
 struct LossParams {
   float alpha, beta, gamma, delta;
@@ -79,19 +80,23 @@ struct Dev {
   float4* tpx;                  // [n] translation in px: (hi.x, hi.y, lo.x, lo.y)
   float4* bbox;                 // [n] outline box relative to the translation, grown by the margin
   int4* rect;                   // [n] tile rectangle (tx0, ty0, tx1, ty1), empty if tx1 < tx0
-  int* tile_cnt;                // [total_tiles] counting-sort counts (zero between iterations)
+  int* tile_cnt;                // [total_tiles] counting-sort counts (the tile scan zeroes them)
+  int* tile_fill;               // [total_tiles] slots taken by the emission (the composite zeroes them)
   int* scan_part;               // [scan rounds] round totals, then offsets (levels above one round)
   int* total_pairs;             // [1]
   int cap;                      // pair capacity
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
-  int* pair_tile;               // [cap] tile of each pair slot
-  int* pair_txy;                // [cap] the tile's column | row << 16 within its problem
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
-  int4* near_list;              // [cap] near pairs (slot, element, tile column | row << 16, problem), the
-                                //   distance kernel's work list:
-                                //   heavy ones from the front, light ones from the back
-  int4* live_list;              // [cap] pairs with some non-saturated pixel, as near_list
-                                //   (the adjoint's work list; order depends on atomics)
+  int4* near_list;              // [list_cap] the emission's work list: (element, chunk origin tile
+                                //   column | row << 16, problem, 0), one per kChunkPx-square chunk of
+                                //   every element's tile rectangle, appended by the transform: heavy
+                                //   ones from the front, light ones from the back
+  int list_cap;                 // entries near_list holds
+  int* chunk_count;             // [2] heavy and light chunks appended by the transform (the tile
+                                //   scan moves them to work[6], work[7] and zeroes them)
+  int4* live_list;              // [cap] pairs with some non-saturated pixel: (slot, element, tile
+                                //   column | row << 16, problem), the adjoint's work list (order
+                                //   depends on atomics)
   int* pair_sorted;             // [cap] each tile's elements in increasing element order
   int* pair_slot;               // [cap] the pair slot of each pair_sorted entry
   uint2* range;                 // [total_tiles] [begin, end) into the pair arrays
@@ -116,16 +121,16 @@ struct Dev {
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
   int* sched_base;              // [1] Adam step count when the running schedule graph began
   int* work;                    // [8] per-iteration counters, zeroed by the tile scan:
-                                //   [0] near pairs taken by the distance kernel's blocks,
-                                //   [1] entries of live_list, [2] heavy near pairs (front of
-                                //   near_list), [3] blocks of the last gradient kernel that have
-                                //   finished, [4] light near pairs (back of near_list), [5] blocks
-                                //   of the Adam flush that have finished (its last block resets
-                                //   it), [6..7] spare
+                                //   [0] chunks taken by the emission's blocks, [1] entries of
+                                //   live_list, [3] blocks of the last gradient kernel that have
+                                //   finished, [5] blocks of the Adam flush that have finished
+                                //   (its last block resets it), [6] heavy chunks listed (front of
+                                //   near_list), [7] light chunks (back of near_list), [2, 4] spare
   unsigned long long* paths;    // [4] cumulative counts of the rarely taken kernel paths (since
                                 //   create): [0] pixel rows of a near pair whose crossings
                                 //   overflow the per-row list (winding over every segment),
-                                //   [1] near pairs with more near segments than one staged chunk,
+                                //   [1] emission chunks of outlines with more segments than
+                                //   are staged in shared memory,
                                 //   [2] tiles listing more than 32 pairs (ranked in global
                                 //   memory), [3] container ring chunks after a ring's first
   LossParams L;
@@ -227,9 +232,9 @@ __device__ __forceinline__ void mark_step_if_last(const Dev& d) {
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
 cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
 int scan_rounds(int total_tiles);                                 // rounds (blocks) of the scan
-cudaError_t launch_bin(const Dev& d, cudaStream_t s);            // emit pairs into tile ranges
 cudaError_t launch_container(const Dev& d, cudaStream_t s);
-// part 1: per-pair signed distances; part 2: per-tile composite and loss partials; 3: both
+// part 1: pair emission, classification and per-pixel signed distances (per element chunk);
+// part 2: per-tile composite and loss partials; 3: both
 cudaError_t launch_raster_fwd(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid,
                               float* out_bw, float* out_tau, int part = 3);
 cudaError_t prepare_dilate(int n_dil);  // sets dynamic shared memory limits (not capturable)

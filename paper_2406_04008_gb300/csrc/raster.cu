@@ -71,8 +71,7 @@ __device__ __forceinline__ void seg_update(SegQuery& Q, float dx, float dy, floa
 }
 
 constexpr int kSegCap = 1024;   // container segments staged per chunk
-constexpr int kNearCap = 64;    // near segments staged per chunk of one (tile, element) pair
-constexpr int kRowCross = 16;   // crossings listed per pixel row of a pair
+constexpr int kRowCross = 16;   // crossings listed per pixel row of an emission chunk
 constexpr int kPairWarps = 4;   // pairs per block of the per-pair adjoint (one per warp)
 constexpr float kFar = 1e30f;   // |sd| of a pixel farther than the coverage margin
 
@@ -85,21 +84,8 @@ __device__ __forceinline__ void tile_coords(const Dev& d, int tile, int T, int& 
   ty = lt / ntx;
 }
 
-// ------------------------------------------------------------------------------------------------
-// Signed distances of one near (tile, element) pair per block (the emission lists the near pairs;
-// the others have saturated coverage on the whole tile and need no per-pixel work).
-//
-// The block first splits the outline's segments.  A segment whose box meets the tile's pixel-centre
-// box grown by the coverage margin m = rho + pad (+ stroke half-width) is "near": warp 0 appends
-// it, in index order, to a shared list.  Every other segment lies farther than m from every pixel
-// of the tile; if it spans a pixel row and lies right of the grown box it crosses that row's +x
-// ray right of every pixel, so the other warps add its +-1 to a per-row winding backdrop.  A pixel
-// then runs the distance and crossing tests over the near list only: its winding is backdrop +
-// near crossings; if no near segment is within m the coverage is saturated (0 or 1, as the full
-// loop would give) and sd = +-1e30, else the near minimum is the true distance.
-// ------------------------------------------------------------------------------------------------
 // Winding number of a point (element frame) over every segment of an outline: the crossing test of
-// the distance kernel applied to all segments (the far ones are well conditioned).
+// the per-row lists below applied to all segments (for rows that cross the outline too often).
 __device__ __noinline__ int winding_all(const Dev& d, int v0, int ns, float px, float py) {
   int w = 0;
   for (int j = 0; j < ns; ++j) {
@@ -111,223 +97,313 @@ __device__ __noinline__ int winding_all(const Dev& d, int v0, int ns, float px, 
   return w;
 }
 
-template <int T, int NT>
-__global__ void __launch_bounds__(NT, NT == 64 ? 16 : 1024 / NT) k_pair_sd(Dev d) {
+// ------------------------------------------------------------------------------------------------
+// Emission and signed distances, one (element, chunk) work item per block at a time.  A chunk is a
+// square of up to kChunkPx x kChunkPx pixels of the element's tile rectangle (8 x 8 tiles of 8 px,
+// 4 x 4 of 16 px); the transform kernel lists every element's chunks.  Per chunk the block
+//  1. takes the pair slot of each of its tiles from the tile's range (a fill counter per tile,
+//     which the composite zeroes again);
+//  2. passes once over the element's segments, staging them in shared memory by index: a segment
+//     whose box meets a tile's pixel-centre box grown by the coverage margin m = rho + pad
+//     (+ stroke half-width) (+ 0.06 px of slack) is near that tile (a bit per segment and tile);
+//     for every pixel row of the chunk that a segment crosses (half-open in y, on the dy the
+//     pixels form) the crossing x is listed for the row, or, when it lies right of every pixel of
+//     the chunk, added to the row's backdrop (+1 upward, -1 downward);
+//  3. classifies the tiles: a tile that no segment is near has saturated coverage on every pixel
+//     (0 or 1, as the winding number of its first pixel says) and needs no per-pixel work;
+//  4. its warps take the near tiles one at a time: per pixel, the minimum squared distance over
+//     the tile's near segments in index order (the lowest index wins ties, as the oracle's scan
+//     does); winding = row backdrop + listed crossings right of the pixel (a row with more than
+//     kRowCross crossings tests every segment); sd = +-distance within the margin, else +-1e30
+//     (saturated); the (sd, closest segment) record is saved and pairs with a non-saturated pixel
+//     are listed for the adjoint.
+// Outlines of more than kStageSegs segments are not staged: their tiles test every segment's box
+// on the fly, reading the outline from global memory.
+// A pixel beyond the margin from every segment near its tile is beyond it from all segments (the
+// near test is conservative), so the distance minimum over the near ones is exact wherever it
+// matters, and the winding counts every crossing right of the pixel exactly once.
+// ------------------------------------------------------------------------------------------------
+constexpr int kStageSegs = 512;   // outline segments staged in shared memory
+constexpr int kChunkThreads = 128;
+constexpr int kLiveBatch = 32;
+
+// Tiles of the chunk whose grown pixel-centre box a segment's box [x0, x1] x [y0, y1] (absolute
+// px) meets: columns [*c0, *c1], rows [*r0, *r1] relative to the chunk origin, clipped to it.
+__device__ __forceinline__ void seg_tiles(float x0, float x1, float y0, float y1, float m, int T,
+                                          int tx0, int ty0, int ctw, int cth, int* c0, int* c1,
+                                          int* r0, int* r1) {
+  const float fT = (float)T;
+  *c0 = max((int)floorf((x0 - m - (fT - 0.5f)) / fT) + 1 - tx0, 0);
+  *c1 = min((int)floorf((x1 + m - 0.5f) / fT) - tx0, ctw - 1);
+  *r0 = max((int)floorf((y0 - m - (fT - 0.5f)) / fT) + 1 - ty0, 0);
+  *r1 = min((int)floorf((y1 + m - 0.5f) / fT) - ty0, cth - 1);
+}
+
+template <int T>
+__global__ void __launch_bounds__(kChunkThreads, T == 8 ? 8 : 4) k_raster_chunks(Dev d) {
   pdl_enter();
-  constexpr int NP = T * T, PPT = NP / NT, NW = NT / 32;
-  static_assert(NW >= 2, "warp 0 compacts near segments, the others count the winding backdrop");
-  __shared__ float4 s_seg[kNearCap];
-  __shared__ float2 s_seg2[kNearCap];
-  __shared__ float s_slope[kNearCap];
-  __shared__ int s_idx[kNearCap];
-  __shared__ int s_back[T];
-  __shared__ float s_rx[T][kRowCross];  // per pixel row: x of its crossings with near segments
-  __shared__ signed char s_rd[T][kRowCross];  // and their direction
-  __shared__ int s_rc[T];
-  __shared__ int s_near;
-  if (*d.status & kStatusOverflow) return;
-  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int n_heavy = d.work[2], n_near = n_heavy + d.work[4];
-  // the near pairs: a block's first is its block index in the list, the others are taken from a
-  // shared counter as blocks finish (pair costs vary by two orders of magnitude); s_next is
-  // double-buffered so that thread 0's next write never meets a read of the previous value
+  constexpr int CW = kChunkPx / T, NCT = CW * CW, NP = T * T, PPL = NP / 32;
+  constexpr int ROWS = kChunkPx, MW = kStageSegs / 32;
+  __shared__ float4 s_seg[kStageSegs];  // start (px, relative to the translation), direction
+  __shared__ float s_ie[kStageSegs];    // 1 / |direction|^2
+  __shared__ unsigned s_mask[NCT][MW];  // bit j of tile k: segment j is near tile k
+  __shared__ int s_slot[NCT];           // pair slot of each tile (-1: void)
+  __shared__ unsigned char s_tn[NCT];   // some segment is near the tile
+  __shared__ unsigned char s_ntile[NCT];
+  __shared__ int s_back[ROWS];
+  __shared__ int s_rc[ROWS];
+  __shared__ float s_rx[ROWS][kRowCross];
+  __shared__ signed char s_rd[ROWS][kRowCross];
+  __shared__ int s_nt, s_take;
   __shared__ int s_next[2];
-  constexpr int kLiveBatch = 8;
   __shared__ int4 s_live[kLiveBatch];
-  int n_live = 0;  // thread 0's count of buffered live records
-  for (int i = blockIdx.x, it = 0; i < n_near; ++it) {
-    if (threadIdx.x == 0) s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
-    const int4 rec = d.near_list[i < n_heavy ? i : d.cap - 1 - (i - n_heavy)];
-    const int slot = rec.x, g = rec.y, txy = rec.z;
-    const int tx = txy & 0xffff, ty = txy >> 16, p = rec.w, res = d.prob_res[p];
+  __shared__ int s_nlive;
+  if (*d.status & kStatusOverflow) return;  // the slots are void (the tile scan zeroed the counts)
+  const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int n_heavy = d.work[6], n_chunks = n_heavy + d.work[7];
+  for (int i = blockIdx.x, it = 0; i < n_chunks; ++it) {
+    if (tid == 0) {
+      s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
+      s_nlive = 0;
+      s_take = 0;
+    }
+    const int4 rec = d.near_list[i < n_heavy ? i : d.list_cap - 1 - (i - n_heavy)];
+    const int g = rec.x, tx0 = rec.y & 0xffff, ty0 = rec.y >> 16, p = rec.z;
+    const int4 r = d.rect[g];
+    const int ctw = min(CW, r.z - tx0 + 1), cth = min(CW, r.w - ty0 + 1), nct = ctw * cth;
+    const int res = d.prob_res[p], ntx = d.prob_ntx[p], tb = d.prob_tile_base[p];
     const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
     const bool closed = d.elem_closed[g] != 0;
     const int ns = closed ? nv : nv - 1;
+    const bool staged = ns <= kStageSegs;
+    const int mw = staged ? (ns + 31) >> 5 : 0;
+    // 1. pair slots; cleared marks and row lists
+    if (tid < NCT) {
+      int slot = -1;
+      if (tid < nct) {
+        const int t = tb + (ty0 + tid / ctw) * ntx + tx0 + tid % ctw;
+        const unsigned u = d.range[t].x + (unsigned)atomicAdd(&d.tile_fill[t], 1);
+        if (u < (unsigned)d.cap) {
+          slot = (int)u;
+          d.pair_elem[slot] = g;
+        }
+      }
+      s_slot[tid] = slot;
+      s_tn[tid] = 0;
+    }
+    for (int q = tid; q < nct * mw; q += kChunkThreads) s_mask[q / mw][q % mw] = 0u;
+    for (int q = tid; q < ROWS; q += kChunkThreads) {
+      s_back[q] = 0;
+      s_rc[q] = 0;
+    }
     const float4 tp = d.tpx[g], bb = d.bbox[g];
     const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)res;
-    const float mrg = d.L.rho_px + pad + hwpx;
-    const float mrg2 = mrg * mrg;
-    // tile pixel-centre box in the element frame, grown by the margin (+ rounding slack)
-    const float cx0 = (float)(tx * T) + 0.5f, cx1 = (float)(tx * T + T) - 0.5f;
-    const float cy0 = (float)(ty * T) + 0.5f, cy1 = (float)(ty * T + T) - 0.5f;
-    const float gx0 = (cx0 - tp.x) - tp.z - mrg - 0.01f, gx1 = (cx1 - tp.x) - tp.z + mrg + 0.01f;
-    const float gy0 = (cy0 - tp.y) - tp.w - mrg - 0.01f, gy1 = (cy1 - tp.y) - tp.w + mrg + 0.01f;
-    float dx[PPT], dy[PPT], best[PPT];
-    int bj[PPT], wn[PPT], idx[PPT];
-    bool act[PPT];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int local = threadIdx.x + k * NT;
-      const int X = tx * T + local % T, Y = ty * T + local / T;
-      dx[k] = ((float)X + 0.5f - tp.x) - tp.z;
-      dy[k] = ((float)Y + 0.5f - tp.y) - tp.w;
-      act[k] = X < res && Y < res && dx[k] >= bb.x && dx[k] <= bb.z && dy[k] >= bb.y && dy[k] <= bb.w;
-      any |= act[k];
-      best[k] = FLT_MAX;
-      idx[k] = 0;
-      bj[k] = -1;
-      wn[k] = 0;
-    }
-    // the compaction (warp 0) and the backdrop (the other warps) read the outline from global
-    // memory side by side: the second reader finds it in L1, and no block-wide staging round and
-    // barrier precede them
-    const float4* SA = d.segA + v0;
-    const float2* SB = d.segB + v0;
-    const float* SS = d.segS + v0;
-    for (int base = 0;; base += kNearCap) {
-      __syncthreads();  // the previous users of the shared lists are done
-      if (wid == 0) {
-        // ordered compaction of the near segments with positions in [base, base + kNearCap)
-        int cnt = 0;
-        for (int j0 = 0; j0 < ns; j0 += 32) {
-          const int j = j0 + lane;
-          bool nr = false;
-          float4 sa = make_float4(0.f, 0.f, 0.f, 0.f);
-          float2 sb = make_float2(0.f, 0.f);
-          if (j < ns) {
-            sa = SA[j];
-            sb = SB[j];
-            const float bx = sa.x + sa.z;
-            nr = !(fmaxf(sa.x, bx) < gx0 || fminf(sa.x, bx) > gx1 || fmaxf(sa.y, sb.x) < gy0 ||
-                   fminf(sa.y, sb.x) > gy1);
-          }
-          const unsigned bal = __ballot_sync(0xffffffffu, nr);
-          const int pos = cnt + __popc(bal & ((1u << lane) - 1u)) - base;
-          if (nr && pos >= 0 && pos < kNearCap) {
-            s_seg[pos] = sa;
-            s_seg2[pos] = sb;
-            s_slope[pos] = SS[j];
-            s_idx[pos] = j;
-          }
-          cnt += __popc(bal);
-        }
-        if (lane == 0) s_near = cnt;
-      } else if (base == 0 && closed) {
-        // winding backdrop of the far segments right of the tile
-        for (int r = threadIdx.x - 32; r < T; r += NT - 32) {
-          s_back[r] = 0;
-          s_rc[r] = 0;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(NT - 32));
-        // the rows' dy as the pixels form them: non-decreasing in the row, so a segment whose y
-        // range misses [first row, last row] crosses no row's ray
-        const float yr0 = ((float)(ty * T) + 0.5f - tp.y) - tp.w;
-        const float yr1 = ((float)(ty * T + T - 1) + 0.5f - tp.y) - tp.w;
-        for (int j = threadIdx.x - 32; j < ns; j += NT - 32) {
-          const float4 sa = SA[j];
-          const float2 sb = SB[j];
-          if (fminf(sa.x, sa.x + sa.z) <= gx1) continue;  // near, left or overlapping in x
-          if (fmaxf(sa.y, sb.x) <= yr0 || fminf(sa.y, sb.x) > yr1) continue;
-          const int up = sa.y < sb.x ? 1 : -1;
-          for (int r = 0; r < T; ++r) {
-            const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;  // as a pixel forms dy
-            if ((yr >= sa.y) != (yr >= sb.x)) atomicAdd(&s_back[r], up);
-          }
-        }
+    const float mrg = d.L.rho_px + pad + hwpx, mrg2 = mrg * mrg;
+    const float tpx = tp.x + tp.z, tpy = tp.y + tp.w;
+    const int X0 = tx0 * T, Y0 = ty0 * T, ncol = ctw * T, nrow = cth * T;
+    // the chunk's pixel-centre box in the element frame, as the pixels form dx and dy
+    const float min_dx = ((float)X0 + 0.5f - tp.x) - tp.z;
+    const float max_dx = ((float)(X0 + ncol - 1) + 0.5f - tp.x) - tp.z;
+    const float sl = mrg + 0.06f;  // near test margin with slack
+    __syncthreads();
+    // 2. one pass over the segments: staging, the tiles they are near, row crossings
+    if (ns > kStageSegs && tid == 0 && d.paths) atomicAdd(&d.paths[1], 1ull);
+    for (int j = tid; j < ns; j += kChunkThreads) {
+      const float4 sa = d.segA[v0 + j];
+      const float2 sb = d.segB[v0 + j];
+      if (staged) {
+        s_seg[j] = sa;
+        s_ie[j] = sb.y;
       }
-      __syncthreads();
-      const int total_near = s_near;
-      const int cn = min(kNearCap, total_near - base);
-      if (closed && cn > 0) {
-        // the crossings of the pixel rows with the chunk's near segments, listed per row.  Row r
-        // crosses segment j when its end points lie on different sides of the row (half-open, on
-        // the dy the pixels form); the crossing counts for a pixel left of its x, +1 upward and
-        // -1 downward.  (x of the crossing instead of the sign of cross(e, p - a): the two differ
-        // only for a pixel within rounding of the segment, where sd ~ 0 and c ~ 1/2 either way.)
-        for (int e = threadIdx.x; e < cn * T; e += NT) {
-          const int j = e / T, r = e % T;
-          const float4 sa = s_seg[j];
-          const float yr = ((float)(ty * T + r) + 0.5f - tp.y) - tp.w;
-          const bool a_le = yr - sa.y >= 0.0f, b_le = yr - s_seg2[j].x >= 0.0f;
-          if (a_le != b_le) {
-            const int q = atomicAdd(&s_rc[r], 1);
-            if (q < kRowCross) {
-              s_rx[r][q] = fmaf(yr - sa.y, s_slope[j], sa.x);
-              s_rd[r][q] = a_le ? 1 : -1;
+      const float bx = sa.x + sa.z, by = sb.x;
+      const float x0 = fminf(sa.x, bx), x1 = fmaxf(sa.x, bx), y0 = fminf(sa.y, by), y1 = fmaxf(sa.y, by);
+      int c0, c1, r0, r1;
+      seg_tiles(x0 + tpx, x1 + tpx, y0 + tpy, y1 + tpy, sl, T, tx0, ty0, ctw, cth, &c0, &c1, &r0, &r1);
+      for (int rr = r0; rr <= r1; ++rr)
+        for (int cc = c0; cc <= c1; ++cc) {
+          s_tn[rr * ctw + cc] = 1;
+          if (staged) atomicOr(&s_mask[rr * ctw + cc][j >> 5], 1u << (j & 31));
+        }
+      if (closed && y1 > y0 && x1 > min_dx) {  // crosses some row right of the first pixel column
+        // candidate rows (one row of slack each side), then the exact half-open test
+        const int q0 = max((int)floorf(y0 + tpy - 0.5f) - Y0 - 1, 0);
+        const int q1 = min((int)ceilf(y1 + tpy - 0.5f) - Y0 + 1, nrow - 1);
+        const float slope = d.segS[v0 + j];
+        for (int q = q0; q <= q1; ++q) {
+          const float yr = ((float)(Y0 + q) + 0.5f - tp.y) - tp.w;
+          const bool a_le = yr - sa.y >= 0.0f, b_le = yr - by >= 0.0f;
+          if (a_le == b_le) continue;
+          const float xc = fmaf(yr - sa.y, slope, sa.x);
+          const int dir = a_le ? 1 : -1;
+          if (xc > max_dx) {
+            atomicAdd(&s_back[q], dir);  // right of every pixel of the row
+          } else if (xc > min_dx) {
+            const int k = atomicAdd(&s_rc[q], 1);
+            if (k < kRowCross) {
+              s_rx[q][k] = xc;
+              s_rd[q][k] = (signed char)dir;
             }
           }
         }
       }
-      if (any && cn > 0) {
-#pragma unroll 2
-        for (int j = 0; j < cn; ++j) {
-          const float4 s = s_seg[j];
-          const float ie = s_seg2[j].y;
+    }
+    __syncthreads();
+    // 3. classification; the near tiles in tile order
+    if (tid < nct && s_slot[tid] >= 0) {
+      const int slot = s_slot[tid];
+      uint8_t cls = kPairNear;
+      if (!s_tn[tid]) {
+        int w = 0;
+        if (closed) {
+          const int q = (tid / ctw) * T;
+          const float dx0 = ((float)(X0 + (tid % ctw) * T) + 0.5f - tp.x) - tp.z;
+          const int rc = s_rc[q];
+          if (rc <= kRowCross) {
+            w = s_back[q];
+            for (int k = 0; k < rc; ++k)
+              if (dx0 < s_rx[q][k]) w += s_rd[q][k];
+          } else {
+            w = winding_all(d, v0, ns, dx0, ((float)(Y0 + q) + 0.5f - tp.y) - tp.w);
+          }
+        }
+        cls = w != 0 ? kPairIn : kPairOut;
+        if (d.deterministic) d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      d.pair_cls[slot] = cls;
+    }
+    if (tid < 32) {  // warp 0: the near tiles, in tile order
+      int n = 0;
+      for (int k0 = 0; k0 < nct; k0 += 32) {
+        const int k = k0 + lane;
+        const bool nr = k < nct && s_slot[k] >= 0 && s_tn[k];
+        const unsigned bal = __ballot_sync(0xffffffffu, nr);
+        if (nr) s_ntile[n + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)k;
+        n += __popc(bal);
+      }
+      if (lane == 0) s_nt = n;
+    }
+    __syncthreads();
+    const int nt = s_nt;
+    // 4. the near tiles, one per warp at a time
+    for (;;) {
+      int ni = 0;
+      if (lane == 0) ni = atomicAdd(&s_take, 1);
+      ni = __shfl_sync(0xffffffffu, ni, 0);
+      if (ni >= nt) break;
+      const int k = s_ntile[ni];
+      const int slot = s_slot[k];
+      const int tcx = tx0 + k % ctw, tcy = ty0 + k / ctw;
+      float dx[PPL], dy[PPL], best[PPL];
+      int bidx[PPL];
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            if (!act[k]) continue;
-            const float wx = dx[k] - s.x, wy = dy[k] - s.y;
-            const float t = __saturatef((wx * s.z + wy * s.w) * ie);
+      for (int e = 0; e < PPL; ++e) {
+        const int local = lane + 32 * e;
+        dx[e] = ((float)(tcx * T + local % T) + 0.5f - tp.x) - tp.z;
+        dy[e] = ((float)(tcy * T + local / T) + 0.5f - tp.y) - tp.w;
+        best[e] = FLT_MAX;
+        bidx[e] = 0;
+      }
+      if (staged) {
+        for (int w = 0; w < mw; ++w) {
+          unsigned bits = s_mask[k][w];
+          while (bits) {
+            const int j = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float4 s = s_seg[j];
+            const float ie = s_ie[j];
+#pragma unroll
+            for (int e = 0; e < PPL; ++e) {
+              const float wx = dx[e] - s.x, wy = dy[e] - s.y;
+              const float t = __saturatef((wx * s.z + wy * s.w) * ie);
+              const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
+              const float d2 = fmaf(qx, qx, qy * qy);
+              if (d2 < best[e]) {
+                best[e] = d2;
+                bidx[e] = j;
+              }
+            }
+          }
+        }
+      } else {
+        // the tile's near segments by the same box test as the marks, from global memory
+        const int kc = k % ctw, kr = k / ctw;
+        for (int j = 0; j < ns; ++j) {
+          const float4 s = d.segA[v0 + j];
+          const float2 sb = d.segB[v0 + j];
+          const float bx = s.x + s.z;
+          int c0, c1, r0, r1;
+          seg_tiles(fminf(s.x, bx) + tpx, fmaxf(s.x, bx) + tpx, fminf(s.y, sb.x) + tpy,
+                    fmaxf(s.y, sb.x) + tpy, sl, T, tx0, ty0, ctw, cth, &c0, &c1, &r0, &r1);
+          if (kc < c0 || kc > c1 || kr < r0 || kr > r1) continue;
+#pragma unroll
+          for (int e = 0; e < PPL; ++e) {
+            const float wx = dx[e] - s.x, wy = dy[e] - s.y;
+            const float t = __saturatef((wx * s.z + wy * s.w) * sb.y);
             const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
             const float d2 = fmaf(qx, qx, qy * qy);
-            if (d2 < best[k]) {
-              best[k] = d2;
-              bj[k] = j;
+            if (d2 < best[e]) {
+              best[e] = d2;
+              bidx[e] = j;
             }
           }
         }
+      }
+      float2* sv = d.saved + (size_t)slot * NP;
+      bool live = false;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k)  // a minimum set in this chunk: its segment index
-          if (bj[k] >= 0) {
-            idx[k] = s_idx[bj[k]];
-            bj[k] = -1;
+      for (int e = 0; e < PPL; ++e) {
+        const int local = lane + 32 * e;
+        const int X = tcx * T + local % T, Y = tcy * T + local / T;
+        const bool act = X < res && Y < res && dx[e] >= bb.x && dx[e] <= bb.z && dy[e] >= bb.y &&
+                         dy[e] <= bb.w;
+        float sd = -kFar;
+        if (act) {
+          int w = 0;
+          if (closed) {
+            const int q = Y - Y0, rc = s_rc[q];
+            if (rc <= kRowCross) {
+              w = s_back[q];
+              for (int c = 0; c < rc; ++c)
+                if (dx[e] < s_rx[q][c]) w += s_rd[q][c];
+            } else {
+              w = winding_all(d, v0, ns, dx[e], dy[e]);
+            }
           }
-      }
-      if (total_near <= base + kNearCap) break;
-    }
-    if (closed) __syncthreads();  // the row crossing lists are complete
-    if (d.paths) {
-      if (closed && threadIdx.x < T && s_rc[threadIdx.x] > kRowCross) atomicAdd(&d.paths[0], 1ull);
-      if (threadIdx.x == 0 && s_near > kNearCap) atomicAdd(&d.paths[1], 1ull);
-    }
-    float2* sv = d.saved + (size_t)slot * NP;
-    bool live = false;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      float sd = -kFar;
-      if (act[k] && closed) {
-        const int row = (threadIdx.x + k * NT) / T, rc = s_rc[row];
-        if (rc <= kRowCross) {
-          wn[k] = s_back[row];
-          for (int q = 0; q < rc; ++q)
-            if (dx[k] < s_rx[row][q]) wn[k] += s_rd[row][q];
-        } else {  // a row crossing the outline more often than the list holds: all segments
-          wn[k] = winding_all(d, v0, ns, dx[k], dy[k]);
+          if (best[e] < mrg2) {
+            const float dist = sqrtf(best[e]);
+            sd = closed ? (w != 0 ? dist : -dist) : hwpx - dist;
+          } else {
+            sd = (closed && w != 0) ? kFar : -kFar;
+          }
+          live |= fabsf(sd * inv_rho) < 1.0f || fabsf((sd + pad) * inv_rho) < 1.0f;
         }
+        sv[local] = make_float2(sd, __int_as_float(bidx[e]));
       }
-      if (act[k]) {
-        const int w = closed ? wn[k] : 0;
-        if (best[k] < mrg2) {
-          const float dist = sqrtf(best[k]);
-          sd = closed ? (w != 0 ? dist : -dist) : hwpx - dist;
-        } else {
-          sd = (closed && w != 0) ? kFar : -kFar;
+      if (d.paths && closed && lane < T && s_rc[(k / ctw) * T + lane] > kRowCross)
+        atomicAdd(&d.paths[0], 1ull);
+      if (__any_sync(0xffffffffu, live)) {
+        if (lane == 0) {
+          const int4 lr = make_int4(slot, g, tcx | (tcy << 16), p);
+          const int q = atomicAdd(&s_nlive, 1);
+          if (q < kLiveBatch) s_live[q] = lr;
+          else d.live_list[atomicAdd(&d.work[1], 1)] = lr;
         }
-        live |= fabsf(sd * inv_rho) < 1.0f || fabsf((sd + pad) * inv_rho) < 1.0f;
-      }
-      sv[threadIdx.x + k * NT] = make_float2(sd, __int_as_float(idx[k]));
-    }
-    live = __syncthreads_or(live);
-    if (threadIdx.x == 0) {
-      if (live) {
-        // live pairs are appended kLiveBatch at a time: one atomic per batch
-        s_live[n_live++] = rec;
-        if (n_live == kLiveBatch) {
-          const int at = atomicAdd(&d.work[1], kLiveBatch);
-          for (int q = 0; q < kLiveBatch; ++q) d.live_list[at + q] = s_live[q];
-          n_live = 0;
-        }
-      } else if (d.deterministic) {
+      } else if (lane == 0 && d.deterministic) {
         d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    __syncthreads();
+    // the chunk's live pairs go out with one atomic
+    if (tid < 32) {
+      const int n = min(s_nlive, kLiveBatch);
+      int at = 0;
+      if (lane == 0 && n > 0) at = atomicAdd(&d.work[1], n);
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (lane < n) d.live_list[at + lane] = s_live[lane];
+    }
+    __syncthreads();  // s_live, s_nlive and the shared lists are reused by the next chunk
     i = s_next[it & 1];
-  }
-  if (threadIdx.x == 0 && n_live > 0) {
-    const int at = atomicAdd(&d.work[1], n_live);
-    for (int q = 0; q < n_live; ++q) d.live_list[at + q] = s_live[q];
   }
 }
 
@@ -355,6 +431,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     tile_coords(d, tile, T, p, tx, ty, res);
     const long long pixbase = d.prob_pix_base[p];
     const uint2 rg = d.range[tile];
+    if (lane == 0) d.tile_fill[tile] = 0;  // the emission's slot counter, for the next iteration
     const int m = (int)(rg.y - rg.x);
     const bool small = m <= 32;
     __syncwarp();  // the previous tile's readers of this warp's lists are done
@@ -679,7 +756,7 @@ static cudaError_t fwd_t(const Dev& d, cudaStream_t s, int pair_grid, int tile_g
                          float* tau, int part) {
   constexpr int NT = TileCfg<T>::NT;
   cudaError_t e = cudaSuccess;
-  if (part & 1) e = klaunch(d.pdl, k_pair_sd<T, NT>, pair_grid, NT, 0, s, d);
+  if (part & 1) e = klaunch(d.pdl, k_raster_chunks<T>, pair_grid, kChunkThreads, 0, s, d);
   if (e == cudaSuccess && (part & 2))
     e = klaunch(d.pdl, k_composite<T>, tile_grid, kCompWarps * 32, 0, s, d, bw, tau);
   return e;
@@ -720,7 +797,7 @@ template <int T>
 static void per_sm_t(RasterOcc* o) {
   constexpr int NT = TileCfg<T>::NT;
   int a = 1, b = 1, c = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pair_sd<T, NT>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_raster_chunks<T>, kChunkThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T, false>, kPairWarps * 32, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_composite<T>, kCompWarps * 32, 0);
   o->fwd_per_sm = a > 0 ? a : 1;

@@ -3,8 +3,8 @@
 Each case is built so that one path must run, and the library's path counters (collage_get_info)
 prove that it did:
   - a comb whose pixel rows cross the outline more than 16 times inside one tile: the winding
-    number of those rows is taken over every segment (and, with 16-px tiles, more than 64
-    segments lie near one tile, so the distance loop runs over its near list in chunks);
+    number of those rows is taken over every segment; its 523 segments are more than the 512
+    the emission stages in shared memory, so its tiles read the outline from global memory;
   - 40 small disks stacked at one spot: tiles that list more than 32 elements, ranked in global
     memory by the composite;
   - a disk container of 3000 segments: the container raster stages its ring in chunks.
@@ -45,7 +45,7 @@ def comb(width_px, teeth, tooth_px, body_px, res):
 
 
 def comb_problem(res):
-    els = [(1, comb(24.0, 60, 6.0, 5.0, res), 0.0)]
+    els = [(1, comb(48.0, 260, 6.0, 5.0, res), 0.0)]
     params = [(0.5, 0.5, 0.12, 1.0)]
     rng = np.random.default_rng(3)
     for _ in range(6):  # ordinary elements beside it
@@ -100,8 +100,7 @@ def _check_case(env, prob, res, tile, det=0, opts=None):
 def test_comb_rows_over_the_crossing_list(env, tile, det):
     info = _check_case(env, comb_problem(128), 128, tile, det)
     assert info["path_row_fallback"] > 0, info
-    if tile == 16:
-        assert info["path_long_near"] > 0, info
+    assert info["path_long_near"] > 0, info
 
 
 @pytest.mark.parametrize("tile,det", [(8, 0), (8, 1), (16, 0)])
