@@ -388,6 +388,7 @@ def batch_vs_plain(steps, flush, torch):
     kw = dict(n_levels=1, level_res=[1], level_iters=[50])
     col = Collage(probs, use_graphs=1, persistent=1, tile=0, **kw)
     tile, _ = col.autotune()
+    tuning = col.tuning()
     col.step(3)
     torch.cuda.synchronize()
     bt = sum(_time_steps(col, steps, flush, torch))
@@ -414,7 +415,9 @@ def batch_vs_plain(steps, flush, torch):
         c.close()
     return {"workload": "batch64: 64 collages, %d elements in all, grids 256/512/1024" % n_elems,
             "batched": steps / bt, "plain_sequential": steps / pt, "speedup": pt / bt,
-            "unit": "batch iterations/s (every collage one fwd+bwd+Adam iteration)", "tile": tile}
+            "unit": "batch iterations/s (every collage one fwd+bwd+Adam iteration)", "tile": tile,
+            "tuning": dict(tuning, gain_over_defaults=(tuning["default_ms"] / tuning["best_ms"]
+                                                       if tuning["default_ms"] else None))}
 
 
 def outline_fitting(steps, flush, torch):
@@ -565,6 +568,7 @@ def main():
     col = Collage(prob, **_opts(use_graphs=1, persistent=1, tile=0))
     col.set_level(3)
     tile, _ = col.autotune()
+    tuning = col.tuning()
     col.step(args.warmup)
     torch.cuda.synchronize()
     info = col.info()
@@ -676,6 +680,8 @@ def main():
            "data": "synthetic",
            "config": _config(world),
            "tile": tile, "step_time": spread,
+           "tuning": dict(tuning, gain_over_defaults=(tuning["default_ms"] / tuning["best_ms"]
+                                                      if tuning["default_ms"] else None)),
            "plain": {"value": plain_value, "unit": "iters/s",
                      "path": "eager launches, one block per tile, 16 px tiles",
                      "speedup": value / world / plain_value},

@@ -247,9 +247,33 @@ collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_e
 #define COLLAGE_STAGE_ADAM 8      /* (empty: the Adam step is applied by the next transform) */
 collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float* h_ms);
 
-/* Times each raster tile size on the current level and keeps the fastest (the autotuner);
- * h_best_ms receives its iteration time (may be NULL).  Params are restored afterwards. */
+/* A launch configuration of the iteration's kernels, as the autotuner chooses it. */
+typedef struct {
+  int tile;              /* raster tile side, 8 or 16 */
+  int emit_threads;      /* threads per block of the emission / signed-distance kernel: 128, 256 */
+  float fwd_grid;        /* persistent grids of the emission, adjoint and composite kernels, as */
+  float bwd_grid;        /*   multiples of (SM count x blocks resident per SM): 0.5, 1 or 2 */
+  float comp_grid;
+  float default_ms;      /* loss + gradient iteration time of the defaults (tile 16, 128 threads,
+                            grids x1), ms; 0 when the choice came from the cache */
+  float best_ms;         /* iteration time of the chosen configuration, ms */
+  int trials;            /* configurations timed */
+  int from_cache;        /* 1: the choice of an earlier search with the same key was reused */
+} collage_tuning;
+
+/* The autotuner (no counterpart in the paper): at the current level, times the raster tile sizes
+ * with the other parameters at their defaults, then in turn the emission block size and the
+ * persistent-grid multiples of the emission, adjoint and composite kernels (each candidate a
+ * captured one-iteration graph of loss and gradient, no Adam step, 20 timed replays), and keeps
+ * the fastest.  The choice is cached for the process, keyed on (pixels of the level, element
+ * count, pair density in half-octaves, deterministic mode); a handle with the same key reuses it
+ * without a search.  One configuration serves the whole handle (every problem of a batch).
+ * h_best_ms (may be NULL) receives the chosen configuration's iteration time.  Params and Adam
+ * state are not changed (a pending Adam step is applied as the next iteration would).
+ * Synchronises the device; drops captured graphs.  On failure the previous configuration is
+ * restored. */
 collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
+collage_status collage_get_tuning(collage_t h, collage_tuning* out);
 
 /* The even-distribution term of one res x res image, as collage_loss_backward evaluates it, and
  * its gradient with respect to the occupancy O = 1 - d_ihat, computed without allocating any

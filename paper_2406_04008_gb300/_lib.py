@@ -53,6 +53,12 @@ class collage_info(C.Structure):
                 ("path_wide_tile", C.c_longlong), ("path_ring_chunk", C.c_longlong)]
 
 
+class collage_tuning(C.Structure):
+    _fields_ = [("tile", C.c_int), ("emit_threads", C.c_int), ("fwd_grid", C.c_float),
+                ("bwd_grid", C.c_float), ("comp_grid", C.c_float), ("default_ms", C.c_float),
+                ("best_ms", C.c_float), ("trials", C.c_int), ("from_cache", C.c_int)]
+
+
 # name -> (restype, argtypes), the C ABI of include/collage.h
 _vp = C.c_void_p
 SIGNATURES = {
@@ -80,6 +86,7 @@ SIGNATURES = {
     "collage_get_bins": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _ip]),
     "collage_stage_times": (C.c_int, [_vp, _vp, C.c_int, _fp]),
     "collage_autotune": (C.c_int, [_vp, _vp, _fp]),
+    "collage_get_tuning": (C.c_int, [_vp, C.POINTER(collage_tuning)]),
     "collage_uniform_term_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, _fp, _vp, _vp, _vp, _vp]),
     "collage_get_info": (C.c_int, [_vp, C.POINTER(collage_info)]),
     "collage_sync": (C.c_int, [_vp, _vp]),

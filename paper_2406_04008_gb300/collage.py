@@ -171,6 +171,11 @@ class Collage:
         self._check(self.lib.collage_autotune(self.h, _stream(), C.byref(best)))
         return self.info()["tile"], best.value
 
+    def tuning(self) -> dict:
+        t = L.collage_tuning()
+        self._check(self.lib.collage_get_tuning(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in L.collage_tuning._fields_}
+
     def metrics(self):
         """[n_probs, 8]: object-in-shape, shape, overlap, object-outside-shape pixel counts, then
         LC, OO, EA and L-nU (Sec. 6 and Sec. 6.1) at the current params."""

@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "collage.h"
@@ -52,10 +55,14 @@ struct collage_s {
   };
   std::vector<LevelTab> lv;
   int lv_tile = 0;
-  int pair_grid = 0;  // grid of the per-pair distance kernel
+  int pair_grid = 0;  // grid of the emission / distance kernel
   int bwd_grid = 0;   // grid of the per-pair adjoint
   int tile_grid = 0;  // grid of the per-tile composite
   int sms = 1;
+  // launch configuration (the autotuner's choice): persistent grids are these multiples of the SM
+  // count x resident blocks per SM
+  float fwd_mult = 1.0f, bwd_mult = 1.0f, comp_mult = 1.0f;
+  collage_tuning tuning{};
   // device memory
   Dev d{};
   size_t pix_cap = 0, tile_cap = 0, dtile_cap = 0, pair_cap = 0, saved_tile = 0;
@@ -319,12 +326,13 @@ static void flatten(const collage_problem& p, int e, int spc, std::vector<float2
 // item (pairs up to the capacity, every tile).
 static void set_grids(collage_t h) {
   RasterOcc o{};
-  raster_occupancy(h->d.tile, &o);
+  raster_occupancy(h->d.tile, h->d.emit_threads, &o);
+  auto scaled = [&](int per_sm, float mult) { return std::max(1, (int)std::lround(h->sms * per_sm * mult)); };
   if (h->opt.persistent) {
-    h->pair_grid = h->sms * o.fwd_per_sm;
-    h->bwd_grid = h->sms * o.bwd_per_sm;
+    h->pair_grid = scaled(o.fwd_per_sm, h->fwd_mult);
+    h->bwd_grid = scaled(o.bwd_per_sm, h->bwd_mult);
     h->tile_grid = std::min((h->d.total_tiles + o.tiles_per_block - 1) / o.tiles_per_block,
-                            h->sms * o.tile_per_sm);
+                            scaled(o.tile_per_sm, h->comp_mult));
   } else {
     h->pair_grid = std::max(h->d.cap, 1);
     h->bwd_grid = std::max((h->d.cap + o.bwd_pairs_per_block - 1) / o.bwd_pairs_per_block, 1);
@@ -722,6 +730,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.max_segs = 0;
   for (int e = 0; e < h->N; ++e) d.max_segs = std::max(d.max_segs, h->elem_voff[e + 1] - h->elem_voff[e]);
   d.tile = h->opt.tile;
+  d.emit_threads = 128;
   d.deterministic = o.deterministic ? 1 : 0;
   d.pdl = o.overlap_launches ? 1 : 0;
   d.lr = o.lr;
@@ -1272,45 +1281,183 @@ extern "C" collage_status collage_stage_times(collage_t h, void* stream, int n_i
   return check_and_grow(h, s, &over);
 }
 
+// --------------------------------------------------------------------------------------------
+// Autotuner: raster tile, emission block size and the persistent grids of the emission, adjoint
+// and composite kernels, timed on a captured graph of one loss + gradient iteration; the choice
+// is cached per (level pixels, elements, pair density) for the process.
+// --------------------------------------------------------------------------------------------
+namespace {
+struct TuneChoice {
+  int tile, emit_threads;
+  float fwd, bwd, comp;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<long long, int, int, int>, TuneChoice> g_tune_cache;
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
+// Applies a choice (tile change: new level tables and pair buffers).
+static collage_status apply_choice(collage_t h, const TuneChoice& c) {
+  const bool retile = c.tile != h->d.tile;
+  h->d.tile = c.tile;
+  h->opt.tile = c.tile;
+  h->d.emit_threads = c.emit_threads;
+  h->fwd_mult = c.fwd;
+  h->bwd_mult = c.bwd;
+  h->comp_mult = c.comp;
+  drop_graph(h);
+  if (retile) return setup_level(h, h->level);
+  set_grids(h);
+  return COLLAGE_OK;
+}
+
+// Milliseconds per loss + gradient iteration (no Adam step) in the current configuration: a
+// captured one-iteration graph, 3 replays to warm up, then `reps` timed replays.
+static collage_status time_config(collage_t h, cudaStream_t s, int reps, float* ms) {
+  collage_status st = run_checked(h, s, kLossBwd, nullptr, nullptr);  // regrows if needed
+  if (st) return st;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t e = enqueue_iter(h, h->cap_stream, kLossBwd, nullptr, nullptr);
+  const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, e != cudaSuccess ? e : e2, "autotune capture");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  CK(h, ei);
+  EventPair ev;
+  cudaError_t er = cudaEventCreate(&ev.a);
+  if (er == cudaSuccess) er = cudaEventCreate(&ev.b);
+  for (int i = 0; i < 3 && er == cudaSuccess; ++i) er = cudaGraphLaunch(ge, s);
+  if (er == cudaSuccess) er = cudaEventRecord(ev.a, s);
+  for (int i = 0; i < reps && er == cudaSuccess; ++i) er = cudaGraphLaunch(ge, s);
+  if (er == cudaSuccess) er = cudaEventRecord(ev.b, s);
+  if (er == cudaSuccess) er = cudaEventSynchronize(ev.b);
+  float t = 0.0f;
+  if (er == cudaSuccess) er = cudaEventElapsedTime(&t, ev.a, ev.b);
+  cudaGraphExecDestroy(ge);
+  CK(h, er);
+  bool over = false;
+  st = check_and_grow(h, s, &over);
+  if (st) return st;
+  if (over) return time_config(h, s, reps, ms);  // grown: time again
+  *ms = t / reps;
+  return COLLAGE_OK;
+}
+
 extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int tiles[2] = {8, 16};
-  float best = 1e30f;
-  int best_tile = h->d.tile;
-  cudaEvent_t a, b;
-  CK(h, cudaEventCreate(&a));
-  CK(h, cudaEventCreate(&b));
-  for (int T : tiles) {
-    CK(h, cudaDeviceSynchronize());
-    h->d.tile = T;
-    collage_status st = setup_level(h, h->level);
-    if (st) return st;
-    for (int i = 0; i < 2; ++i) {
-      st = run_checked(h, s, kLossBwd, nullptr, nullptr);
+  const TuneChoice before{h->d.tile, h->d.emit_threads, h->fwd_mult, h->bwd_mult, h->comp_mult};
+  // the key: pixels of the level, elements, and the pair density at 8-px tiles (half-octaves)
+  long long pix = 0;
+  for (int p = 0; p < h->P; ++p) pix += (long long)h->res[p] * h->res[p];
+  const double tiles8 = std::max(1.0, (double)pix / 64.0);
+  const double pairs = (double)std::max(h->h_ctl[2], 1) * (h->d.tile == 8 ? 1.0 : 4.0);
+  const int density = (int)std::floor(2.0 * std::log2(1.0 + pairs / tiles8));
+  const auto key = std::make_tuple(pix, h->N, density, h->opt.deterministic);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      collage_status st = apply_choice(h, it->second);
       if (st) return st;
-    }
-    CK(h, cudaEventRecord(a, s));
-    const int reps = 10;
-    for (int i = 0; i < reps; ++i) CK(h, enqueue_iter(h, s, kLossBwd, nullptr, nullptr));
-    CK(h, cudaEventRecord(b, s));
-    CK(h, cudaEventSynchronize(b));
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, a, b);
-    ms /= reps;
-    if (ms < best) {
-      best = ms;
-      best_tile = T;
+      float ms = 0.0f;
+      st = time_config(h, s, 10, &ms);
+      if (st) return st;
+      h->tuning.tile = it->second.tile;
+      h->tuning.emit_threads = it->second.emit_threads;
+      h->tuning.fwd_grid = it->second.fwd;
+      h->tuning.bwd_grid = it->second.bwd;
+      h->tuning.comp_grid = it->second.comp;
+      h->tuning.best_ms = ms;
+      h->tuning.trials = 0;
+      h->tuning.from_cache = 1;
+      if (h_best_ms) *h_best_ms = ms;
+      return COLLAGE_OK;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  CK(h, cudaDeviceSynchronize());
-  h->d.tile = best_tile;
-  h->opt.tile = best_tile;
-  collage_status st = setup_level(h, h->level);
+  const int reps = 20;
+  int trials = 0;
+  TuneChoice best{16, 128, 1.0f, 1.0f, 1.0f};
+  float best_ms = 1e30f, default_ms = 0.0f;
+  auto trial = [&](const TuneChoice& c, float* out) -> collage_status {
+    collage_status st = apply_choice(h, c);
+    if (!st) st = time_config(h, s, reps, out);
+    ++trials;
+    return st;
+  };
+  collage_status st = COLLAGE_OK;
+  // the tile first (the defaults of everything else), then each launch parameter in turn
+  for (int T : {16, 8}) {
+    float ms = 0.0f;
+    const TuneChoice c{T, 128, 1.0f, 1.0f, 1.0f};
+    if ((st = trial(c, &ms))) break;
+    if (T == 16) default_ms = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  const float mults[3] = {0.5f, 1.0f, 2.0f};
+  for (int dim = 0; dim < 4 && !st; ++dim) {
+    const TuneChoice base = best;
+    for (int k = 0; k < (dim == 0 ? 2 : 3) && !st; ++k) {
+      TuneChoice c = base;
+      if (dim == 0) c.emit_threads = k == 0 ? 128 : 256;
+      if (dim == 1) c.fwd = mults[k];
+      if (dim == 2) c.bwd = mults[k];
+      if (dim == 3) c.comp = mults[k];
+      if (std::memcmp(&c, &base, sizeof(c)) == 0) continue;
+      float ms = 0.0f;
+      if ((st = trial(c, &ms))) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  if (st) {  // leave the handle as it was
+    apply_choice(h, before);
+    return st;
+  }
+  st = apply_choice(h, best);
   if (st) return st;
-  if (h_best_ms) *h_best_ms = best;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  h->tuning.tile = best.tile;
+  h->tuning.emit_threads = best.emit_threads;
+  h->tuning.fwd_grid = best.fwd;
+  h->tuning.bwd_grid = best.bwd;
+  h->tuning.comp_grid = best.comp;
+  h->tuning.default_ms = default_ms;
+  h->tuning.best_ms = best_ms;
+  h->tuning.trials = trials;
+  h->tuning.from_cache = 0;
+  if (h_best_ms) *h_best_ms = best_ms;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_get_tuning(collage_t h, collage_tuning* out) {
+  if (!h || !out) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  *out = h->tuning;
+  out->tile = h->d.tile;
+  out->emit_threads = h->d.emit_threads;
+  out->fwd_grid = h->fwd_mult;
+  out->bwd_grid = h->bwd_mult;
+  out->comp_grid = h->comp_mult;
   return COLLAGE_OK;
 }
 

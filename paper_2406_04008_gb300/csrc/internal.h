@@ -66,6 +66,7 @@ struct Dev {
   int total_tiles, total_dtiles;
   long long total_pix;
   int tile;                     // raster tile side
+  int emit_threads;             // threads per block of the emission / distance kernel (128, 256)
   int n_sort_passes;
   // ---- params / optimiser ----
   float4* q;
@@ -264,7 +265,7 @@ cudaError_t launch_copy_grad(const Dev& d, cudaStream_t s, float* out);
 struct RasterOcc {
   int fwd_per_sm, bwd_per_sm, tile_per_sm, bwd_pairs_per_block, tiles_per_block;
 };
-void raster_occupancy(int tile, RasterOcc* o);
+void raster_occupancy(int tile, int emit_threads, RasterOcc* o);
 // quality metrics after a render pass: counts [4 * n_probs] and squared-distance sums [n_probs]
 cudaError_t launch_metrics(const Dev& d, cudaStream_t s, uint8_t* obj, int* gcol,
                            unsigned long long* cnt, unsigned long long* sums, int max_res);

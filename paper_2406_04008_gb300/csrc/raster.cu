@@ -124,7 +124,6 @@ __device__ __noinline__ int winding_all(const Dev& d, int v0, int ns, float px, 
 // matters, and the winding counts every crossing right of the pixel exactly once.
 // ------------------------------------------------------------------------------------------------
 constexpr int kStageSegs = 512;   // outline segments staged in shared memory
-constexpr int kChunkThreads = 128;
 constexpr int kLiveBatch = 32;
 
 // Tiles of the chunk whose grown pixel-centre box a segment's box [x0, x1] x [y0, y1] (absolute
@@ -139,8 +138,10 @@ __device__ __forceinline__ void seg_tiles(float x0, float x1, float y0, float y1
   *r1 = min((int)floorf((y1 + m - 0.5f) / fT) - ty0, cth - 1);
 }
 
-template <int T>
-__global__ void __launch_bounds__(kChunkThreads, T == 8 ? 8 : 4) k_raster_chunks(Dev d) {
+// NT threads per block (128 or 256, the autotuner's choice); registers capped so that 1024
+// threads (T = 8) or 512 (T = 16, eight pixels per lane) are resident per SM.
+template <int T, int NT>
+__global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunks(Dev d) {
   pdl_enter();
   constexpr int CW = kChunkPx / T, NCT = CW * CW, NP = T * T, PPL = NP / 32;
   constexpr int ROWS = kChunkPx, MW = kStageSegs / 32;
@@ -192,8 +193,8 @@ __global__ void __launch_bounds__(kChunkThreads, T == 8 ? 8 : 4) k_raster_chunks
       s_slot[tid] = slot;
       s_tn[tid] = 0;
     }
-    for (int q = tid; q < nct * mw; q += kChunkThreads) s_mask[q / mw][q % mw] = 0u;
-    for (int q = tid; q < ROWS; q += kChunkThreads) {
+    for (int q = tid; q < nct * mw; q += NT) s_mask[q / mw][q % mw] = 0u;
+    for (int q = tid; q < ROWS; q += NT) {
       s_back[q] = 0;
       s_rc[q] = 0;
     }
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kChunkThreads, T == 8 ? 8 : 4) k_raster_chunks
     __syncthreads();
     // 2. one pass over the segments: staging, the tiles they are near, row crossings
     if (ns > kStageSegs && tid == 0 && d.paths) atomicAdd(&d.paths[1], 1ull);
-    for (int j = tid; j < ns; j += kChunkThreads) {
+    for (int j = tid; j < ns; j += NT) {
       const float4 sa = d.segA[v0 + j];
       const float2 sb = d.segB[v0 + j];
       if (staged) {
@@ -754,9 +755,10 @@ struct TileCfg<16> {
 template <int T>
 static cudaError_t fwd_t(const Dev& d, cudaStream_t s, int pair_grid, int tile_grid, float* bw,
                          float* tau, int part) {
-  constexpr int NT = TileCfg<T>::NT;
   cudaError_t e = cudaSuccess;
-  if (part & 1) e = klaunch(d.pdl, k_raster_chunks<T>, pair_grid, kChunkThreads, 0, s, d);
+  if (part & 1)
+    e = d.emit_threads == 256 ? klaunch(d.pdl, k_raster_chunks<T, 256>, pair_grid, 256, 0, s, d)
+                              : klaunch(d.pdl, k_raster_chunks<T, 128>, pair_grid, 128, 0, s, d);
   if (e == cudaSuccess && (part & 2))
     e = klaunch(d.pdl, k_composite<T>, tile_grid, kCompWarps * 32, 0, s, d, bw, tau);
   return e;
@@ -794,10 +796,10 @@ cudaError_t launch_container(const Dev& d, cudaStream_t s) {
 }
 
 template <int T>
-static void per_sm_t(RasterOcc* o) {
-  constexpr int NT = TileCfg<T>::NT;
+static void per_sm_t(int emit_threads, RasterOcc* o) {
   int a = 1, b = 1, c = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_raster_chunks<T>, kChunkThreads, 0);
+  if (emit_threads == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_raster_chunks<T, 256>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_raster_chunks<T, 128>, 128, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_raster_bwd<T, false>, kPairWarps * 32, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_composite<T>, kCompWarps * 32, 0);
   o->fwd_per_sm = a > 0 ? a : 1;
@@ -807,9 +809,9 @@ static void per_sm_t(RasterOcc* o) {
   o->tiles_per_block = kCompWarps;
 }
 
-void raster_occupancy(int tile, RasterOcc* o) {
-  if (tile == 16) per_sm_t<16>(o);
-  else per_sm_t<8>(o);
+void raster_occupancy(int tile, int emit_threads, RasterOcc* o) {
+  if (tile == 16) per_sm_t<16>(emit_threads, o);
+  else per_sm_t<8>(emit_threads, o);
 }
 
 }  // namespace collage

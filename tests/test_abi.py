@@ -38,7 +38,8 @@ def test_struct_layouts_match_header(lib):
     src = open(os.path.join(ROOT, "include", "collage.h")).read()
     for struct, name in ((lib.collage_problem, "collage_problem"),
                          (lib.collage_options, "collage_options"),
-                         (lib.collage_info, "collage_info")):
+                         (lib.collage_info, "collage_info"),
+                         (lib.collage_tuning, "collage_tuning")):
         body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*" + name + ";", src,
                          re.S).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
