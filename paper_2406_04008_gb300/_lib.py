@@ -14,6 +14,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcollage.so")
+# COLLAGE_CHECKED=1 selects the bounds-checked build of the same sources (see build.py)
+LIB_CHECKED_PATH = os.path.join(_HERE, "_build", "libcollage_checked.so")
 
 COLLAGE_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "OVERFLOW", -5: "TIMEOUT", -6: "STATE"}
@@ -97,11 +99,14 @@ SIGNATURES = {
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libcollage.so (built by paper_2406_04008_gb300.build) and declare its signatures."""
+def load(path: str | None = None):
+    """Load libcollage.so (built by paper_2406_04008_gb300.build), or its bounds-checked build when
+    the environment sets COLLAGE_CHECKED=1, and declare its signatures."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_CHECKED_PATH if os.environ.get("COLLAGE_CHECKED") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libcollage.so is not built ({path}); run "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")

@@ -14,6 +14,10 @@
 #include "collage.h"
 #include "internal.h"
 
+#ifdef COLLAGE_CHECKED
+#include <nvtx3/nvToolsExt.h>
+#endif
+
 using namespace collage;
 
 namespace {
@@ -537,6 +541,17 @@ static collage_status setup_level(collage_t h, int level) {
 // --------------------------------------------------------------------------------------------
 // One iteration: transform -> bin -> raster fwd (+ losses) -> dilation -> adjoint -> loss -> Adam
 // --------------------------------------------------------------------------------------------
+// A named NVTX range around each kernel launch of an iteration (the checked build only; the
+// ranges show in profilers that record NVTX, e.g. ncu --nvtx).
+struct LaunchRange {
+#ifdef COLLAGE_CHECKED
+  explicit LaunchRange(const char* name) { nvtxRangePushA(name); }
+  ~LaunchRange() { nvtxRangePop(); }
+#else
+  explicit LaunchRange(const char*) {}
+#endif
+};
+
 static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* out_bw, float* out_tau,
                                 cudaEvent_t* ev = nullptr) {
   const Dev& d = h->d;
@@ -545,44 +560,50 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   cudaError_t e;
 #define STEP_(x)                      \
   if ((e = (x)) != cudaSuccess) return e;
+#define LAUNCH_(name, x) \
+  {                      \
+    LaunchRange r_(name); \
+    STEP_(x);            \
+  }
 #define MARK_(i) \
   if (ev) STEP_(cudaEventRecord(ev[i], s));
   MARK_(0);
-  STEP_(launch_transform(d, s, bwd && !d.deterministic));
+  LAUNCH_("k_transform", launch_transform(d, s, bwd && !d.deterministic));
   MARK_(1);
-  STEP_(launch_scan(d, s));
+  LAUNCH_("k_tile_scan", launch_scan(d, s));
   MARK_(2);
-  STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 1));
+  LAUNCH_("k_raster_chunks", launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 1));
   MARK_(3);
-  STEP_(launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 2));
+  LAUNCH_("k_composite", launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 2));
   MARK_(4);
   // the loss assembly needs only the composite's and the distribution term's partials: it runs on
   // a side stream beside the distribution adjoint and the raster adjoint (joined at the end of
   // the iteration); under stage timing it stays on the main stream
   const bool side = bwd && !ev;
-  if (dil) STEP_(launch_dilate(d, s, false));
+  if (dil) LAUNCH_("k_dilate_fwd", launch_dilate(d, s, false));
   if (side) {
     STEP_(cudaEventRecord(h->ev_fork, s));
     STEP_(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
-    STEP_(launch_loss(d, h->aux_stream));
+    LAUNCH_("k_loss", launch_loss(d, h->aux_stream));
     STEP_(cudaEventRecord(h->ev_join, h->aux_stream));
   }
-  if (dil) STEP_(launch_dilate(d, s, true));
+  if (dil) LAUNCH_("k_dilate_bwd", launch_dilate(d, s, true));
   MARK_(5);
   // in step mode the last block of the last gradient kernel marks this iteration's Adam step
   // pending; the next transform (or a flush before params are read) applies it
   const bool mark = mode == kStep;
-  if (bwd) STEP_(launch_raster_bwd(d, s, h->bwd_grid, mark && !d.deterministic));
+  if (bwd) LAUNCH_("k_raster_bwd", launch_raster_bwd(d, s, h->bwd_grid, mark && !d.deterministic));
   MARK_(6);
-  if (bwd && d.deterministic) STEP_(launch_grad_reduce(d, s, mark));
+  if (bwd && d.deterministic) LAUNCH_("k_grad_reduce", launch_grad_reduce(d, s, mark));
   MARK_(7);
-  if (bwd && !side) STEP_(launch_loss(d, s));
+  if (bwd && !side) LAUNCH_("k_loss", launch_loss(d, s));
   MARK_(8);
   // outline fitting: the points' gradient, and in step mode their Adam step and new outlines
-  if (bwd && d.fit) STEP_(launch_ctrl_step(d, s, mode == kStep ? 1 : 0));
+  if (bwd && d.fit) LAUNCH_("k_ctrl_step", launch_ctrl_step(d, s, mode == kStep ? 1 : 0));
   if (side) STEP_(cudaStreamWaitEvent(s, h->ev_join, 0));
   MARK_(9);
 #undef STEP_
+#undef LAUNCH_
 #undef MARK_
   return cudaSuccess;
 }

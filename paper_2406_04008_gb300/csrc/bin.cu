@@ -194,8 +194,10 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   if (r.z < r.x || r.w < r.y) return;
   const int w = r.z - r.x + 1, n = w * (r.w - r.y + 1);
   const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
-  for (int i = threadIdx.x; i < n; i += kTfThreads)
-    atomicAdd(&d.tile_cnt[tb + (r.y + i / w) * ntx + r.x + i % w], 1);
+  for (int i = threadIdx.x; i < n; i += kTfThreads) {
+    const int t = tb + (r.y + i / w) * ntx + r.x + i % w;
+    if (in_bounds(d, t >= tb && t < d.prob_tile_base[p + 1])) atomicAdd(&d.tile_cnt[t], 1);
+  }
 }
 
 // Exclusive scan of the per-tile counts into [begin, end) ranges, in rounds of 16384 tiles: each

@@ -149,6 +149,22 @@ struct Dev {
   float2* dv;                   // [V] dL/d(flattened vertex), element-local unit coordinates
 };
 
+// ---- the checked build (-DCOLLAGE_CHECKED, libcollage_checked.so) ----
+// in_bounds(d, ok): a failed index check latches kStatusInternal (the next host call that reads
+// the status word returns COLLAGE_ERR_STATE) and the caller skips the guarded access, so nothing
+// is read or written past a bound and nothing traps.  In the regular build it is the constant
+// true and compiles away.
+__device__ __forceinline__ bool in_bounds(const Dev& d, bool ok) {
+#ifdef COLLAGE_CHECKED
+  if (!ok) atomicOr(d.status, kStatusInternal);
+  return ok;
+#else
+  (void)d;
+  (void)ok;
+  return true;
+#endif
+}
+
 // Adam (bias-corrected, the update torch.optim.Adam performs; it stands in for the plain descent
 // step of Eq. 4) of element g at step t >= 1 with gradient gr, then the clamp of s.
 // An iteration's step is applied lazily: the loss assembly marks it pending, and the next

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
   const int n_own = dil_count(d, 0);
   for (int li = blockIdx.x; li < n_own; li += gridDim.x) {
     const int dt = dil_tile(d, 0, li);
+    if (!in_bounds(d, dt >= 0 && dt < d.total_dtiles)) continue;
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
   const int n_halo = dil_count(d, 1);
   for (int li = blockIdx.x; li < n_halo; li += gridDim.x) {
     const int dt = dil_tile(d, 1, li);
+    if (!in_bounds(d, dt >= 0 && dt < d.total_dtiles)) continue;
     // a tile without coverage of its own was not written by the forward pass: store, not add
     const bool own = (dil_flags(d, dt) & kFlagOwn) != 0;
     const int p = find_prob_d(d.prob_dtile_base, d.n_probs, dt);
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(kReduceWarps * 32) k_grad_reduce(Dev d, int ma
           if (d.pair_sorted[mid] < g) lo = mid + 1;
           else hi = mid;
         }
-        if (lo < rg.y && d.pair_sorted[lo] == g) {
+        if (lo < rg.y && d.pair_sorted[lo] == g && in_bounds(d, d.pair_slot[lo] < d.cap)) {
           const float4 v = d.partial[d.pair_slot[lo]];
           acc.x += v.x;
           acc.y += v.y;

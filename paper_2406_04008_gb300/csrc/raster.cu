@@ -169,8 +169,11 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       s_nlive = 0;
       s_take = 0;
     }
-    const int4 rec = d.near_list[i < n_heavy ? i : d.list_cap - 1 - (i - n_heavy)];
+    const int li = i < n_heavy ? i : d.list_cap - 1 - (i - n_heavy);
+    if (!in_bounds(d, li >= 0 && li < d.list_cap)) break;
+    const int4 rec = d.near_list[li];
     const int g = rec.x, tx0 = rec.y & 0xffff, ty0 = rec.y >> 16, p = rec.z;
+    if (!in_bounds(d, g >= 0 && g < d.n_elems && p >= 0 && p < d.n_probs)) break;
     const int4 r = d.rect[g];
     const int ctw = min(CW, r.z - tx0 + 1), cth = min(CW, r.w - ty0 + 1), nct = ctw * cth;
     const int res = d.prob_res[p], ntx = d.prob_ntx[p], tb = d.prob_tile_base[p];
@@ -182,8 +185,8 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
     // 1. pair slots; cleared marks and row lists
     if (tid < NCT) {
       int slot = -1;
-      if (tid < nct) {
-        const int t = tb + (ty0 + tid / ctw) * ntx + tx0 + tid % ctw;
+      const int t = tb + (ty0 + tid / ctw) * ntx + tx0 + tid % ctw;
+      if (tid < nct && in_bounds(d, t >= tb && t < d.prob_tile_base[p + 1])) {
         const unsigned u = d.range[t].x + (unsigned)atomicAdd(&d.tile_fill[t], 1);
         if (u < (unsigned)d.cap) {
           slot = (int)u;
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       seg_tiles(x0 + tpx, x1 + tpx, y0 + tpy, y1 + tpy, sl, T, tx0, ty0, ctw, cth, &c0, &c1, &r0, &r1);
       for (int rr = r0; rr <= r1; ++rr)
         for (int cc = c0; cc <= c1; ++cc) {
+          if (!in_bounds(d, rr * ctw + cc < NCT)) continue;
           s_tn[rr * ctw + cc] = 1;
           if (staged) atomicOr(&s_mask[rr * ctw + cc][j >> 5], 1u << (j & 31));
         }
@@ -232,6 +236,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         const int q1 = min((int)ceilf(y1 + tpy - 0.5f) - Y0 + 1, nrow - 1);
         const float slope = d.segS[v0 + j];
         for (int q = q0; q <= q1; ++q) {
+          if (!in_bounds(d, q < ROWS)) break;
           const float yr = ((float)(Y0 + q) + 0.5f - tp.y) - tp.w;
           const bool a_le = yr - sa.y >= 0.0f, b_le = yr - by >= 0.0f;
           if (a_le == b_le) continue;
@@ -387,8 +392,12 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         if (lane == 0) {
           const int4 lr = make_int4(slot, g, tcx | (tcy << 16), p);
           const int q = atomicAdd(&s_nlive, 1);
-          if (q < kLiveBatch) s_live[q] = lr;
-          else d.live_list[atomicAdd(&d.work[1], 1)] = lr;
+          if (q < kLiveBatch) {
+            s_live[q] = lr;
+          } else {
+            const int at = atomicAdd(&d.work[1], 1);
+            if (in_bounds(d, at < d.cap)) d.live_list[at] = lr;
+          }
         }
       } else if (lane == 0 && d.deterministic) {
         d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -401,7 +410,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       int at = 0;
       if (lane == 0 && n > 0) at = atomicAdd(&d.work[1], n);
       at = __shfl_sync(0xffffffffu, at, 0);
-      if (lane < n) d.live_list[at + lane] = s_live[lane];
+      if (lane < n && in_bounds(d, at + lane < d.cap)) d.live_list[at + lane] = s_live[lane];
     }
     __syncthreads();  // s_live, s_nlive and the shared lists are reused by the next chunk
     i = s_next[it & 1];
@@ -431,8 +440,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
     const long long pixbase = d.prob_pix_base[p];
-    const uint2 rg = d.range[tile];
+    uint2 rg = d.range[tile];
     if (lane == 0) d.tile_fill[tile] = 0;  // the emission's slot counter, for the next iteration
+    if (!in_bounds(d, rg.x <= rg.y && rg.y <= (unsigned)d.cap)) rg = make_uint2(0u, 0u);
     const int m = (int)(rg.y - rg.x);
     const bool small = m <= 32;
     __syncwarp();  // the previous tile's readers of this warp's lists are done
@@ -543,6 +553,10 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
     // the next pair's record is read while this one is worked on
     const int4 rec_next = i + stride < n_live ? d.live_list[i + stride] : rec;
     const int slot = rec.x, g = rec.y, txy = rec.z, p = rec.w;
+    if (!in_bounds(d, slot >= 0 && slot < d.cap && g >= 0 && g < d.n_elems && p >= 0 && p < d.n_probs)) {
+      rec = rec_next;
+      continue;
+    }
     const int tx = txy & 0xffff, ty = txy >> 16, res = d.prob_res[p];
     const long long pixbase = d.prob_pix_base[p];
     const float inv_np = 1.0f / ((float)res * (float)res);
@@ -604,6 +618,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark)
         const float gcp = gA * tau * pt / (1.0f - tau * cp);
         gsd[k] = (gc * dSfun(x) + gcp * dSfun(xp)) * inv_rho;
       }
+      if (gsd[k] != 0.0f && !in_bounds(d, (unsigned)__float_as_int(srec[k].y) <
+                                               (unsigned)(d.elem_voff[g + 1] - v0)))
+        gsd[k] = 0.0f;
       if (gsd[k] != 0.0f) sa[k] = d.segA[v0 + __float_as_int(srec[k].y)];
     }
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;

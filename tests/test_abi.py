@@ -27,9 +27,10 @@ def _declared():
 def test_every_declared_symbol_is_exported(lib):
     names = _declared()
     assert len(names) >= 20
-    so = C.CDLL(lib.LIB_PATH)
-    for n in names:
-        assert hasattr(so, n), n
+    for path in (lib.LIB_PATH, lib.LIB_CHECKED_PATH):  # the regular and the bounds-checked build
+        so = C.CDLL(path)
+        for n in names:
+            assert hasattr(so, n), (path, n)
     assert set(names) == set(lib.SIGNATURES), set(names) ^ set(lib.SIGNATURES)
 
 
