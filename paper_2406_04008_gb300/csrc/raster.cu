@@ -131,11 +131,20 @@ constexpr int kLiveBatch = 32;
 __device__ __forceinline__ void seg_tiles(float x0, float x1, float y0, float y1, float m, int T,
                                           int tx0, int ty0, int ctw, int cth, int* c0, int* c1,
                                           int* r0, int* r1) {
-  const float fT = (float)T;
-  *c0 = max((int)floorf((x0 - m - (fT - 0.5f)) / fT) + 1 - tx0, 0);
-  *c1 = min((int)floorf((x1 + m - 0.5f) / fT) - tx0, ctw - 1);
-  *r0 = max((int)floorf((y0 - m - (fT - 0.5f)) / fT) + 1 - ty0, 0);
-  *r1 = min((int)floorf((y1 + m - 0.5f) / fT) - ty0, cth - 1);
+  const float fT = (float)T, iT = 1.0f / fT;  // T is a power of two: x * (1 / T) is x / T exactly
+  *c0 = max((int)floorf((x0 - m - (fT - 0.5f)) * iT) + 1 - tx0, 0);
+  *c1 = min((int)floorf((x1 + m - 0.5f) * iT) - tx0, ctw - 1);
+  *r0 = max((int)floorf((y0 - m - (fT - 0.5f)) * iT) + 1 - ty0, 0);
+  *r1 = min((int)floorf((y1 + m - 0.5f) * iT) - ty0, cth - 1);
+}
+
+// Squared distance from (dx, dy) to the segment a + u e, u in [0, 1], with f = e / |e|^2 (the
+// clamped parameter is then a dot product): the operations of the oracle's closest-point rule.
+__device__ __forceinline__ float seg_d2(float dx, float dy, float4 s, float2 f) {
+  const float wx = dx - s.x, wy = dy - s.y;
+  const float t = __saturatef(fmaf(wy, f.y, wx * f.x));
+  const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
+  return fmaf(qx, qx, qy * qy);
 }
 
 // NT threads per block (128 or 256, the autotuner's choice); registers capped so that 1024
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
   constexpr int CW = kChunkPx / T, NCT = CW * CW, NP = T * T, PPL = NP / 32;
   constexpr int ROWS = kChunkPx, MW = kStageSegs / 32;
   __shared__ float4 s_seg[kStageSegs];  // start (px, relative to the translation), direction
-  __shared__ float s_ie[kStageSegs];    // 1 / |direction|^2
+  __shared__ float2 s_f[kStageSegs];    // direction / |direction|^2
   __shared__ unsigned s_mask[NCT][MW];  // bit j of tile k: segment j is near tile k
   __shared__ int s_slot[NCT];           // pair slot of each tile (-1: void)
   __shared__ unsigned char s_tn[NCT];   // some segment is near the tile
@@ -218,7 +227,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       const float2 sb = d.segB[v0 + j];
       if (staged) {
         s_seg[j] = sa;
-        s_ie[j] = sb.y;
+        s_f[j] = make_float2(sa.z * sb.y, sa.w * sb.y);
       }
       const float bx = sa.x + sa.z, by = sb.x;
       const float x0 = fminf(sa.x, bx), x1 = fmaxf(sa.x, bx), y0 = fminf(sa.y, by), y1 = fmaxf(sa.y, by);
@@ -314,16 +323,13 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         for (int w = 0; w < mw; ++w) {
           unsigned bits = s_mask[k][w];
           while (bits) {
-            const int j = w * 32 + __ffs(bits) - 1;
+            const int j = w * 32 + __ffs(bits) - 1;  // in index order
             bits &= bits - 1u;
-            const float4 s = s_seg[j];
-            const float ie = s_ie[j];
+            const float4 sg = s_seg[j];
+            const float2 f = s_f[j];
 #pragma unroll
             for (int e = 0; e < PPL; ++e) {
-              const float wx = dx[e] - s.x, wy = dy[e] - s.y;
-              const float t = __saturatef((wx * s.z + wy * s.w) * ie);
-              const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
-              const float d2 = fmaf(qx, qx, qy * qy);
+              const float d2 = seg_d2(dx[e], dy[e], sg, f);
               if (d2 < best[e]) {
                 best[e] = d2;
                 bidx[e] = j;
@@ -342,12 +348,10 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
           seg_tiles(fminf(s.x, bx) + tpx, fmaxf(s.x, bx) + tpx, fminf(s.y, sb.x) + tpy,
                     fmaxf(s.y, sb.x) + tpy, sl, T, tx0, ty0, ctw, cth, &c0, &c1, &r0, &r1);
           if (kc < c0 || kc > c1 || kr < r0 || kr > r1) continue;
+          const float2 f = make_float2(s.z * sb.y, s.w * sb.y);
 #pragma unroll
           for (int e = 0; e < PPL; ++e) {
-            const float wx = dx[e] - s.x, wy = dy[e] - s.y;
-            const float t = __saturatef((wx * s.z + wy * s.w) * sb.y);
-            const float qx = fmaf(-t, s.z, wx), qy = fmaf(-t, s.w, wy);
-            const float d2 = fmaf(qx, qx, qy * qy);
+            const float d2 = seg_d2(dx[e], dy[e], s, f);
             if (d2 < best[e]) {
               best[e] = d2;
               bidx[e] = j;
