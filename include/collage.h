@@ -237,7 +237,8 @@ collage_status collage_get_bins(collage_t h, void* stream, int* d_tile, int* d_e
  * (see COLLAGE_STAGE_*); the kernels run on `stream`, timed with events on that stream. */
 #define COLLAGE_N_STAGES 9
 #define COLLAGE_STAGE_TRANSFORM 0 /* previous Adam step, transform, segment records, tile counts */
-#define COLLAGE_STAGE_BIN 1       /* tile-count scan */
+#define COLLAGE_STAGE_BIN 1       /* (empty: the transform allocates the pair slots, the emission
+                                     files them in the tiles' lists) */
 #define COLLAGE_STAGE_RASTER_FWD 2 /* pair emission, classification and per-pixel signed distances */
 #define COLLAGE_STAGE_COMPOSITE 3 /* per-tile products and loss partials */
 #define COLLAGE_STAGE_DILATE 4    /* distribution term forward and backward */

@@ -70,8 +70,10 @@ struct collage_s {
   // device memory
   Dev d{};
   size_t pix_cap = 0, tile_cap = 0, dtile_cap = 0, pair_cap = 0, saved_tile = 0;
+  std::vector<void*> list_bufs;  // per-tile pair lists: tile_cap tiles x d.tile_cap entries
   int* ctl = nullptr;        // device: status, step, total_pairs, pending, 8 work counters,
-                             //   schedule base step, 3 spare
+                             //   schedule base step, 2 chunk counts, pairs allocated, emission
+                             //   blocks finished, 7 spare
   int* h_ctl = nullptr;      // pinned mirror
   float* d_stage = nullptr;  // device: params, loss terms and control words gathered for one copy
   float* h_stage = nullptr;  // pinned: their host copy ([4n | 5 n_probs | 4], see k_adam_flush)
@@ -177,6 +179,7 @@ collage_s::~collage_s() {
   if (h_ctl) cudaFreeHost(h_ctl);
   if (h_stage) cudaFreeHost(h_stage);
   free_list(pair_bufs);
+  free_list(list_bufs);
   free_list(level_bufs);
   free_list(owned);
 }
@@ -356,8 +359,6 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
   CK(h, dmalloc(h->pair_bufs, d.live_list, cap));
   CK(h, dmalloc(h->pair_bufs, d.near_list, cap));
   CK(h, dmalloc(h->pair_bufs, d.pair_cls, cap));
-  CK(h, dmalloc(h->pair_bufs, d.pair_sorted, cap));
-  CK(h, dmalloc(h->pair_bufs, d.pair_slot, cap));
   CK(h, dmalloc(h->pair_bufs, d.partial, cap));
   CK(h, dmalloc(h->pair_bufs, d.saved, cap * tt));
   h->pair_cap = cap;
@@ -378,6 +379,20 @@ static collage_status read_ctl(collage_t h, cudaStream_t s) {
   return COLLAGE_OK;
 }
 
+// Per-tile pair lists of capacity `per_tile` for the largest level's tiles.
+static collage_status ensure_tile_lists(collage_t h, int per_tile) {
+  drop_graph(h);
+  CK(h, cudaDeviceSynchronize());
+  free_list(h->list_bufs);
+  Dev& d = h->d;
+  const size_t n = h->tile_cap * (size_t)per_tile;
+  CK(h, dmalloc(h->list_bufs, d.tile_list, n));
+  CK(h, dmalloc(h->list_bufs, d.tile_sorted, n));
+  CK(h, dmalloc(h->list_bufs, d.tile_sorted_slot, n));
+  d.tile_cap = per_tile;
+  return COLLAGE_OK;
+}
+
 // Per-pixel, per-tile and per-dilation-tile buffers for the largest level (regrown if needed).
 static collage_status ensure_level_bufs(collage_t h, size_t np, size_t nt, size_t nd) {
   if (np <= h->pix_cap && nt <= h->tile_cap && nd <= h->dtile_cap) return COLLAGE_OK;
@@ -392,12 +407,10 @@ static collage_status ensure_level_bufs(collage_t h, size_t np, size_t nt, size_
   CK(h, dmalloc(h->level_bufs, d.gOu, np));
   CK(h, dmalloc(h->level_bufs, d.dil_m, np));
   CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
-  CK(h, dmalloc(h->level_bufs, d.range, nt));
-  CK(h, dmalloc(h->level_bufs, d.tile_cnt, nt));
-  CK(h, cudaMemset(d.tile_cnt, 0, sizeof(int) * nt));
-  CK(h, dmalloc(h->level_bufs, d.tile_fill, nt));
-  CK(h, cudaMemset(d.tile_fill, 0, sizeof(int) * nt));
-  CK(h, dmalloc(h->level_bufs, d.scan_part, (size_t)scan_rounds((int)nt)));
+  CK(h, dmalloc(h->level_bufs, d.tile_n, nt));
+  CK(h, cudaMemset(d.tile_n, 0, sizeof(int) * nt));
+  CK(h, dmalloc(h->level_bufs, d.tile_m, nt));
+  CK(h, cudaMemset(d.tile_m, 0, sizeof(int) * nt));
   CK(h, dmalloc(h->level_bufs, d.lossA, nt));
   CK(h, dmalloc(h->level_bufs, d.lossU, nd));
   CK(h, dmalloc(h->level_bufs, d.dtile_flags, nd));
@@ -406,7 +419,7 @@ static collage_status ensure_level_bufs(collage_t h, size_t np, size_t nt, size_
   h->pix_cap = np;
   h->tile_cap = nt;
   h->dtile_cap = nd;
-  return COLLAGE_OK;
+  return ensure_tile_lists(h, d.tile_cap);
 }
 
 // Every level's tables for the current raster tile: per problem the resolution, tiles per side and
@@ -496,21 +509,25 @@ static cudaError_t enqueue_level_switch(const Dev& d, cudaStream_t s) {
   return e;
 }
 
-// Pairs that binning the current params at the selected level produces: the transform and the
-// tile scan with an unbounded capacity, read back (synchronises the stream).  The tile counts are
-// left at zero.  A pending Adam step is applied on the way, as the next iteration would.
+// Pairs that binning the current params at the selected level produces: the transform with an
+// unbounded capacity allocates the slots, and their count is read back (synchronises the stream).
+// A pending Adam step is applied on the way, as the next iteration would.
 static collage_status probe_pairs(collage_t h, cudaStream_t s, size_t* need) {
   Dev& d = h->d;
-  CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
   Dev probe = d;
   probe.cap = 0x7fffffff;
+  probe.list_cap = 0;  // no chunk is listed
   CK(h, launch_transform(probe, s, false));
-  CK(h, launch_scan(probe, s));
-  collage_status st = read_ctl(h, s);
-  if (st) return st;
-  // the probe counted tiles without emitting: clear the counts for the first real iteration
-  CK(h, cudaMemsetAsync(d.tile_cnt, 0, sizeof(int) * (size_t)d.total_tiles, s));
+  CK(h, cudaMemcpyAsync(h->h_ctl + 2, d.pair_need, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // the probe allocated slots and counted chunks without an emission: reset both, and the pending
+  // Adam step it applied
+  CK(h, cudaMemsetAsync(d.pair_need, 0, sizeof(int), s));
+  CK(h, cudaMemsetAsync(d.chunk_count, 0, 2 * sizeof(int), s));
+  CK(h, cudaMemsetAsync(d.pending, 0, sizeof(int), s));
+  CK(h, cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
+  h->h_ctl[3] = 0;
+  h->ctl_current = false;  // h_ctl[1] was not read
   if (h->h_ctl[0] & kStatusBadParam) return fail(h, COLLAGE_ERR_INVALID_ARG, "params are not finite or s <= 0");
   *need = (size_t)h->h_ctl[2];
   return COLLAGE_OK;
@@ -570,7 +587,6 @@ static cudaError_t enqueue_iter(collage_t h, cudaStream_t s, int mode, float* ou
   MARK_(0);
   LAUNCH_("k_transform", launch_transform(d, s, bwd && !d.deterministic));
   MARK_(1);
-  LAUNCH_("k_tile_scan", launch_scan(d, s));
   MARK_(2);
   LAUNCH_("k_raster_chunks", launch_raster_fwd(d, s, h->pair_grid, h->tile_grid, out_bw, out_tau, 1));
   MARK_(3);
@@ -638,12 +654,22 @@ static collage_status check_and_grow(collage_t h, cudaStream_t s, bool* overflow
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));
     return fail(h, COLLAGE_ERR_INVALID_ARG, "params became non-finite or s <= 0");
   }
-  if (status & kStatusOverflow) {
+  if (status & (kStatusOverflow | kStatusTileCap)) {
+    // void bins: the tiles' lists are cleared, then the pair buffers or the lists regrown
     *overflowed = true;
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));
+    CK(h, cudaMemsetAsync(h->d.tile_n, 0, sizeof(int) * h->tile_cap, s));
     CK(h, cudaStreamSynchronize(s));
-    if (need + need / 2 + 256 > 0x7fffffff / 2) return fail(h, COLLAGE_ERR_OVERFLOW, "bin pairs exceed 2^30");
-    return ensure_pairs(h, need + need / 2 + 256);
+    if (status & kStatusTileCap) {
+      if (h->d.tile_cap >= (1 << 20)) return fail(h, COLLAGE_ERR_OVERFLOW, "a tile lists more than 2^20 pairs");
+      collage_status st2 = ensure_tile_lists(h, 2 * h->d.tile_cap);
+      if (st2) return st2;
+    }
+    if (status & kStatusOverflow) {
+      if (need + need / 2 + 256 > 0x7fffffff / 2) return fail(h, COLLAGE_ERR_OVERFLOW, "bin pairs exceed 2^30");
+      return ensure_pairs(h, need + need / 2 + 256);
+    }
+    return COLLAGE_OK;
   }
   if (need * 4 > h->pair_cap * 3) return ensure_pairs(h, need + need / 2 + 256);
   return COLLAGE_OK;
@@ -856,8 +882,9 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
   CKC(dmalloc(h->owned, d.paths, 4));
   CKC(cudaMemset(d.paths, 0, sizeof(unsigned long long) * 4));
-  CKC(dmalloc(h->owned, h->ctl, 16));
-  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 16));
+  CKC(dmalloc(h->owned, h->ctl, 24));
+  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 24));
+  CKC(dmalloc(h->owned, d.elem_pbase, h->N));
   d.status = h->ctl;
   d.step = h->ctl + 1;
   d.total_pairs = h->ctl + 2;
@@ -865,6 +892,9 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.work = h->ctl + 4;
   d.sched_base = h->ctl + 12;
   d.chunk_count = h->ctl + 13;  // [13], [14]
+  d.pair_need = h->ctl + 15;
+  d.emit_done = h->ctl + 16;
+  d.tile_cap = 16;  // pairs per tile list (doubled when a tile outgrows it)
   CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
   CKC(dmalloc(h->owned, h->d_stage, stage_floats(h)));
   CKC(cudaHostAlloc(&h->h_stage, sizeof(float) * stage_floats(h), cudaHostAllocMapped));
@@ -1095,7 +1125,7 @@ extern "C" collage_status collage_run_schedule(collage_t h, void* stream) {
   // the device now holds the last level that ran (or the last level): the host view follows
   drop_iter_graph(h);
   h->level = -1;
-  if (done == total && !(h->h_ctl[0] & (kStatusOverflow | kStatusBadParam | kStatusInternal))) {
+  if (done == total && !(h->h_ctl[0] & (kStatusVoid | kStatusInternal))) {
     st = apply_level(h, L - 1);
     if (st) return st;
     set_grids(h);
@@ -1148,7 +1178,7 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
   st = copy_out();
   if (st) return st;
   const int status = h->h_ctl[0], done = h->h_ctl[1] - step0;
-  if (!(status & (kStatusOverflow | kStatusBadParam | kStatusInternal)) && done == n_iters &&
+  if (!(status & (kStatusVoid | kStatusInternal)) && done == n_iters &&
       (size_t)h->h_ctl[2] * 4 <= h->pair_cap * 3)
     return COLLAGE_OK;
   // an overflow (or a status to report): the synchronous path regrows and runs the rest
@@ -1255,15 +1285,18 @@ extern "C" collage_status collage_get_bins(collage_t h, void* stream, int* d_til
   *h_n = n;
   if (!d_tile && !d_elem) return COLLAGE_OK;
   if (cap < n) return fail(h, COLLAGE_ERR_INVALID_ARG, "cap is smaller than the pair count");
-  std::vector<uint2> rg(h->d.total_tiles);
-  std::vector<int> el(n), te(n), ee(n);
-  CK(h, cudaMemcpy(rg.data(), h->d.range, sizeof(uint2) * rg.size(), cudaMemcpyDeviceToHost));
-  if (n) CK(h, cudaMemcpy(el.data(), h->d.pair_sorted, sizeof(int) * n, cudaMemcpyDeviceToHost));
-  for (int t = 0; t < h->d.total_tiles; ++t)
-    for (uint32_t k = rg[t].x; k < rg[t].y && k < (uint32_t)n; ++k) {
-      te[k] = t;
-      ee[k] = el[k];
+  const size_t nt = (size_t)h->d.total_tiles, C = (size_t)h->d.tile_cap;
+  std::vector<int> tm(nt), ts(nt * C), te, ee;
+  CK(h, cudaMemcpy(tm.data(), h->d.tile_m, sizeof(int) * nt, cudaMemcpyDeviceToHost));
+  CK(h, cudaMemcpy(ts.data(), h->d.tile_sorted, sizeof(int) * nt * C, cudaMemcpyDeviceToHost));
+  te.reserve(n);
+  ee.reserve(n);
+  for (size_t t = 0; t < nt; ++t)
+    for (int k = 0; k < tm[t] && k < (int)C; ++k) {
+      te.push_back((int)t);
+      ee.push_back(ts[t * C + k]);
     }
+  if ((int)te.size() != n) return fail(h, COLLAGE_ERR_STATE, "tile lists disagree with the pair count");
   if (d_tile && n) CK(h, cudaMemcpy(d_tile, te.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   if (d_elem && n) CK(h, cudaMemcpy(d_elem, ee.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   return COLLAGE_OK;
@@ -1563,10 +1596,10 @@ extern "C" collage_status collage_get_info(collage_t h, collage_info* out) {
   out->total_pixels = h->d.total_pix;
   out->pair_capacity = h->d.cap;
   out->last_pairs = h->h_ctl ? h->h_ctl[2] : 0;
-  // transform (with the previous Adam step), tile scan, emission with signed distances,
+  // transform (with the previous Adam step and the pair slots), emission with signed distances,
   // composite, (2 dilation), raster bwd, (gradient reduce), loss
   const bool dil = h->d.L.gamma != 0.0f && h->d.L.n_dil > 0;
-  out->kernels_per_iter = 4 + (scan_rounds(h->d.total_tiles) > 1 ? 2 : 0) + (dil ? 2 : 0) + 1 +
+  out->kernels_per_iter = 3 + (dil ? 2 : 0) + 1 +
                          (h->d.deterministic ? 1 : 0) + 1 + (h->d.fit ? 1 : 0);
   unsigned long long paths[4] = {0, 0, 0, 0};
   CK(h, cudaDeviceSynchronize());

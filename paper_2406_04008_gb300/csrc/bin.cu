@@ -1,12 +1,11 @@
 // Transform (Eq. 2) and tile binning.
 //
-// Binning is a counting sort keyed on the tile: the transform kernel counts, per tile, the elements
-// whose tile rectangle covers it (integer atomics), and lists every element's kChunkPx-square
-// chunks of its rectangle; one prefix scan over the tiles turns the counts into [begin, end) ranges (and
-// zeroes the counts for the next iteration); the emission (csrc/raster.cu, per chunk) places each
-// (tile, element) pair in its tile's range; the composite then orders each tile's short list by
-// element id before using it, so every tile lists its elements in increasing order whatever the
-// order of the atomics.  The tile rectangle follows a fixed float formula
+// Binning: the transform kernel gives every element a block of consecutive pair slots, one per tile
+// of its tile rectangle (one atomic per element; a total beyond the capacity latches the overflow
+// bit before any pair is written), and lists every element's kChunkPx-square chunks of its
+// rectangle; the emission (csrc/raster.cu, per chunk) records each (tile, element) pair's slot in
+// its tile's list; the composite then orders each tile's short list by element id before using it,
+// so every tile lists its elements in increasing order whatever the order of the atomics.  The tile rectangle follows a fixed float formula
 // (bin_rect), so the bins are bit-exact against the oracle's rule.
 #include <cfloat>
 
@@ -78,7 +77,7 @@ __device__ __forceinline__ float2 vertex_px(const float2 v, const RotFF& M) {
 // One block per element: the pending Adam step of the previous iteration, then segment records
 // (start, direction, end y, 1/|e|^2) of the vertices
 // relative to the translation, translation in pixels as a float hi/lo pair, outline box grown by
-// the coverage margin, tile rectangle, and the per-tile element counts of the counting sort.
+// the coverage margin, tile rectangle, the element's pair slots and its emission chunks.
 // Lanes own consecutive vertices; a segment's end point is the next lane's start point (shuffled),
 // so each vertex is transformed once.
 constexpr int kTfThreads = 128;
@@ -86,11 +85,14 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   pdl_enter();
   __shared__ RotFF s_rot;
   __shared__ float s_box[4][kTfThreads / 32];
-  __shared__ int4 s_rect;
   const int g = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = d.elem_prob[g];
   const int res = d.prob_res[p];
+  if (g == 0 && threadIdx.x == 0) {  // this iteration's live pairs and finished gradient blocks
+    d.work[1] = 0;
+    d.work[3] = 0;
+  }
   // the previous iteration's step (when the outlines are fitted the transforms stay fixed)
   if (threadIdx.x == 0 && *d.pending && !d.fit) adam_update(d, g, *d.step, d.dq[g]);
   __syncthreads();
@@ -170,8 +172,14 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     if (finite) r = bin_rect(q, d.elem_rbin[g], hw, res, d.tile, d.L.rho_px, d.L.pad_px);
     else atomicOr(d.status, kStatusBadParam);
     d.rect[g] = r;
-    s_rect = r;
     if (zero_grad) d.dq[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the pair slots of the rectangle; beyond the capacity the bins of the iteration are void
+    if (r.z >= r.x && r.w >= r.y) {
+      const int n = (r.z - r.x + 1) * (r.w - r.y + 1);
+      const int base = atomicAdd(d.pair_need, n);
+      if (base > d.cap - n) atomicOr(d.status, kStatusOverflow);
+      d.elem_pbase[g] = base;
+    }
     // the emission's work: the rectangle in chunks of kChunkPx / T tiles a side; chunks whose
     // segments x tiles exceed kHeavyChunk are listed from the front, the others from the back, so
     // that the emission takes the costliest first and none trails at the end
@@ -182,166 +190,12 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
       const int base = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);
       // (heavy + light chunks beyond the list mean more pairs than the capacity too: the iteration
       // overflows and the list is not read; every write stays inside it)
-      if (base + nx * ny <= d.list_cap)
+      if (base + nx * ny <= d.list_cap && !(*d.status & kStatusOverflow))
         for (int c = 0; c < nx * ny; ++c) {
           const int at = heavy ? base + c : d.list_cap - 1 - (base + c);
           d.near_list[at] = make_int4(g, (r.x + (c % nx) * cw) | ((r.y + (c / nx) * cw) << 16), p, 0);
         }
     }
-  }
-  __syncthreads();
-  const int4 r = s_rect;
-  if (r.z < r.x || r.w < r.y) return;
-  const int w = r.z - r.x + 1, n = w * (r.w - r.y + 1);
-  const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
-  for (int i = threadIdx.x; i < n; i += kTfThreads) {
-    const int t = tb + (r.y + i / w) * ntx + r.x + i % w;
-    if (in_bounds(d, t >= tb && t < d.prob_tile_base[p + 1])) atomicAdd(&d.tile_cnt[t], 1);
-  }
-}
-
-// Exclusive scan of the per-tile counts into [begin, end) ranges, in rounds of 16384 tiles: each
-// thread loads 16 consecutive counts with vector loads, scans them in registers, the block scans
-// the per-thread totals, and the thread writes its 16 ranges with vector stores.  The total is the
-// pair count; above the capacity the overflow bit is latched.  Up to one round the scan is one
-// block; beyond that the rounds run as separate blocks (ranges relative to their round), one block
-// scans the round totals into offsets, and a third kernel adds each round's offset.
-constexpr int kScanThreads = 1024, kScanPer = 16, kScanRound = kScanThreads * kScanPer;
-
-// The round of counts from `base`, its ranges written from `carry`; returns the round's total.
-__device__ __forceinline__ int scan_round(const Dev& d, int base, int carry, int* wsum) {
-  const int n = d.total_tiles, t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int i0 = base + t * kScanPer;
-  const bool full = i0 + kScanPer <= n;
-  int v[kScanPer];
-  // the counts are read once and zeroed for the next iteration's transform
-  if (full) {
-    int4* src = reinterpret_cast<int4*>(d.tile_cnt + i0);
-#pragma unroll
-    for (int q = 0; q < kScanPer / 4; ++q) {
-      const int4 a = src[q];
-      v[4 * q] = a.x;
-      v[4 * q + 1] = a.y;
-      v[4 * q + 2] = a.z;
-      v[4 * q + 3] = a.w;
-    }
-#pragma unroll
-    for (int q = 0; q < kScanPer / 4; ++q) src[q] = make_int4(0, 0, 0, 0);
-  } else {
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-      v[i] = i0 + i < n ? d.tile_cnt[i0 + i] : 0;
-      if (i0 + i < n) d.tile_cnt[i0 + i] = 0;
-    }
-  }
-  int s = 0;
-#pragma unroll
-  for (int i = 0; i < kScanPer; ++i) s += v[i];
-  int x = s;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    int ws = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, ws, o);
-      if (lane >= o) ws += y;
-    }
-    wsum[lane] = ws;  // inclusive
-  }
-  __syncthreads();
-  int run = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
-  const int round_total = wsum[31];
-  unsigned st[kScanPer + 1];
-#pragma unroll
-  for (int i = 0; i < kScanPer; ++i) {
-    st[i] = (unsigned)run;
-    run += v[i];
-  }
-  st[kScanPer] = (unsigned)run;
-  if (full) {
-    uint4* dst = reinterpret_cast<uint4*>(d.range + i0);
-#pragma unroll
-    for (int q = 0; q < kScanPer / 2; ++q)
-      dst[q] = make_uint4(st[2 * q], st[2 * q + 1], st[2 * q + 1], st[2 * q + 2]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i)
-      if (i0 + i < n) d.range[i0 + i] = make_uint2(st[i], st[i + 1]);
-  }
-  __syncthreads();  // wsum is reused by the next round
-  return round_total;
-}
-
-// The pair count, the overflow bit, and the per-iteration counters cleared.
-__device__ __forceinline__ void scan_finish(const Dev& d, int total) {
-  *d.total_pairs = total;
-  if (total > d.cap) atomicOr(d.status, kStatusOverflow);
-  *d.pending = 0;  // every transform block has applied the pending Adam step
-  for (int i = 0; i < 8; ++i) d.work[i] = 0;
-  d.work[6] = d.chunk_count[0];  // the emission's work list is complete: heavy chunks from the
-  d.work[7] = d.chunk_count[1];  //   front, light ones from the back
-  d.chunk_count[0] = d.chunk_count[1] = 0;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_tile_scan(Dev d) {
-  pdl_enter();
-  __shared__ int wsum[32];
-  int carry = 0;
-  for (int base = 0; base < d.total_tiles; base += kScanRound) carry += scan_round(d, base, carry, wsum);
-  if (threadIdx.x == 0) scan_finish(d, carry);
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_rounds(Dev d) {
-  pdl_enter();
-  __shared__ int wsum[32];
-  const int total = scan_round(d, blockIdx.x * kScanRound, 0, wsum);
-  if (threadIdx.x == 0) d.scan_part[blockIdx.x] = total;
-}
-
-// One block: the round totals into exclusive offsets (in place), then the scan's finish.
-__global__ void __launch_bounds__(kScanThreads) k_scan_offsets(Dev d, int rounds) {
-  pdl_enter();
-  __shared__ int wsum[32];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  int carry = 0;
-  for (int base = 0; base < rounds; base += kScanThreads) {
-    const int v = base + t < rounds ? d.scan_part[base + t] : 0;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      int ws = wsum[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += y;
-      }
-      wsum[lane] = ws;
-    }
-    __syncthreads();
-    if (base + t < rounds) d.scan_part[base + t] = carry + x - v + (w > 0 ? wsum[w - 1] : 0);
-    carry += wsum[31];
-    __syncthreads();
-  }
-  if (t == 0) scan_finish(d, carry);
-}
-
-// Each round's ranges moved by the round's offset.
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(Dev d) {
-  pdl_enter();
-  if (blockIdx.x == 0) return;  // the first round starts at 0
-  const unsigned off = (unsigned)d.scan_part[blockIdx.x];
-  const int i0 = blockIdx.x * kScanRound + threadIdx.x * kScanPer;
-  for (int i = i0; i < i0 + kScanPer && i < d.total_tiles; ++i) {
-    const uint2 r = d.range[i];
-    d.range[i] = make_uint2(r.x + off, r.y + off);
   }
 }
 
@@ -349,15 +203,6 @@ cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad) {
   return klaunch(d.pdl, k_transform, d.n_elems, kTfThreads, 0, s, d, zero_grad ? 1 : 0);
 }
 
-cudaError_t launch_scan(const Dev& d, cudaStream_t s) {
-  const int rounds = (d.total_tiles + kScanRound - 1) / kScanRound;
-  if (rounds <= 1 || !d.scan_part) return klaunch(d.pdl, k_tile_scan, 1, kScanThreads, 0, s, d);
-  cudaError_t e = klaunch(d.pdl, k_scan_rounds, rounds, kScanThreads, 0, s, d);
-  if (e == cudaSuccess) e = klaunch(d.pdl, k_scan_offsets, 1, kScanThreads, 0, s, d, rounds);
-  if (e == cudaSuccess) e = klaunch(d.pdl, k_scan_add, rounds, kScanThreads, 0, s, d);
-  return e;
-}
 
-int scan_rounds(int total_tiles) { return (total_tiles + kScanRound - 1) / kScanRound; }
 
 }  // namespace collage

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kCtrlThreads) k_ctrl_step(Dev d, int mode) {
   __shared__ float s_r[kCtrlThreads / 32];
   __shared__ float s_w[kBernMax][4];  // the Bernstein weights of the samples, formed once
   __shared__ float2 s_dv[kStageDv];    // the element's vertex gradients, read once
-  if (mode != 2 && (*d.status & (kStatusOverflow | kStatusBadParam))) return;  // a void iteration
+  if (mode != 2 && (*d.status & kStatusVoid)) return;  // a void iteration
   const int g = blockIdx.x;
   const int c0 = d.elem_coff[g], np = d.elem_coff[g + 1] - c0;
   const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;

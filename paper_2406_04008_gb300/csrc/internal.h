@@ -23,6 +23,9 @@ constexpr int kHeavyChunk = 1024;       // segments x tiles above which a chunk 
 constexpr int kStatusOverflow = 1;      // device status bits
 constexpr int kStatusBadParam = 2;
 constexpr int kStatusInternal = 4;      // an internal bounds check failed (a bug)
+constexpr int kStatusTileCap = 8;       // a tile's pair list outgrew its capacity (regrown, re-run)
+constexpr int kStatusNoBins = kStatusOverflow | kStatusTileCap;  // the bins of the iteration are void
+constexpr int kStatusVoid = kStatusNoBins | kStatusBadParam;      // the iteration is void
 
 // Class of a (tile, element) pair.  A pair is near when some segment of the outline lies within
 // the coverage margin (rho + pad + stroke half-width) of some pixel centre of the tile; otherwise
@@ -81,11 +84,19 @@ struct Dev {
   float4* tpx;                  // [n] translation in px: (hi.x, hi.y, lo.x, lo.y)
   float4* bbox;                 // [n] outline box relative to the translation, grown by the margin
   int4* rect;                   // [n] tile rectangle (tx0, ty0, tx1, ty1), empty if tx1 < tx0
-  int* tile_cnt;                // [total_tiles] counting-sort counts (the tile scan zeroes them)
-  int* tile_fill;               // [total_tiles] slots taken by the emission (the composite zeroes them)
-  int* scan_part;               // [scan rounds] round totals, then offsets (levels above one round)
-  int* total_pairs;             // [1]
+  int* elem_pbase;              // [n] first pair slot of each element: its tile rectangle's pairs
+                                //   take consecutive slots, row-major (the transform allocates them)
+  int* pair_need;               // [1] pair slots allocated by this iteration's transform
+  int* total_pairs;             // [1] pairs of the last binning (copied from pair_need)
   int cap;                      // pair capacity
+  int* tile_n;                  // [total_tiles] pairs registered in each tile's list by the
+                                //   emission (the composite zeroes it)
+  int* tile_m;                  // [total_tiles] pairs of each tile (the composite's count, kept)
+  int* tile_list;               // [total_tiles * tile_cap] pair slots of each tile, emission order
+  int* tile_sorted;             // [total_tiles * tile_cap] each tile's elements in increasing order
+  int* tile_sorted_slot;        //   and their pair slots (written by the composite)
+  int tile_cap;                 // pair-list capacity of a tile
+  int* emit_done;               // [1] emission blocks finished (its last block resets it)
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
   int4* near_list;              // [list_cap] the emission's work list: (element, chunk origin tile
@@ -93,14 +104,11 @@ struct Dev {
                                 //   every element's tile rectangle, appended by the transform: heavy
                                 //   ones from the front, light ones from the back
   int list_cap;                 // entries near_list holds
-  int* chunk_count;             // [2] heavy and light chunks appended by the transform (the tile
-                                //   scan moves them to work[6], work[7] and zeroes them)
+  int* chunk_count;             // [2] heavy and light chunks appended by the transform (the
+                                //   emission's last block zeroes them)
   int4* live_list;              // [cap] pairs with some non-saturated pixel: (slot, element, tile
                                 //   column | row << 16, problem), the adjoint's work list (order
                                 //   depends on atomics)
-  int* pair_sorted;             // [cap] each tile's elements in increasing element order
-  int* pair_slot;               // [cap] the pair slot of each pair_sorted entry
-  uint2* range;                 // [total_tiles] [begin, end) into the pair arrays
   float2* saved;                // [cap * tile*tile] (sd px, closest segment as int bits)
   float* covc;                  // [pix] container coverage
   float* img_I;                 // [pix] Ihat = prod(1 - c)
@@ -121,12 +129,11 @@ struct Dev {
   int* step;                    // [1] Adam step count (the loss assembly advances it)
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
   int* sched_base;              // [1] Adam step count when the running schedule graph began
-  int* work;                    // [8] per-iteration counters, zeroed by the tile scan:
-                                //   [0] chunks taken by the emission's blocks, [1] entries of
-                                //   live_list, [3] blocks of the last gradient kernel that have
-                                //   finished, [5] blocks of the Adam flush that have finished
-                                //   (its last block resets it), [6] heavy chunks listed (front of
-                                //   near_list), [7] light chunks (back of near_list), [2, 4] spare
+  int* work;                    // [8] per-iteration counters: [0] chunks taken by the emission's
+                                //   blocks (its last block zeroes it), [1] entries of live_list and
+                                //   [3] blocks of the last gradient kernel that have finished
+                                //   (zeroed by the transform), [5] blocks of the Adam flush that
+                                //   have finished (its last block zeroes it), [2, 4, 6, 7] spare
   unsigned long long* paths;    // [4] cumulative counts of the rarely taken kernel paths (since
                                 //   create): [0] pixel rows of a near pair whose crossings
                                 //   overflow the per-row list (winding over every segment),
@@ -236,8 +243,7 @@ __device__ __forceinline__ void mark_step_if_last(const Dev& d) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();  // this block's gradient writes are visible before it is counted
-    if (atomicAdd(&d.work[3], 1) == (int)gridDim.x - 1 &&
-        !(atomicAdd(d.status, 0) & (kStatusOverflow | kStatusBadParam))) {
+    if (atomicAdd(&d.work[3], 1) == (int)gridDim.x - 1 && !(atomicAdd(d.status, 0) & kStatusVoid)) {
       __threadfence();
       *d.step += 1;
       *d.pending = 1;
@@ -247,8 +253,6 @@ __device__ __forceinline__ void mark_step_if_last(const Dev& d) {
 
 // ---- launchers (each enqueues on `s`, returns the launch error) ----
 cudaError_t launch_transform(const Dev& d, cudaStream_t s, bool zero_grad);
-cudaError_t launch_scan(const Dev& d, cudaStream_t s);           // tile counts -> ranges, total
-int scan_rounds(int total_tiles);                                 // rounds (blocks) of the scan
 cudaError_t launch_container(const Dev& d, cudaStream_t s);
 // part 1: pair emission, classification and per-pixel signed distances (per element chunk);
 // part 2: per-tile composite and loss partials; 3: both

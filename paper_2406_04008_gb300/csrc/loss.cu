@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
   constexpr float inv_q = 1.0f / (float)(1u << Q);
   extern __shared__ uint32_t sm[];
   __shared__ float s_red[kDThreads / 32];
-  if (*d.status & kStatusOverflow) return;
+  if (*d.status & kStatusNoBins) return;
   uint32_t* sO = sm;
   uint32_t* H = sO + S * SP;
   // the tiles with container coverage; on the others M_C (1 - O) = 0, dL_u/dO = 0 and the loss
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
   constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
   constexpr float inv_q = 1.0f / (float)(1u << Q);
   extern __shared__ uint32_t sm[];
-  if (*d.status & kStatusOverflow) return;
+  if (*d.status & kStatusNoBins) return;
   uint32_t* sM = sm;
   uint32_t* H = sM + S * SP;
   // the tiles with container coverage within the halo (G = 0 over the others and their halos)
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kReduceWarps * 32) k_grad_reduce(Dev d, int ma
   pdl_enter();
   const int lane = threadIdx.x & 31;
   const int g = blockIdx.x * kReduceWarps + (threadIdx.x >> 5);
-  if (g < d.n_elems && !(*d.status & kStatusOverflow)) {
+  if (g < d.n_elems && !(*d.status & kStatusNoBins)) {
     const int4 rc = d.rect[g];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (rc.z >= rc.x && rc.w >= rc.y) {
@@ -384,15 +384,18 @@ __global__ void __launch_bounds__(kReduceWarps * 32) k_grad_reduce(Dev d, int ma
       const int tb = d.prob_tile_base[p], ntx = d.prob_ntx[p];
       const int w = rc.z - rc.x + 1, n = w * (rc.w - rc.y + 1);
       for (int i = lane; i < n; i += 32) {
-        const uint2 rg = d.range[tb + (rc.y + i / w) * ntx + rc.x + i % w];
-        unsigned lo = rg.x, hi = rg.y;  // first entry >= g
+        const int t = tb + (rc.y + i / w) * ntx + rc.x + i % w;
+        const int* sorted = d.tile_sorted + (size_t)t * d.tile_cap;
+        const int m = d.tile_m[t];
+        int lo = 0, hi = m;  // first entry >= g
         while (lo < hi) {
-          const unsigned mid = (lo + hi) >> 1;
-          if (d.pair_sorted[mid] < g) lo = mid + 1;
+          const int mid = (lo + hi) >> 1;
+          if (sorted[mid] < g) lo = mid + 1;
           else hi = mid;
         }
-        if (lo < rg.y && d.pair_sorted[lo] == g && in_bounds(d, d.pair_slot[lo] < d.cap)) {
-          const float4 v = d.partial[d.pair_slot[lo]];
+        const int sl = lo < m ? d.tile_sorted_slot[(size_t)t * d.tile_cap + lo] : -1;
+        if (lo < m && sorted[lo] == g && in_bounds(d, sl >= 0 && sl < d.cap)) {
+          const float4 v = d.partial[sl];
           acc.x += v.x;
           acc.y += v.y;
           acc.z += v.z;

@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(kMetWarps * 32) k_metric_counts(Dev d, uint8_t
     const int lt = tile - d.prob_tile_base[p], ntx = d.prob_ntx[p], res = d.prob_res[p];
     const int tx = lt % ntx, ty = lt / ntx;
     const long long pixbase = d.prob_pix_base[p];
-    const uint2 rg = d.range[tile];
+    const int m = d.tile_m[tile];
+    const int* slots = d.tile_sorted_slot + (size_t)tile * d.tile_cap;
     unsigned c_in = 0, c_shape = 0, c_over = 0, c_out = 0;
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
@@ -43,10 +44,11 @@ __global__ void __launch_bounds__(kMetWarps * 32) k_metric_counts(Dev d, uint8_t
       if (valid) {
         const long long pix = pixbase + (long long)Y * res + X;
         int n_in = 0;
-        for (unsigned i = rg.x; i < rg.y && n_in < 2; ++i) {
-          const uint8_t cls = d.pair_cls[i];
+        for (int i = 0; i < m && n_in < 2; ++i) {
+          const int sl = slots[i];
+          const uint8_t cls = d.pair_cls[sl];
           if (cls == kPairIn) n_in += 1;
-          else if (cls == kPairNear && d.saved[(size_t)i * NP + local].x >= 0.0f) n_in += 1;
+          else if (cls == kPairNear && d.saved[(size_t)sl * NP + local].x >= 0.0f) n_in += 1;
         }
         o = d.img_I[pix] <= 0.5f;
         sh = d.covc[pix] >= 0.5f;

@@ -101,8 +101,9 @@ __device__ __noinline__ int winding_all(const Dev& d, int v0, int ns, float px, 
 // Emission and signed distances, one (element, chunk) work item per block at a time.  A chunk is a
 // square of up to kChunkPx x kChunkPx pixels of the element's tile rectangle (8 x 8 tiles of 8 px,
 // 4 x 4 of 16 px); the transform kernel lists every element's chunks.  Per chunk the block
-//  1. takes the pair slot of each of its tiles from the tile's range (a fill counter per tile,
-//     which the composite zeroes again);
+//  1. takes the pair slot of each of its tiles (the element's slots follow its tile rectangle
+//     row-major from the base the transform allocated) and records it in the tile's list (a
+//     list beyond its capacity latches a status bit: the host grows the lists and runs again);
 //  2. passes once over the element's segments, staging them in shared memory by index: a segment
 //     whose box meets a tile's pixel-centre box grown by the coverage margin m = rho + pad
 //     (+ stroke half-width) (+ 0.06 px of slack) is near that tile (a bit per segment and tile);
@@ -168,11 +169,11 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
   __shared__ int s_next[2];
   __shared__ int4 s_live[kLiveBatch];
   __shared__ int s_nlive;
-  if (*d.status & kStatusOverflow) return;  // the slots are void (the tile scan zeroed the counts)
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int n_heavy = d.work[6], n_chunks = n_heavy + d.work[7];
-  for (int i = blockIdx.x, it = 0; i < n_chunks; ++it) {
+  const int n_heavy = d.chunk_count[0], n_chunks = n_heavy + d.chunk_count[1];
+  // the slots are void when the pairs exceed the capacity (the transform latched it)
+  for (int i = (*d.status & kStatusOverflow) ? n_chunks : blockIdx.x, it = 0; i < n_chunks; ++it) {
     if (tid == 0) {
       s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
       s_nlive = 0;
@@ -196,10 +197,13 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       int slot = -1;
       const int t = tb + (ty0 + tid / ctw) * ntx + tx0 + tid % ctw;
       if (tid < nct && in_bounds(d, t >= tb && t < d.prob_tile_base[p + 1])) {
-        const unsigned u = d.range[t].x + (unsigned)atomicAdd(&d.tile_fill[t], 1);
-        if (u < (unsigned)d.cap) {
-          slot = (int)u;
+        const int u = d.elem_pbase[g] + (ty0 + tid / ctw - r.y) * (r.z - r.x + 1) + tx0 + tid % ctw - r.x;
+        if (in_bounds(d, u >= 0 && u < d.cap)) {
+          slot = u;
           d.pair_elem[slot] = g;
+          const int k = atomicAdd(&d.tile_n[t], 1);
+          if (k < d.tile_cap) d.tile_list[(size_t)t * d.tile_cap + k] = slot;
+          else atomicOr(d.status, kStatusTileCap);
         }
       }
       s_slot[tid] = slot;
@@ -419,6 +423,20 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
     __syncthreads();  // s_live, s_nlive and the shared lists are reused by the next chunk
     i = s_next[it & 1];
   }
+  // the last block to finish resets the iteration's work counters for the next one
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(d.emit_done, 1) == (int)gridDim.x - 1) {
+      *d.total_pairs = *d.pair_need;
+      *d.pair_need = 0;
+      d.chunk_count[0] = d.chunk_count[1] = 0;
+      d.work[0] = 0;
+      *d.pending = 0;  // every transform block has applied the pending Adam step
+      __threadfence();
+      *d.emit_done = 0;
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -435,7 +453,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
   constexpr int NP = T * T, PPL = NP / 32;
   __shared__ int s_slot[kCompWarps][32];
   __shared__ uint8_t s_cls[kCompWarps][32];
-  if (*d.status & kStatusOverflow) return;
+  if (*d.status & kStatusNoBins) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int* w_slot = s_slot[wid];
@@ -444,30 +462,37 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
     const long long pixbase = d.prob_pix_base[p];
-    uint2 rg = d.range[tile];
-    if (lane == 0) d.tile_fill[tile] = 0;  // the emission's slot counter, for the next iteration
-    if (!in_bounds(d, rg.x <= rg.y && rg.y <= (unsigned)d.cap)) rg = make_uint2(0u, 0u);
-    const int m = (int)(rg.y - rg.x);
+    // the tile's pairs (emission order) and, for the next iteration, an empty list
+    int m = d.tile_n[tile];
+    if (!in_bounds(d, m >= 0 && m <= d.tile_cap)) m = 0;
+    const size_t lb = (size_t)tile * d.tile_cap;
+    __syncwarp();  // the previous tile's readers of this warp's lists and of tile_n are done
+    if (lane == 0) {
+      d.tile_n[tile] = 0;
+      d.tile_m[tile] = m;
+    }
     const bool small = m <= 32;
-    __syncwarp();  // the previous tile's readers of this warp's lists are done
+    int* sorted = d.tile_sorted + lb;
+    int* sorted_slot = d.tile_sorted_slot + lb;
     if (small) {
-      const int v = lane < m ? d.pair_elem[rg.x + lane] : 0;
+      const int sl = lane < m ? d.tile_list[lb + lane] : 0;
+      const int v = lane < m ? d.pair_elem[sl] : 0;
       int r = 0;
       for (int j = 0; j < m; ++j) r += __shfl_sync(0xffffffffu, v, j) < v ? 1 : 0;
       if (lane < m) {
-        w_slot[r] = (int)rg.x + lane;
-        w_cls[r] = d.pair_cls[rg.x + lane];
-        d.pair_sorted[rg.x + r] = v;
-        d.pair_slot[rg.x + r] = (int)rg.x + lane;
+        w_slot[r] = sl;
+        w_cls[r] = d.pair_cls[sl];
+        sorted[r] = v;
+        sorted_slot[r] = sl;
       }
     } else {
       if (lane == 0 && d.paths) atomicAdd(&d.paths[2], 1ull);
       for (int i = lane; i < m; i += 32) {
-        const int vi = d.pair_elem[rg.x + i];
+        const int si = d.tile_list[lb + i], vi = d.pair_elem[si];
         int r = 0;
-        for (int j = 0; j < m; ++j) r += d.pair_elem[rg.x + j] < vi ? 1 : 0;
-        d.pair_sorted[rg.x + r] = vi;
-        d.pair_slot[rg.x + r] = (int)rg.x + i;
+        for (int j = 0; j < m; ++j) r += d.pair_elem[d.tile_list[lb + j]] < vi ? 1 : 0;
+        sorted[r] = vi;
+        sorted_slot[r] = si;
       }
     }
     __syncwarp();  // the ordered list is visible to the whole warp
@@ -485,7 +510,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
       partial[k] = false;
     }
     for (int i = 0; i < m; ++i) {
-      const int slot = small ? w_slot[i] : d.pair_slot[rg.x + i];
+      const int slot = small ? w_slot[i] : sorted_slot[i];
       const uint8_t cls = small ? w_cls[i] : d.pair_cls[slot];
       if (cls == kPairOut) continue;  // c = c^pad = 0: factors of 1
       float sd[PPL];
@@ -545,7 +570,7 @@ template <int T, bool FIT>  // FIT: also dL/d(vertex) for outline fitting (d.fit
 __global__ void __launch_bounds__(kPairWarps * 32) k_raster_bwd(Dev d, int mark) {
   pdl_enter();
   constexpr int NP = T * T, PPL = NP / 32;
-  if (*d.status & kStatusOverflow) return;
+  if (*d.status & kStatusNoBins) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   const bool use_u = d.L.gamma != 0.0f;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -18,7 +18,7 @@ __global__ void k_sched_begin(Dev d) { *d.sched_base = *d.step; }
 // iterations runs no body) and as the last kernel of each body.
 __global__ void k_sched_cond(Dev d, cudaGraphConditionalHandle cond, int target) {
   const int done = *d.step - *d.sched_base;
-  const bool ok = (*d.status & (kStatusOverflow | kStatusBadParam | kStatusInternal)) == 0;
+  const bool ok = (*d.status & (kStatusVoid | kStatusInternal)) == 0;
   cudaGraphSetConditional(cond, ok && done < target ? 1u : 0u);
 }
 
