@@ -420,6 +420,29 @@ def batch_vs_plain(steps, flush, torch):
                                                        if tuning["default_ms"] else None))}
 
 
+def batch_sharded(steps, flush, torch, world, rank, barrier, max_over_ranks):
+    """The 64-collage batch split across the ranks by whole collages (sharding.shard: greedy LPT on
+    estimated work, the same on every rank without communication, no collective on the data
+    path): each rank steps its shard in one batched, graph-captured, autotuned handle.  A step
+    advances every collage of the batch by one iteration; the time is the slowest rank's."""
+    from paper_2406_04008_gb300 import sharding
+    from paper_2406_04008_gb300 import workloads as W
+    from paper_2406_04008_gb300.collage import Collage
+    probs = [W.config_problem(4, i) for i in range(64)]
+    mine = sharding.shard(probs, world, rank)
+    col = Collage([probs[i] for i in mine], use_graphs=1, persistent=1, tile=0, n_levels=1,
+                  level_res=[1], level_iters=[50])
+    col.autotune()
+    col.step(3)
+    torch.cuda.synchronize()
+    barrier()
+    t = max_over_ranks(sum(_time_steps(col, steps, flush, torch)))
+    col.close()
+    return {"workload": "batch64 sharded by whole collages over %d rank(s) (LPT)" % world,
+            "value": steps / t, "unit": "batch iterations/s (every collage of the 64 one iteration)",
+            "collages_on_rank0": len(sharding.shard(probs, world, 0)), "scaling": "strong"}
+
+
 def outline_fitting(steps, flush, torch):
     """Outline fitting (Sec. 3, Vector Representation): closed paths of 20 cubics (the paper's N)
     fitted to seeded star silhouettes at 256^2 by Adam on their control points; one outline, and 64
@@ -638,12 +661,20 @@ def main():
     plain.close()
     plain_value = 1.0 / statistics.median(ptimes)
 
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    extra = {}
+    if not args.no_extra:
+        extra["batch64_sharded"] = batch_sharded(10, flush, torch, world, rank, barrier, max_over_ranks)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-
-    extra = {}
     if world == 1 and not args.no_extra:
         extra["batch64"] = batch_vs_plain(10, flush, torch)
         extra["open5000"] = open_packing(10, flush, torch)

@@ -370,10 +370,10 @@ static collage_status ensure_pairs(collage_t h, size_t cap) {
 }
 
 // floats of the gathered output: params, loss terms, control words
-static size_t stage_floats(const collage_s* h) { return 4 * (size_t)h->N + 5 * (size_t)h->P + 4; }
+static size_t stage_floats(const collage_s* h) { return 4 * (size_t)h->N + 5 * (size_t)h->P + kCtlWords; }
 
 static collage_status read_ctl(collage_t h, cudaStream_t s) {
-  CK(h, cudaMemcpyAsync(h->h_ctl, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(h->h_ctl, h->ctl, kCtlWords * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   h->ctl_current = true;
   return COLLAGE_OK;
@@ -671,6 +671,10 @@ static collage_status check_and_grow(collage_t h, cudaStream_t s, bool* overflow
     }
     return COLLAGE_OK;
   }
+  if (h->h_ctl[17] * 4 > h->d.tile_cap * 3) {  // the fullest tile list used more than 3/4
+    collage_status st2 = ensure_tile_lists(h, 2 * h->d.tile_cap);
+    if (st2) return st2;
+  }
   if (need * 4 > h->pair_cap * 3) return ensure_pairs(h, need + need / 2 + 256);
   return COLLAGE_OK;
 }
@@ -882,8 +886,8 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   CKC(cudaMemset(d.loss_terms, 0, sizeof(float) * 5 * h->P));
   CKC(dmalloc(h->owned, d.paths, 4));
   CKC(cudaMemset(d.paths, 0, sizeof(unsigned long long) * 4));
-  CKC(dmalloc(h->owned, h->ctl, 24));
-  CKC(cudaMemset(h->ctl, 0, sizeof(int) * 24));
+  CKC(dmalloc(h->owned, h->ctl, kCtlWords));
+  CKC(cudaMemset(h->ctl, 0, sizeof(int) * kCtlWords));
   CKC(dmalloc(h->owned, d.elem_pbase, h->N));
   d.status = h->ctl;
   d.step = h->ctl + 1;
@@ -894,8 +898,10 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.chunk_count = h->ctl + 13;  // [13], [14]
   d.pair_need = h->ctl + 15;
   d.emit_done = h->ctl + 16;
+  d.tile_max = h->ctl + 17;
   d.tile_cap = 16;  // pairs per tile list (doubled when a tile outgrows it)
-  CKC(cudaMallocHost(&h->h_ctl, 4 * sizeof(int)));
+  CKC(cudaMallocHost(&h->h_ctl, kCtlWords * sizeof(int)));
+  std::memset(h->h_ctl, 0, kCtlWords * sizeof(int));
   CKC(dmalloc(h->owned, h->d_stage, stage_floats(h)));
   CKC(cudaHostAlloc(&h->h_stage, sizeof(float) * stage_floats(h), cudaHostAllocMapped));
   if (cudaHostGetDevicePointer(&h->h_stage_dev, h->h_stage, 0) != cudaSuccess) {
@@ -1171,7 +1177,7 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
     const float* tail = h->h_stage + 4 * (size_t)h->N;
     if (h_params_out) std::memcpy(h_params_out, h->h_stage, sizeof(float4) * h->N);
     if (h_loss_out) std::memcpy(h_loss_out, tail, sizeof(float) * 5 * h->P);
-    std::memcpy(h->h_ctl, tail + 5 * h->P, 4 * sizeof(int));
+    std::memcpy(h->h_ctl, tail + 5 * h->P, kCtlWords * sizeof(int));
     h->ctl_current = true;
     return COLLAGE_OK;
   };
@@ -1179,7 +1185,7 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
   if (st) return st;
   const int status = h->h_ctl[0], done = h->h_ctl[1] - step0;
   if (!(status & (kStatusVoid | kStatusInternal)) && done == n_iters &&
-      (size_t)h->h_ctl[2] * 4 <= h->pair_cap * 3)
+      (size_t)h->h_ctl[2] * 4 <= h->pair_cap * 3 && h->h_ctl[17] * 4 <= h->d.tile_cap * 3)
     return COLLAGE_OK;
   // an overflow (or a status to report): the synchronous path regrows and runs the rest
   bool over = false;

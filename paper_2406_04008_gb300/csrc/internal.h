@@ -18,6 +18,7 @@
 namespace collage {
 
 constexpr int kMaxDil = 8;
+constexpr int kCtlWords = 24;           // device control words (status first, see Dev)
 constexpr int kChunkPx = 64;            // side, in pixels, of the emission's chunks of an element
 constexpr int kHeavyChunk = 1024;       // segments x tiles above which a chunk is taken first
 constexpr int kStatusOverflow = 1;      // device status bits
@@ -97,6 +98,8 @@ struct Dev {
   int* tile_sorted_slot;        //   and their pair slots (written by the composite)
   int tile_cap;                 // pair-list capacity of a tile
   int* emit_done;               // [1] emission blocks finished (its last block resets it)
+  int* tile_max;                // [1] pairs of the fullest tile list of the iteration (the
+                                //   composite's maximum; the emission's last block zeroes it)
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
   int4* near_list;              // [list_cap] the emission's work list: (element, chunk origin tile

@@ -430,10 +430,8 @@ __global__ void k_adam_flush(Dev d, float* out) {
     for (int i = threadIdx.x; i < 5 * d.n_probs; i += blockDim.x) tail[i] = d.loss_terms[i];
     if (threadIdx.x == 0) {
       int* c = reinterpret_cast<int*>(tail + 5 * d.n_probs);
-      c[0] = *d.status;
-      c[1] = *d.step;
-      c[2] = *d.total_pairs;
-      c[3] = 0;
+      for (int i = 0; i < kCtlWords; ++i) c[i] = d.status[i];  // the control words, in order
+      c[3] = 0;  // the pending step is applied by this flush
     }
   }
   __syncthreads();  // every thread of the block has read the flag

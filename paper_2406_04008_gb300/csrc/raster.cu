@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       *d.pair_need = 0;
       d.chunk_count[0] = d.chunk_count[1] = 0;
       d.work[0] = 0;
+      *d.tile_max = 0;
       *d.pending = 0;  // every transform block has applied the pending Adam step
       __threadfence();
       *d.emit_done = 0;
@@ -458,6 +459,10 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int* w_slot = s_slot[wid];
   uint8_t* w_cls = s_cls[wid];
+  __shared__ int s_mmax;
+  if (threadIdx.x == 0) s_mmax = 0;
+  __syncthreads();
+  int m_max = 0;  // the fullest list this warp saw (the host keeps the lists' capacity ahead of it)
   for (int tile = blockIdx.x * kCompWarps + wid; tile < d.total_tiles; tile += gridDim.x * kCompWarps) {
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
@@ -465,6 +470,7 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     // the tile's pairs (emission order) and, for the next iteration, an empty list
     int m = d.tile_n[tile];
     if (!in_bounds(d, m >= 0 && m <= d.tile_cap)) m = 0;
+    m_max = max(m_max, m);
     const size_t lb = (size_t)tile * d.tile_cap;
     __syncwarp();  // the previous tile's readers of this warp's lists and of tile_n are done
     if (lane == 0) {
@@ -559,6 +565,9 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     }
     if (lane == 0) d.lossA[tile] = make_float4(lc, lo, ld, 0.0f);
   }
+  if (lane == 0) atomicMax(&s_mmax, m_max);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_mmax > 0) atomicMax(d.tile_max, s_mmax);
 }
 
 // ------------------------------------------------------------------------------------------------
