@@ -669,6 +669,8 @@ def main():
         return float(t.item())
 
     extra = {}
+    if world == 1 and not args.no_extra:  # first: its autotuner search is the one reported
+        extra["batch64"] = batch_vs_plain(10, flush, torch)
     if not args.no_extra:
         extra["batch64_sharded"] = batch_sharded(10, flush, torch, world, rank, barrier, max_over_ranks)
     if rank != 0:
@@ -676,7 +678,6 @@ def main():
             dist.destroy_process_group()
         return
     if world == 1 and not args.no_extra:
-        extra["batch64"] = batch_vs_plain(10, flush, torch)
         extra["open5000"] = open_packing(10, flush, torch)
         extra["schedule_mixed1000"] = schedule_time(torch)
         extra["fit20"] = outline_fitting(50, flush, torch)

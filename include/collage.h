@@ -252,19 +252,22 @@ collage_status collage_stage_times(collage_t h, void* stream, int n_iters, float
 typedef struct {
   int tile;              /* raster tile side, 8 or 16 */
   int emit_threads;      /* threads per block of the emission / signed-distance kernel: 128, 256 */
+  int chunk_px;          /* side of the emission's work items (squares of an element's tile
+                            rectangle), pixels: 64 or 32 */
   float fwd_grid;        /* persistent grids of the emission, adjoint and composite kernels, as */
   float bwd_grid;        /*   multiples of (SM count x blocks resident per SM): 0.5, 1 or 2 */
   float comp_grid;
   float default_ms;      /* loss + gradient iteration time of the defaults (tile 16, 128 threads,
-                            grids x1), ms; 0 when the choice came from the cache */
+                            64-px chunks, grids x1), ms; 0 when the choice came from the cache */
   float best_ms;         /* iteration time of the chosen configuration, ms */
   int trials;            /* configurations timed */
   int from_cache;        /* 1: the choice of an earlier search with the same key was reused */
 } collage_tuning;
 
 /* The autotuner (no counterpart in the paper): at the current level, times the raster tile sizes
- * with the other parameters at their defaults, then in turn the emission block size and the
- * persistent-grid multiples of the emission, adjoint and composite kernels (each candidate a
+ * with the other parameters at their defaults, then in turn the emission block size, the
+ * emission's chunk side and the persistent-grid multiples of the emission, adjoint and composite
+ * kernels (each candidate a
  * captured one-iteration graph of loss and gradient, no Adam step, 20 timed replays), and keeps
  * the fastest.  The choice is cached for the process, keyed on (pixels of the level, element
  * count, pair density in half-octaves, deterministic mode); a handle with the same key reuses it

@@ -56,7 +56,7 @@ class collage_info(C.Structure):
 
 
 class collage_tuning(C.Structure):
-    _fields_ = [("tile", C.c_int), ("emit_threads", C.c_int), ("fwd_grid", C.c_float),
+    _fields_ = [("tile", C.c_int), ("emit_threads", C.c_int), ("chunk_px", C.c_int), ("fwd_grid", C.c_float),
                 ("bwd_grid", C.c_float), ("comp_grid", C.c_float), ("default_ms", C.c_float),
                 ("best_ms", C.c_float), ("trials", C.c_int), ("from_cache", C.c_int)]
 

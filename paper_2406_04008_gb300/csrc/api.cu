@@ -782,6 +782,7 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   for (int e = 0; e < h->N; ++e) d.max_segs = std::max(d.max_segs, h->elem_voff[e + 1] - h->elem_voff[e]);
   d.tile = h->opt.tile;
   d.emit_threads = 128;
+  d.chunk_tiles = kChunkPx / d.tile;
   d.deterministic = o.deterministic ? 1 : 0;
   d.pdl = o.overlap_launches ? 1 : 0;
   d.lr = o.lr;
@@ -1348,7 +1349,7 @@ extern "C" collage_status collage_stage_times(collage_t h, void* stream, int n_i
 // --------------------------------------------------------------------------------------------
 namespace {
 struct TuneChoice {
-  int tile, emit_threads;
+  int tile, emit_threads, chunk_px;
   float fwd, bwd, comp;
 };
 std::mutex g_tune_mu;
@@ -1369,6 +1370,7 @@ static collage_status apply_choice(collage_t h, const TuneChoice& c) {
   h->d.tile = c.tile;
   h->opt.tile = c.tile;
   h->d.emit_threads = c.emit_threads;
+  h->d.chunk_tiles = std::max(1, c.chunk_px / c.tile);
   h->fwd_mult = c.fwd;
   h->bwd_mult = c.bwd;
   h->comp_mult = c.comp;
@@ -1418,7 +1420,8 @@ static collage_status time_config(collage_t h, cudaStream_t s, int reps, float* 
 extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms) {
   if (!h) return fail(nullptr, COLLAGE_ERR_INVALID_ARG, "handle is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const TuneChoice before{h->d.tile, h->d.emit_threads, h->fwd_mult, h->bwd_mult, h->comp_mult};
+  const TuneChoice before{h->d.tile, h->d.emit_threads, h->d.chunk_tiles * h->d.tile, h->fwd_mult,
+                          h->bwd_mult, h->comp_mult};
   // the key: pixels of the level, elements, and the pair density at 8-px tiles (half-octaves)
   long long pix = 0;
   for (int p = 0; p < h->P; ++p) pix += (long long)h->res[p] * h->res[p];
@@ -1437,6 +1440,7 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
       if (st) return st;
       h->tuning.tile = it->second.tile;
       h->tuning.emit_threads = it->second.emit_threads;
+      h->tuning.chunk_px = it->second.chunk_px;
       h->tuning.fwd_grid = it->second.fwd;
       h->tuning.bwd_grid = it->second.bwd;
       h->tuning.comp_grid = it->second.comp;
@@ -1449,7 +1453,7 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   }
   const int reps = 20;
   int trials = 0;
-  TuneChoice best{16, 128, 1.0f, 1.0f, 1.0f};
+  TuneChoice best{16, 128, kChunkPx, 1.0f, 1.0f, 1.0f};
   float best_ms = 1e30f, default_ms = 0.0f;
   auto trial = [&](const TuneChoice& c, float* out) -> collage_status {
     collage_status st = apply_choice(h, c);
@@ -1461,7 +1465,7 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   // the tile first (the defaults of everything else), then each launch parameter in turn
   for (int T : {16, 8}) {
     float ms = 0.0f;
-    const TuneChoice c{T, 128, 1.0f, 1.0f, 1.0f};
+    const TuneChoice c{T, 128, kChunkPx, 1.0f, 1.0f, 1.0f};
     if ((st = trial(c, &ms))) break;
     if (T == 16) default_ms = ms;
     if (ms < best_ms) {
@@ -1470,14 +1474,15 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
     }
   }
   const float mults[3] = {0.5f, 1.0f, 2.0f};
-  for (int dim = 0; dim < 4 && !st; ++dim) {
+  for (int dim = 0; dim < 5 && !st; ++dim) {
     const TuneChoice base = best;
-    for (int k = 0; k < (dim == 0 ? 2 : 3) && !st; ++k) {
+    for (int k = 0; k < (dim <= 1 ? 2 : 3) && !st; ++k) {
       TuneChoice c = base;
       if (dim == 0) c.emit_threads = k == 0 ? 128 : 256;
-      if (dim == 1) c.fwd = mults[k];
-      if (dim == 2) c.bwd = mults[k];
-      if (dim == 3) c.comp = mults[k];
+      if (dim == 1) c.chunk_px = k == 0 ? kChunkPx : kChunkPx / 2;
+      if (dim == 2) c.fwd = mults[k];
+      if (dim == 3) c.bwd = mults[k];
+      if (dim == 4) c.comp = mults[k];
       if (std::memcmp(&c, &base, sizeof(c)) == 0) continue;
       float ms = 0.0f;
       if ((st = trial(c, &ms))) break;
@@ -1499,6 +1504,7 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   }
   h->tuning.tile = best.tile;
   h->tuning.emit_threads = best.emit_threads;
+  h->tuning.chunk_px = best.chunk_px;
   h->tuning.fwd_grid = best.fwd;
   h->tuning.bwd_grid = best.bwd;
   h->tuning.comp_grid = best.comp;
@@ -1515,6 +1521,7 @@ extern "C" collage_status collage_get_tuning(collage_t h, collage_tuning* out) {
   *out = h->tuning;
   out->tile = h->d.tile;
   out->emit_threads = h->d.emit_threads;
+  out->chunk_px = h->d.chunk_tiles * h->d.tile;
   out->fwd_grid = h->fwd_mult;
   out->bwd_grid = h->bwd_mult;
   out->comp_grid = h->comp_mult;

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     // segments x tiles exceed kHeavyChunk are listed from the front, the others from the back, so
     // that the emission takes the costliest first and none trails at the end
     if (r.z >= r.x && r.w >= r.y) {
-      const int cw = kChunkPx / d.tile, nx = (r.z - r.x) / cw + 1, ny = (r.w - r.y) / cw + 1;
+      const int cw = d.chunk_tiles, nx = (r.z - r.x) / cw + 1, ny = (r.w - r.y) / cw + 1;
       const int tiles = min(r.z - r.x + 1, cw) * min(r.w - r.y + 1, cw);
       const bool heavy = nv * tiles > kHeavyChunk;
       const int base = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);

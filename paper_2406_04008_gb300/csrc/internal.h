@@ -71,6 +71,7 @@ struct Dev {
   long long total_pix;
   int tile;                     // raster tile side
   int emit_threads;             // threads per block of the emission / distance kernel (128, 256)
+  int chunk_tiles;              // side of the emission's chunks, in tiles (<= kChunkPx / tile)
   int n_sort_passes;
   // ---- params / optimiser ----
   float4* q;

@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
     const int g = rec.x, tx0 = rec.y & 0xffff, ty0 = rec.y >> 16, p = rec.z;
     if (!in_bounds(d, g >= 0 && g < d.n_elems && p >= 0 && p < d.n_probs)) break;
     const int4 r = d.rect[g];
-    const int ctw = min(CW, r.z - tx0 + 1), cth = min(CW, r.w - ty0 + 1), nct = ctw * cth;
+    const int cs = min(d.chunk_tiles, CW);
+    const int ctw = min(cs, r.z - tx0 + 1), cth = min(cs, r.w - ty0 + 1), nct = ctw * cth;
     const int res = d.prob_res[p], ntx = d.prob_ntx[p], tb = d.prob_tile_base[p];
     const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
     const bool closed = d.elem_closed[g] != 0;

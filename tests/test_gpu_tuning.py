@@ -36,7 +36,7 @@ def test_autotune_choice_cache_and_results(Collage, oracle_mod):
     tile, best = a.autotune()
     t = a.tuning()
     assert t["tile"] == tile and tile in (8, 16)
-    assert t["emit_threads"] in (128, 256)
+    assert t["emit_threads"] in (128, 256) and t["chunk_px"] in (32, 64)
     for k in ("fwd_grid", "bwd_grid", "comp_grid"):
         assert t[k] in (0.5, 1.0, 2.0)
     assert t["from_cache"] == 0 and t["trials"] >= 8
@@ -49,7 +49,7 @@ def test_autotune_choice_cache_and_results(Collage, oracle_mod):
     b.autotune()
     tb = b.tuning()
     assert tb["from_cache"] == 1 and tb["trials"] == 0
-    for k in ("tile", "emit_threads", "fwd_grid", "bwd_grid", "comp_grid"):
+    for k in ("tile", "emit_threads", "chunk_px", "fwd_grid", "bwd_grid", "comp_grid"):
         assert tb[k] == t[k]
     tb_, gb = b.loss_backward()
     assert torch.equal(ta, tb_) and torch.equal(ga, gb)
