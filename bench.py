@@ -352,6 +352,10 @@ def cpu_per_config():
         return (time.perf_counter() - t0) / iters
 
     out = {"unit": "s/iteration", "cores": os.cpu_count()}
+    # the method work of configs 1 and 2 (pixel-segment pairs, the roofline's denominator)
+    out["pairs"] = {name: O.Scene(W.config_problem(cfg)).pair_work(
+        W.config_problem(cfg)["params0"].astype(np.float64), grid, O.options(**kw))
+        for name, cfg, grid, kw in CONFIG_LINES}
     out["disks16_128"] = per_iter(W.config_problem(1), 128, dict(gamma=0.0), 3)
     out["blobs200_star_512"] = per_iter(W.config_problem(2), 512, {})
     t0 = time.perf_counter()
@@ -441,6 +445,37 @@ def batch_sharded(steps, flush, torch, world, rank, barrier, max_over_ranks):
     return {"workload": "batch64 sharded by whole collages over %d rank(s) (LPT)" % world,
             "value": steps / t, "unit": "batch iterations/s (every collage of the 64 one iteration)",
             "collages_on_rank0": len(sharding.shard(probs, world, 0)), "scaling": "strong"}
+
+
+CONFIG_LINES = (("disks16_disk_128", 1, 128, dict(gamma=0.0)), ("blobs200_star_512", 2, 512, {}))
+
+
+def config_lines(steps, flush, torch):
+    """Configs 1 (16 disks, 128^2) and 2 (200 blobs, 512^2) of the workload list: the graph-captured,
+    persistent, autotuned path against the plain one (eager launches, one block per tile, 16-px
+    tiles), and the forward and backward raster stages' times (the forward's method work comes
+    from the CPU-baseline leg)."""
+    from paper_2406_04008_gb300 import workloads as W
+    from paper_2406_04008_gb300.collage import Collage
+    out = {}
+    for name, cfg, grid, kw in CONFIG_LINES:
+        prob = W.config_problem(cfg)
+        base = dict(n_levels=1, level_res=[grid], level_iters=[50], **kw)
+        col = Collage(prob, use_graphs=1, persistent=1, tile=0, **base)
+        col.autotune()
+        col.step(3)
+        torch.cuda.synchronize()
+        tuned = 1.0 / statistics.median(_time_steps(col, steps, flush, torch))
+        stages = col.stage_times(20)
+        col.close()
+        plain = Collage(prob, use_graphs=0, persistent=0, tile=16, **base)
+        plain.step(3)
+        torch.cuda.synchronize()
+        pl = 1.0 / statistics.median(_time_steps(plain, steps, flush, torch))
+        plain.close()
+        out[name] = {"tuned": tuned, "plain": pl, "speedup": tuned / pl, "unit": "iters/s",
+                     "raster_fwd_ms": stages["raster_fwd"], "raster_bwd_ms": stages["raster_bwd"]}
+    return out
 
 
 def outline_fitting(steps, flush, torch):
@@ -688,11 +723,17 @@ def main():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     fp32_nominal = sms * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2
     fp32_peak = _measured_fp32_peak(torch)
+    if world == 1 and not args.no_extra:
+        extra["configs_1_2"] = config_lines(50, flush, torch)
     cpu = None
     pairs = None
     if not args.no_cpu_baseline and world == 1:
         cpu, pairs = cpu_baseline()
         cpu["per_workload"] = cpu_per_config()
+        for name, line in extra.get("configs_1_2", {}).items():
+            pw = cpu["per_workload"]["pairs"][name]
+            line["pairs"] = pw
+            line["raster_fwd_frac_fp32"] = pw * FLOP_PER_PAIR / (line["raster_fwd_ms"] / 1e3) / 1e12 / fp32_peak
     roof = None
     if pairs is not None:
         t_fwd = stages["raster_fwd"] / 1e3
