@@ -279,6 +279,13 @@ typedef struct {
  * restored. */
 collage_status collage_autotune(collage_t h, void* stream, float* h_best_ms);
 collage_status collage_get_tuning(collage_t h, collage_tuning* out);
+/* Applies a launch configuration without a search (one an earlier collage_autotune chose, saved by
+ * the caller): tile, emit_threads, chunk_px and the three grid multiples must be values the
+ * autotuner searches (8/16, 128/256, 64/32, 0.5/1/2); anything else returns
+ * COLLAGE_ERR_INVALID_ARG and changes nothing.  The timing fields are ignored; collage_get_tuning
+ * then reports zeros for them.  Synchronises the device; drops captured graphs.  On failure the
+ * previous configuration is restored. */
+collage_status collage_set_tuning(collage_t h, void* stream, const collage_tuning* c);
 
 /* The even-distribution term of one res x res image, as collage_loss_backward evaluates it, and
  * its gradient with respect to the occupancy O = 1 - d_ihat, computed without allocating any

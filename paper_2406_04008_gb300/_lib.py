@@ -89,6 +89,7 @@ SIGNATURES = {
     "collage_stage_times": (C.c_int, [_vp, _vp, C.c_int, _fp]),
     "collage_autotune": (C.c_int, [_vp, _vp, _fp]),
     "collage_get_tuning": (C.c_int, [_vp, C.POINTER(collage_tuning)]),
+    "collage_set_tuning": (C.c_int, [_vp, _vp, C.POINTER(collage_tuning)]),
     "collage_uniform_term_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, _fp, _vp, _vp, _vp, _vp]),
     "collage_get_info": (C.c_int, [_vp, C.POINTER(collage_info)]),
     "collage_sync": (C.c_int, [_vp, _vp]),

@@ -176,6 +176,13 @@ class Collage:
         self._check(self.lib.collage_get_tuning(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in L.collage_tuning._fields_}
 
+    def set_tuning(self, **choice):
+        """Applies a launch configuration (the keys of tuning(); missing ones keep their values)."""
+        cur = self.tuning()
+        cur.update(choice)
+        t = L.collage_tuning(**{f: cur[f] for f, _ in L.collage_tuning._fields_})
+        self._check(self.lib.collage_set_tuning(self.h, _stream(), C.byref(t)))
+
     def metrics(self):
         """[n_probs, 8]: object-in-shape, shape, overlap, object-outside-shape pixel counts, then
         LC, OO, EA and L-nU (Sec. 6 and Sec. 6.1) at the current params."""

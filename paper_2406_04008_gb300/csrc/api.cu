@@ -559,10 +559,16 @@ static collage_status setup_level(collage_t h, int level) {
 // One iteration: transform -> bin -> raster fwd (+ losses) -> dilation -> adjoint -> loss -> Adam
 // --------------------------------------------------------------------------------------------
 // A named NVTX range around each kernel launch of an iteration (the checked build only; the
-// ranges show in profilers that record NVTX, e.g. ncu --nvtx).
+// ranges show in profilers that record NVTX, e.g. ncu --nvtx).  With COLLAGE_TRACE=1 in the
+// environment the checked build also names each launch on stderr before it is made (with
+// CUDA_LAUNCH_BLOCKING=1 the last name printed is the kernel that did not return).
 struct LaunchRange {
 #ifdef COLLAGE_CHECKED
-  explicit LaunchRange(const char* name) { nvtxRangePushA(name); }
+  explicit LaunchRange(const char* name) {
+    static const bool trace = getenv("COLLAGE_TRACE") && getenv("COLLAGE_TRACE")[0] == '1';
+    if (trace) fprintf(stderr, "collage launch %s\n", name);
+    nvtxRangePushA(name);
+  }
   ~LaunchRange() { nvtxRangePop(); }
 #else
   explicit LaunchRange(const char*) {}
@@ -1530,6 +1536,27 @@ extern "C" collage_status collage_get_tuning(collage_t h, collage_tuning* out) {
   out->fwd_grid = h->fwd_mult;
   out->bwd_grid = h->bwd_mult;
   out->comp_grid = h->comp_mult;
+  return COLLAGE_OK;
+}
+
+extern "C" collage_status collage_set_tuning(collage_t h, void* stream, const collage_tuning* c) {
+  (void)stream;
+  if (!h || !c) return fail(h, COLLAGE_ERR_INVALID_ARG, "NULL argument");
+  auto grid_ok = [](float m) { return m == 0.5f || m == 1.0f || m == 2.0f; };
+  if ((c->tile != 8 && c->tile != 16) || (c->emit_threads != 128 && c->emit_threads != 256) ||
+      (c->chunk_px != kChunkPx && c->chunk_px != kChunkPx / 2) || !grid_ok(c->fwd_grid) ||
+      !grid_ok(c->bwd_grid) || !grid_ok(c->comp_grid))
+    return fail(h, COLLAGE_ERR_INVALID_ARG, "tuning outside the searched values");
+  CK(h, cudaDeviceSynchronize());
+  const TuneChoice before{h->d.tile, h->d.emit_threads, h->d.chunk_tiles * h->d.tile, h->fwd_mult,
+                          h->bwd_mult, h->comp_mult};
+  const TuneChoice want{c->tile, c->emit_threads, c->chunk_px, c->fwd_grid, c->bwd_grid, c->comp_grid};
+  collage_status st = apply_choice(h, want);
+  if (st) {
+    apply_choice(h, before);
+    return st;
+  }
+  h->tuning = collage_tuning{};
   return COLLAGE_OK;
 }
 

@@ -13,6 +13,7 @@
 //   per tile:              counting-sort count, [begin, end) into the pairs, loss partials
 #pragma once
 #include <cstdint>
+#include <cstdio>
 #include <cuda_runtime.h>
 
 namespace collage {
@@ -163,18 +164,25 @@ struct Dev {
 // ---- the checked build (-DCOLLAGE_CHECKED, libcollage_checked.so) ----
 // in_bounds(d, ok): a failed index check latches kStatusInternal (the next host call that reads
 // the status word returns COLLAGE_ERR_STATE) and the caller skips the guarded access, so nothing
-// is read or written past a bound and nothing traps.  In the regular build it is the constant
-// true and compiles away.
-__device__ __forceinline__ bool in_bounds(const Dev& d, bool ok) {
+// is read or written past a bound and nothing traps; the checked build also prints the first
+// failures' source lines.  In the regular build it is the constant true and compiles away.
 #ifdef COLLAGE_CHECKED
-  if (!ok) atomicOr(d.status, kStatusInternal);
+static __device__ int g_bounds_reports = 0;
+__device__ __forceinline__ bool in_bounds_at(const Dev& d, bool ok, int line, const char* file) {
+  if (!ok) {
+    atomicOr(d.status, kStatusInternal);
+    if (atomicAdd(&g_bounds_reports, 1) < 8) printf("collage: bounds check failed at %s:%d\n", file, line);
+  }
   return ok;
+}
+#define in_bounds(d, ok) in_bounds_at((d), (ok), __LINE__, __FILE__)
 #else
+__device__ __forceinline__ bool in_bounds(const Dev& d, bool ok) {
   (void)d;
   (void)ok;
   return true;
-#endif
 }
+#endif
 
 // Adam (bias-corrected, the update torch.optim.Adam performs; it stands in for the plain descent
 // step of Eq. 4) of element g at step t >= 1 with gradient gr, then the clamp of s.

@@ -116,4 +116,6 @@ def test_null_arguments(lib):
     assert L.collage_create(None, 1, None, C.byref(h)) == -1
     assert L.collage_step(None, None, 1) == -1
     assert L.collage_set_level(None, 0) == -1
+    assert L.collage_set_tuning(None, None, None) == -1
+    assert L.collage_get_tuning(None, None) == -1
     L.collage_destroy(None)  # no-op

@@ -65,3 +65,36 @@ def test_autotune_choice_cache_and_results(Collage, oracle_mod):
     U.check_grad(ga.cpu().numpy(), ref["grad_a"])
     for h in (a, b, c):
         h.close()
+
+
+def test_set_tuning_applies_a_saved_choice(Collage):
+    # in deterministic mode the launch parameters change no result at a given tile (the tile sets
+    # the order of the per-tile loss sums); values outside the search are refused and leave the
+    # handle as it was
+    prob = W.config_problem(2, collage_index=4, n_elems=60, grid=256)
+    kw = _kw()
+    kw["level_res"] = [256]
+    ref = {}
+    for T in (8, 16):
+        h = Collage(prob, tile=T, **kw)
+        ref[T] = h.loss_backward()
+        h.close()
+    a = Collage(prob, tile=16, **kw)
+    for choice in (dict(tile=8, emit_threads=256, chunk_px=32, fwd_grid=0.5, bwd_grid=2.0, comp_grid=2.0),
+                   dict(tile=16, emit_threads=256, chunk_px=64, fwd_grid=2.0, bwd_grid=0.5, comp_grid=0.5),
+                   dict(tile=8, emit_threads=128, chunk_px=64, fwd_grid=1.0, bwd_grid=1.0, comp_grid=1.0),
+                   dict(tile=16, emit_threads=128, chunk_px=32, fwd_grid=0.5, bwd_grid=1.0, comp_grid=2.0)):
+        a.set_tuning(**choice)
+        t = a.tuning()
+        for k, v in choice.items():
+            assert t[k] == v, (k, t[k], v)
+        assert t["best_ms"] == 0 and t["trials"] == 0
+        tc, gc = a.loss_backward()
+        t0, g0 = ref[choice["tile"]]
+        assert torch.equal(t0, tc) and torch.equal(g0, gc), choice
+    before = a.tuning()
+    for bad in (dict(tile=12), dict(emit_threads=192), dict(chunk_px=48), dict(fwd_grid=3.0)):
+        with pytest.raises(Exception):
+            a.set_tuning(**bad)
+        assert a.tuning() == before
+    a.close()
