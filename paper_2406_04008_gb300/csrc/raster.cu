@@ -160,11 +160,9 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
   __shared__ unsigned s_mask[NCT][MW];  // bit j of tile k: segment j is near tile k
   __shared__ int s_slot[NCT];           // pair slot of each tile (-1: void)
   __shared__ unsigned char s_tn[NCT];   // some segment is near the tile
-  __shared__ unsigned char s_ntile[NCT];
-  __shared__ int s_back[ROWS];
-  __shared__ int s_rc[ROWS];
-  __shared__ float s_rx[ROWS][kRowCross];
-  __shared__ signed char s_rd[ROWS][kRowCross];
+  __shared__ int2 s_ntile[NCT];         // the near tiles: (pair slot, tile | column << 8 | row << 16)
+  __shared__ int2 s_row[ROWS];          // per pixel row: (crossings right of every pixel, listed)
+  __shared__ float2 s_rx[ROWS][kRowCross];  // listed crossings: (x, +1 upward / -1 downward)
   __shared__ int s_nt, s_take;
   __shared__ int s_next[2];
   __shared__ int4 s_live[kLiveBatch];
@@ -211,10 +209,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       s_tn[tid] = 0;
     }
     for (int q = tid; q < nct * mw; q += NT) s_mask[q / mw][q % mw] = 0u;
-    for (int q = tid; q < ROWS; q += NT) {
-      s_back[q] = 0;
-      s_rc[q] = 0;
-    }
+    for (int q = tid; q < ROWS; q += NT) s_row[q] = make_int2(0, 0);
     const float4 tp = d.tpx[g], bb = d.bbox[g];
     const float hwpx = closed ? 0.0f : d.elem_hw[g] * (float)res;
     const float mrg = d.L.rho_px + pad + hwpx, mrg2 = mrg * mrg;
@@ -257,13 +252,10 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
           const float xc = fmaf(yr - sa.y, slope, sa.x);
           const int dir = a_le ? 1 : -1;
           if (xc > max_dx) {
-            atomicAdd(&s_back[q], dir);  // right of every pixel of the row
+            atomicAdd(&s_row[q].x, dir);  // right of every pixel of the row
           } else if (xc > min_dx) {
-            const int k = atomicAdd(&s_rc[q], 1);
-            if (k < kRowCross) {
-              s_rx[q][k] = xc;
-              s_rd[q][k] = (signed char)dir;
-            }
+            const int k = atomicAdd(&s_row[q].y, 1);
+            if (k < kRowCross) s_rx[q][k] = make_float2(xc, (float)dir);
           }
         }
       }
@@ -278,11 +270,14 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         if (closed) {
           const int q = (tid / ctw) * T;
           const float dx0 = ((float)(X0 + (tid % ctw) * T) + 0.5f - tp.x) - tp.z;
-          const int rc = s_rc[q];
-          if (rc <= kRowCross) {
-            w = s_back[q];
-            for (int k = 0; k < rc; ++k)
-              if (dx0 < s_rx[q][k]) w += s_rd[q][k];
+          const int2 row = s_row[q];
+          if (row.y <= kRowCross) {
+            float wf = (float)row.x;
+            for (int k = 0; k < row.y; ++k) {
+              const float2 c = s_rx[q][k];
+              if (dx0 < c.x) wf += c.y;
+            }
+            w = (int)wf;
           } else {
             w = winding_all(d, v0, ns, dx0, ((float)(Y0 + q) + 0.5f - tp.y) - tp.w);
           }
@@ -298,22 +293,23 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         const int k = k0 + lane;
         const bool nr = k < nct && s_slot[k] >= 0 && s_tn[k];
         const unsigned bal = __ballot_sync(0xffffffffu, nr);
-        if (nr) s_ntile[n + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)k;
+        if (nr) s_ntile[n + __popc(bal & ((1u << lane) - 1u))] = make_int2(s_slot[k], k | (k % ctw) << 8 | (k / ctw) << 16);
         n += __popc(bal);
       }
       if (lane == 0) s_nt = n;
     }
     __syncthreads();
     const int nt = s_nt;
-    // 4. the near tiles, one per warp at a time
-    for (;;) {
-      int ni = 0;
-      if (lane == 0) ni = atomicAdd(&s_take, 1);
-      ni = __shfl_sync(0xffffffffu, ni, 0);
-      if (ni >= nt) break;
-      const int k = s_ntile[ni];
-      const int slot = s_slot[k];
-      const int tcx = tx0 + k % ctw, tcy = ty0 + k / ctw;
+    // 4. the near tiles, one per warp at a time (the next one taken while this one is worked on)
+    int ni = 0;
+    if (lane == 0) ni = atomicAdd(&s_take, 1);
+    ni = __shfl_sync(0xffffffffu, ni, 0);
+    while (ni < nt) {
+      int nn = 0;
+      if (lane == 0) nn = atomicAdd(&s_take, 1);
+      const int2 nti = s_ntile[ni];
+      const int slot = nti.x, k = nti.y & 0xff, kr = nti.y >> 16;
+      const int tcx = tx0 + ((nti.y >> 8) & 0xff), tcy = ty0 + kr;
       float dx[PPL], dy[PPL], best[PPL];
       int bidx[PPL];
 #pragma unroll
@@ -376,11 +372,15 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         if (act) {
           int w = 0;
           if (closed) {
-            const int q = Y - Y0, rc = s_rc[q];
-            if (rc <= kRowCross) {
-              w = s_back[q];
-              for (int c = 0; c < rc; ++c)
-                if (dx[e] < s_rx[q][c]) w += s_rd[q][c];
+            const int q = Y - Y0;
+            const int2 row = s_row[q];
+            if (row.y <= kRowCross) {
+              float wf = (float)row.x;
+              for (int c = 0; c < row.y; ++c) {
+                const float2 cr = s_rx[q][c];
+                if (dx[e] < cr.x) wf += cr.y;
+              }
+              w = (int)wf;
             } else {
               w = winding_all(d, v0, ns, dx[e], dy[e]);
             }
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
         }
         sv[local] = make_float2(sd, __int_as_float(bidx[e]));
       }
-      if (d.paths && closed && lane < T && s_rc[(k / ctw) * T + lane] > kRowCross)
+      if (d.paths && closed && lane < T && s_row[kr * T + lane].y > kRowCross)
         atomicAdd(&d.paths[0], 1ull);
       if (__any_sync(0xffffffffu, live)) {
         if (lane == 0) {
@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
       } else if (lane == 0 && d.deterministic) {
         d.partial[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      ni = __shfl_sync(0xffffffffu, nn, 0);
     }
     __syncthreads();
     // the chunk's live pairs go out with one atomic
