@@ -155,7 +155,7 @@ __device__ __forceinline__ int dil_tile(const Dev& d, int which, int i) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
+__global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
   pdl_enter();
   constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
   constexpr float inv_q = 1.0f / (float)(1u << Q);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
       sO[(idx / S) * SP + idx % S] =
@@ -187,6 +187,15 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
     float lu = 0.0f;
     for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
       const int c = it % kDT, r0 = (it / kDT) * kVRows;
+      // the item's per-pixel inputs, read (from a clamped address, used only inside the image)
+      // before its box sums are formed, so that the loads are in flight meanwhile
+      float Iv[kVRows], Mv[kVRows];
+#pragma unroll
+      for (int i = 0; i < kVRows; ++i) {
+        const long long pix = pb + (long long)min(y0 + r0 + i, res - 1) * res + min(x0 + c, res - 1);
+        Iv[i] = d.img_I[pix];
+        Mv[i] = d.covc[pix];
+      }
       uint32_t B[K][kVRows];
       vsums_col<K>(H, c, r0, B);
 #pragma unroll
@@ -194,8 +203,8 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_fwd(Dev d) {
         const int X = x0 + c, Y = y0 + r0 + i;
         if (X >= res || Y >= res) continue;
         const long long pix = pb + (long long)Y * res + X;
-        const float O = 1.0f - d.img_I[pix];
-        const float M = d.covc[pix];
+        const float O = 1.0f - Iv[i];
+        const float M = Mv[i];
         const float mval = M * (1.0f - O);
         float gdir = 0.0f;
         unsigned mask = 0u;
@@ -245,7 +254,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
       const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
       const bool in = X >= 0 && Y >= 0 && X < res && Y < res;
@@ -258,6 +267,11 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
     __syncthreads();
     for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
       const int c = it % kDT, r0 = (it / kDT) * kVRows;
+      // the forward pass's direct part of dL_u/dO, read before the box sums are formed
+      float gv[kVRows];
+#pragma unroll
+      for (int i = 0; i < kVRows; ++i)
+        gv[i] = own ? d.gOu[pb + (long long)min(y0 + r0 + i, res - 1) * res + min(x0 + c, res - 1)] : 0.0f;
       uint32_t B[K][kVRows];
       vsums_col<K>(H, c, r0, B);
 #pragma unroll
@@ -267,8 +281,7 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
         float acc = 0.0f;
 #pragma unroll
         for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * ((float)B[k][i] * inv_q);
-        float* g = d.gOu + pb + (long long)Y * res + X;
-        *g = own ? *g + acc : acc;
+        d.gOu[pb + (long long)Y * res + X] = gv[i] + acc;
       }
     }
   }
