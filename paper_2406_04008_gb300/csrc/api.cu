@@ -72,8 +72,8 @@ struct collage_s {
   size_t pix_cap = 0, tile_cap = 0, dtile_cap = 0, pair_cap = 0, saved_tile = 0;
   std::vector<void*> list_bufs;  // per-tile pair lists: tile_cap tiles x d.tile_cap entries
   int* ctl = nullptr;        // device: status, step, total_pairs, pending, 8 work counters,
-                             //   schedule base step, 2 chunk counts, pairs allocated, emission
-                             //   blocks finished, 7 spare
+                             //   schedule base step, 2 chunk counts, pairs allocated, 1 spare,
+                             //   fullest tile list, 6 spare
   int* h_ctl = nullptr;      // pinned mirror
   float* d_stage = nullptr;  // device: params, loss terms and control words gathered for one copy
   float* h_stage = nullptr;  // pinned: their host copy ([4n | 5 n_probs | 4], see k_adam_flush)
@@ -904,7 +904,6 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
   d.sched_base = h->ctl + 12;
   d.chunk_count = h->ctl + 13;  // [13], [14]
   d.pair_need = h->ctl + 15;
-  d.emit_done = h->ctl + 16;
   d.tile_max = h->ctl + 17;
   d.tile_cap = 16;  // pairs per tile list (doubled when a tile outgrows it)
   CKC(cudaMallocHost(&h->h_ctl, kCtlWords * sizeof(int)));

@@ -99,9 +99,8 @@ struct Dev {
   int* tile_sorted;             // [total_tiles * tile_cap] each tile's elements in increasing order
   int* tile_sorted_slot;        //   and their pair slots (written by the composite)
   int tile_cap;                 // pair-list capacity of a tile
-  int* emit_done;               // [1] emission blocks finished (its last block resets it)
   int* tile_max;                // [1] pairs of the fullest tile list of the iteration (the
-                                //   composite's maximum; the emission's last block zeroes it)
+                                //   composite's maximum; the emission's block 0 zeroes it)
   int* pair_elem;               // [cap] element of each pair slot (tile ranges, emission order)
   uint8_t* pair_cls;            // [cap] kPairOut / kPairIn / kPairNear, set by the emission
   int4* near_list;              // [list_cap] the emission's work list: (element, chunk origin tile
@@ -110,7 +109,7 @@ struct Dev {
                                 //   ones from the front, light ones from the back
   int list_cap;                 // entries near_list holds
   int* chunk_count;             // [2] heavy and light chunks appended by the transform (the
-                                //   emission's last block zeroes them)
+                                //   composite's block 0 zeroes them)
   int4* live_list;              // [cap] pairs with some non-saturated pixel: (slot, element, tile
                                 //   column | row << 16, problem), the adjoint's work list (order
                                 //   depends on atomics)
@@ -135,7 +134,7 @@ struct Dev {
   int* pending;                 // [1] 1: the Adam step `step` is computed (dq) but not yet applied
   int* sched_base;              // [1] Adam step count when the running schedule graph began
   int* work;                    // [8] per-iteration counters: [0] chunks taken by the emission's
-                                //   blocks (its last block zeroes it), [1] entries of live_list and
+                                //   blocks beyond the first (the composite's block 0 zeroes it), [1] entries of live_list and
                                 //   [3] blocks of the last gradient kernel that have finished
                                 //   (zeroed by the transform), [5] blocks of the Adam flush that
                                 //   have finished (its last block zeroes it), [2, 4, 6, 7] spare

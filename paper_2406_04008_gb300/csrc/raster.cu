@@ -170,10 +170,19 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px;
   const int tid = threadIdx.x, lane = tid & 31;
   const int n_heavy = d.chunk_count[0], n_chunks = n_heavy + d.chunk_count[1];
+  if (blockIdx.x == 0 && tid == 0) {
+    // the transform has completed: its slot count becomes the iteration's pair count, its
+    // pending-step flag is spent, and the composite's fullest-tile maximum starts over
+    *d.total_pairs = *d.pair_need;
+    *d.pair_need = 0;
+    *d.tile_max = 0;
+    *d.pending = 0;
+  }
   // the slots are void when the pairs exceed the capacity (the transform latched it)
   for (int i = (*d.status & kStatusOverflow) ? n_chunks : blockIdx.x, it = 0; i < n_chunks; ++it) {
     if (tid == 0) {
-      s_next[it & 1] = (int)gridDim.x + atomicAdd(&d.work[0], 1);
+      // chunks beyond the grid are taken by an atomic count (none when the grid covers them all)
+      s_next[it & 1] = n_chunks > (int)gridDim.x ? (int)gridDim.x + atomicAdd(&d.work[0], 1) : n_chunks;
       s_nlive = 0;
       s_take = 0;
     }
@@ -425,21 +434,6 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
     __syncthreads();  // s_live, s_nlive and the shared lists are reused by the next chunk
     i = s_next[it & 1];
   }
-  // the last block to finish resets the iteration's work counters for the next one
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(d.emit_done, 1) == (int)gridDim.x - 1) {
-      *d.total_pairs = *d.pair_need;
-      *d.pair_need = 0;
-      d.chunk_count[0] = d.chunk_count[1] = 0;
-      d.work[0] = 0;
-      *d.tile_max = 0;
-      *d.pending = 0;  // every transform block has applied the pending Adam step
-      __threadfence();
-      *d.emit_done = 0;
-    }
-  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -456,6 +450,10 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
   constexpr int NP = T * T, PPL = NP / 32;
   __shared__ int s_slot[kCompWarps][32];
   __shared__ uint8_t s_cls[kCompWarps][32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the emission has completed: its work list is spent
+    d.chunk_count[0] = d.chunk_count[1] = 0;
+    d.work[0] = 0;
+  }
   if (*d.status & kStatusNoBins) return;
   const float inv_rho = 1.0f / d.L.rho_px, pad = d.L.pad_px, tau = d.L.tau;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
