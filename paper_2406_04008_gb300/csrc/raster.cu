@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
 // tile by a fixed shuffle tree.  No block-wide barrier: each warp owns its tile.
 // ------------------------------------------------------------------------------------------------
 constexpr int kCompWarps = 4;
+constexpr int kCompGroup = 4;  // pairs whose records are read together
 template <int T>
 __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out_bw, float* out_tau) {
   pdl_enter();
@@ -467,11 +468,22 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     int p, tx, ty, res;
     tile_coords(d, tile, T, p, tx, ty, res);
     const long long pixbase = d.prob_pix_base[p];
-    // the tile's pairs (emission order) and, for the next iteration, an empty list
+    // the tile's pairs (emission order) and, for the next iteration, an empty list; the count and
+    // the first list entries are read together (an entry is used only below the count, and the
+    // slot it names is clamped into the buffer before its element and class are read)
+    const size_t lb = (size_t)tile * d.tile_cap;
     int m = d.tile_n[tile];
+    const int sl0 = lane < d.tile_cap ? d.tile_list[lb + lane] : 0;
+    // the container coverage of the lane's pixels (independent of the pairs)
+    float cov[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int local = lane + 32 * k;
+      const int X = min(tx * T + local % T, res - 1), Y = min(ty * T + local / T, res - 1);
+      cov[k] = d.covc[pixbase + (long long)Y * res + X];
+    }
     if (!in_bounds(d, m >= 0 && m <= d.tile_cap)) m = 0;
     m_max = max(m_max, m);
-    const size_t lb = (size_t)tile * d.tile_cap;
     __syncwarp();  // the previous tile's readers of this warp's lists and of tile_n are done
     if (lane == 0) {
       d.tile_n[tile] = 0;
@@ -481,13 +493,15 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
     int* sorted = d.tile_sorted + lb;
     int* sorted_slot = d.tile_sorted_slot + lb;
     if (small) {
-      const int sl = lane < m ? d.tile_list[lb + lane] : 0;
-      const int v = lane < m ? d.pair_elem[sl] : 0;
+      const int sl = (unsigned)sl0 < (unsigned)d.cap ? sl0 : 0;
+      const int v0 = d.pair_elem[sl];
+      const uint8_t c0 = d.pair_cls[sl];
+      const int v = lane < m ? v0 : 0;
       int r = 0;
       for (int j = 0; j < m; ++j) r += __shfl_sync(0xffffffffu, v, j) < v ? 1 : 0;
       if (lane < m) {
         w_slot[r] = sl;
-        w_cls[r] = d.pair_cls[sl];
+        w_cls[r] = c0;
         sorted[r] = v;
         sorted_slot[r] = sl;
       }
@@ -515,23 +529,35 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
       nfull[k] = 0;
       partial[k] = false;
     }
-    for (int i = 0; i < m; ++i) {
-      const int slot = small ? w_slot[i] : sorted_slot[i];
-      const uint8_t cls = small ? w_cls[i] : d.pair_cls[slot];
-      if (cls == kPairOut) continue;  // c = c^pad = 0: factors of 1
-      float sd[PPL];
+    // in groups of kCompGroup pairs whose signed distances are read before any is used
+    for (int i0 = 0; i0 < m; i0 += kCompGroup) {
+      float sd[kCompGroup][PPL];
+      uint8_t cls[kCompGroup];
 #pragma unroll
-      for (int k = 0; k < PPL; ++k)  // an inside pair has c = c^pad = 1: sd = +1e30 gives that
-        sd[k] = cls == kPairIn ? kFar : d.saved[(size_t)slot * NP + lane + 32 * k].x;
+      for (int u = 0; u < kCompGroup; ++u) {
+        const int i = i0 + u;
+        cls[u] = kPairOut;
+        if (i < m) {
+          const int slot = small ? w_slot[i] : sorted_slot[i];
+          cls[u] = small ? w_cls[i] : d.pair_cls[slot];
 #pragma unroll
-      for (int k = 0; k < PPL; ++k) {
-        const float x = sd[k] * inv_rho;
-        const float omc = Sfun(-x), cp = Sfun((sd[k] + pad) * inv_rho);
-        if (omc == 0.0f) zc[k] += 1;
-        else keep[k] *= omc;
-        keept[k] *= 1.0f - tau * cp;
-        nfull[k] += cp == 1.0f;
-        partial[k] |= cp > 0.0f && cp < 1.0f;
+          for (int k = 0; k < PPL; ++k)  // an inside pair has c = c^pad = 1: sd = +1e30 gives that
+            sd[u][k] = cls[u] == kPairNear ? d.saved[(size_t)slot * NP + lane + 32 * k].x : kFar;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kCompGroup; ++u) {
+        if (cls[u] == kPairOut) continue;  // c = c^pad = 0: factors of 1
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+          const float x = sd[u][k] * inv_rho;
+          const float omc = Sfun(-x), cp = Sfun((sd[u][k] + pad) * inv_rho);
+          if (omc == 0.0f) zc[k] += 1;
+          else keep[k] *= omc;
+          keept[k] *= 1.0f - tau * cp;
+          nfull[k] += cp == 1.0f;
+          partial[k] |= cp > 0.0f && cp < 1.0f;
+        }
       }
     }
     float lc = 0.0f, lo = 0.0f, ld = 0.0f;
@@ -542,9 +568,8 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
       if (X >= res || Y >= res) continue;
       const long long pix = pixbase + (long long)Y * res + X;
       const float ihat = zc[k] ? 0.0f : keep[k];
-      const float cov = d.covc[pix];
-      const float W = cov >= 0.5f ? d.L.w_in : d.L.w_out;
-      const float df = ihat - (1.0f - cov);
+      const float W = cov[k] >= 0.5f ? d.L.w_in : d.L.w_out;
+      const float df = ihat - (1.0f - cov[k]);
       lc += W * df * df;
       const float A = 1.0f - keept[k];
       // the kink of max(0, A - tau): one fully covering element gives A = tau exactly and any
