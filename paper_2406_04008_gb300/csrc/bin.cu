@@ -75,16 +75,21 @@ __device__ __forceinline__ float2 vertex_px(const float2 v, const RotFF& M) {
 }
 
 // One block per element: the pending Adam step of the previous iteration, then segment records
-// (start, direction, end y, 1/|e|^2) of the vertices
-// relative to the translation, translation in pixels as a float hi/lo pair, outline box grown by
-// the coverage margin, tile rectangle, the element's pair slots and its emission chunks.
-// Lanes own consecutive vertices; a segment's end point is the next lane's start point (shuffled),
-// so each vertex is transformed once.
+// (start, direction, end y, 1/|e|^2) of the vertices relative to the translation, translation in
+// pixels as a float hi/lo pair, outline box grown by the coverage margin, tile rectangle, the
+// element's pair slots and its emission chunks.
+// Threads 0..3 each take the step in registers (the same arithmetic), write back one parameter and
+// form one entry of the rotation-scale matrix, so one barrier separates the step from the vertices.
+// Warps 0..2 then transform the vertices (lanes own consecutive vertices; a segment's end point is
+// the next lane's start point, shuffled, so each vertex is transformed once) while warp 3 files the
+// tile rectangle, the pair slots and the chunk list, which do not depend on the vertices.
 constexpr int kTfThreads = 128;
+constexpr int kTfVertexWarps = 3;
 __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) {
   pdl_enter();
   __shared__ RotFF s_rot;
-  __shared__ float s_box[4][kTfThreads / 32];
+  __shared__ float4 s_q;
+  __shared__ float s_box[4][kTfVertexWarps];
   const int g = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = d.elem_prob[g];
@@ -93,25 +98,74 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     d.work[1] = 0;
     d.work[3] = 0;
   }
-  // the previous iteration's step (when the outlines are fitted the transforms stay fixed)
-  if (threadIdx.x == 0 && *d.pending && !d.fit) adam_update(d, g, *d.step, d.dq[g]);
-  __syncthreads();
-  const float4 q = d.q[g];
   if (threadIdx.x < 4) {
+    const int k = threadIdx.x;
+    float4 q = d.q[g];
+    // the previous iteration's step (when the outlines are fitted the transforms stay fixed)
+    if (*d.pending && !d.fit) {
+      float4 m = d.m[g], v = d.v[g];
+      const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
+      adam_apply(d, *d.step, d.dq[g], tr, q, m, v);
+      __syncwarp(0xfu);  // every reader of the old params is done
+      auto pick = [k](float4 x) { return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w; };
+      reinterpret_cast<float*>(d.q + g)[k] = pick(q);
+      reinterpret_cast<float*>(d.m + g)[k] = pick(m);
+      reinterpret_cast<float*>(d.v + g)[k] = pick(v);
+    }
+    if (k == 0) s_q = q;
     double sn, c;
     sincos((double)q.z, &sn, &c);
     const double sc = (double)q.w * (double)res;
-    const double m = threadIdx.x == 0 ? sc * c : threadIdx.x == 1 ? -sc * sn : threadIdx.x == 2 ? sc * sn : sc * c;
+    const double m = k == 0 ? sc * c : k == 1 ? -sc * sn : k == 2 ? sc * sn : sc * c;
     const float hi = (float)m;
-    s_rot.m[threadIdx.x][0] = hi;
-    s_rot.m[threadIdx.x][1] = (float)(m - (double)hi);
+    s_rot.m[k][0] = hi;
+    s_rot.m[k][1] = (float)(m - (double)hi);
   }
   __syncthreads();
-  const RotFF rot = s_rot;
+  const float4 q = s_q;
   const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
   const bool closed = d.elem_closed[g] != 0;
+  const float hw = closed ? 0.0f : d.elem_hw[g];
+  if (wid == kTfVertexWarps) {
+    // the tile rectangle, the pair slots and the emission's chunks (lane 0 takes the counts)
+    const bool finite = isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && q.w > 0.0f;
+    int4 r = make_int4(0, 0, -1, -1);
+    if (finite) r = bin_rect(q, d.elem_rbin[g], hw, res, d.tile, d.L.rho_px, d.L.pad_px);
+    else if (lane == 0) atomicOr(d.status, kStatusBadParam);
+    if (lane == 0) {
+      d.rect[g] = r;
+      if (zero_grad) d.dq[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (r.z >= r.x && r.w >= r.y) {
+      // the pair slots of the rectangle; beyond the capacity the bins of the iteration are void
+      const int n = (r.z - r.x + 1) * (r.w - r.y + 1);
+      // the emission's work: the rectangle in chunks of kChunkPx / T tiles a side; chunks whose
+      // segments x tiles exceed kHeavyChunk are listed from the front, the others from the back,
+      // so that the emission takes the costliest first and none trails at the end
+      const int cw = d.chunk_tiles, nx = (r.z - r.x) / cw + 1, ny = (r.w - r.y) / cw + 1;
+      const int tiles = min(r.z - r.x + 1, cw) * min(r.w - r.y + 1, cw);
+      const bool heavy = nv * tiles > kHeavyChunk;
+      int pbase = 0, cbase = 0;
+      if (lane == 0) {
+        pbase = atomicAdd(d.pair_need, n);
+        if (pbase > d.cap - n) atomicOr(d.status, kStatusOverflow);
+        d.elem_pbase[g] = pbase;
+        cbase = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);
+      }
+      cbase = __shfl_sync(0xffffffffu, cbase, 0);
+      // (heavy + light chunks beyond the list mean more pairs than the capacity too: the iteration
+      // overflows and the list is not read; every write stays inside it)
+      if (cbase + nx * ny <= d.list_cap && !(*d.status & kStatusOverflow))
+        for (int c = lane; c < nx * ny; c += 32) {
+          const int at = heavy ? cbase + c : d.list_cap - 1 - (cbase + c);
+          d.near_list[at] = make_int4(g, (r.x + (c % nx) * cw) | ((r.y + (c / nx) * cw) << 16), p, 0);
+        }
+    }
+    return;  // no barrier follows for this warp
+  }
+  const RotFF rot = s_rot;
   float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
-  for (int k0 = wid * 32; k0 < nv; k0 += kTfThreads) {  // warp-uniform trip count
+  for (int k0 = wid * 32; k0 < nv; k0 += kTfVertexWarps * 32) {  // warp-uniform trip count
     const int k = k0 + lane;
     float2 a = make_float2(0.f, 0.f);
     if (k < nv) {
@@ -152,9 +206,10 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     s_box[2][wid] = xmax;
     s_box[3][wid] = ymax;
   }
-  __syncthreads();
+  // the vertex warps only (warp 3 has left): named barrier 1 over their threads
+  asm volatile("bar.sync 1, %0;" ::"n"(kTfVertexWarps * 32) : "memory");
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kTfThreads / 32; ++w) {
+    for (int w = 1; w < kTfVertexWarps; ++w) {
       xmin = fminf(xmin, s_box[0][w]);
       ymin = fminf(ymin, s_box[1][w]);
       xmax = fmaxf(xmax, s_box[2][w]);
@@ -163,39 +218,9 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     const double tx = (double)q.x * res, ty = (double)q.y * res;
     const float hx = (float)tx, hy = (float)ty;
     d.tpx[g] = make_float4(hx, hy, (float)(tx - (double)hx), (float)(ty - (double)hy));
-    const float hw = closed ? 0.0f : d.elem_hw[g];
     // outline box relative to the translation, grown by the coverage margin (+ rounding slack)
     const float m = d.L.rho_px + d.L.pad_px + hw * (float)res + 0.01f;
     d.bbox[g] = make_float4(xmin - m, ymin - m, xmax + m, ymax + m);
-    const bool finite = isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && q.w > 0.0f;
-    int4 r = make_int4(0, 0, -1, -1);
-    if (finite) r = bin_rect(q, d.elem_rbin[g], hw, res, d.tile, d.L.rho_px, d.L.pad_px);
-    else atomicOr(d.status, kStatusBadParam);
-    d.rect[g] = r;
-    if (zero_grad) d.dq[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // the pair slots of the rectangle; beyond the capacity the bins of the iteration are void
-    if (r.z >= r.x && r.w >= r.y) {
-      const int n = (r.z - r.x + 1) * (r.w - r.y + 1);
-      const int base = atomicAdd(d.pair_need, n);
-      if (base > d.cap - n) atomicOr(d.status, kStatusOverflow);
-      d.elem_pbase[g] = base;
-    }
-    // the emission's work: the rectangle in chunks of kChunkPx / T tiles a side; chunks whose
-    // segments x tiles exceed kHeavyChunk are listed from the front, the others from the back, so
-    // that the emission takes the costliest first and none trails at the end
-    if (r.z >= r.x && r.w >= r.y) {
-      const int cw = d.chunk_tiles, nx = (r.z - r.x) / cw + 1, ny = (r.w - r.y) / cw + 1;
-      const int tiles = min(r.z - r.x + 1, cw) * min(r.w - r.y + 1, cw);
-      const bool heavy = nv * tiles > kHeavyChunk;
-      const int base = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);
-      // (heavy + light chunks beyond the list mean more pairs than the capacity too: the iteration
-      // overflows and the list is not read; every write stays inside it)
-      if (base + nx * ny <= d.list_cap && !(*d.status & kStatusOverflow))
-        for (int c = 0; c < nx * ny; ++c) {
-          const int at = heavy ? base + c : d.list_cap - 1 - (base + c);
-          d.near_list[at] = make_int4(g, (r.x + (c % nx) * cw) | ((r.y + (c / nx) * cw) << 16), p, 0);
-        }
-    }
   }
 }
 

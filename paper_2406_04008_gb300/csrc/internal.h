@@ -188,11 +188,10 @@ __device__ __forceinline__ bool in_bounds(const Dev& d, bool ok) {
 // An iteration's step is applied lazily: the loss assembly marks it pending, and the next
 // iteration's transform kernel (one block per element, which reads the params first anyway)
 // applies it before forming the geometry; API calls that read or replace params flush it.
-__device__ __forceinline__ void adam_update(const Dev& d, int g, int t, float4 gr) {
+__device__ __forceinline__ void adam_apply(const Dev& d, int t, float4 gr, uchar4 tr, float4& q, float4& m,
+                                           float4& v) {
   const float bc1 = 1.0f - powf(d.b1, (float)t), bc2 = 1.0f - powf(d.b2, (float)t);
   const float step_size = d.lr / bc1, bc2s = sqrtf(bc2);
-  float4 q = d.q[g], m = d.m[g], v = d.v[g];
-  const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
   float* qp = &q.x;
   float* mp = &m.x;
   float* vp = &v.x;
@@ -207,6 +206,11 @@ __device__ __forceinline__ void adam_update(const Dev& d, int g, int t, float4 g
     qp[k] -= step_size * mp[k] / denom;
   }
   q.w = fminf(fmaxf(q.w, d.s_min), d.s_max);
+}
+__device__ __forceinline__ void adam_update(const Dev& d, int g, int t, float4 gr) {
+  float4 q = d.q[g], m = d.m[g], v = d.v[g];
+  const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
+  adam_apply(d, t, gr, tr, q, m, v);
   d.q[g] = q;
   d.m[g] = m;
   d.v[g] = v;
