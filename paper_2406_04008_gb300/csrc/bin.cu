@@ -98,6 +98,16 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     d.work[1] = 0;
     d.work[3] = 0;
   }
+  // the outline and its first vertices do not depend on the step: read before the barrier
+  const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
+  const bool closed = d.elem_closed[g] != 0;
+  const float hw = closed ? 0.0f : d.elem_hw[g];
+  const int k_first = wid * 32 + lane;
+  float2 va0 = make_float2(0.f, 0.f), vb0 = make_float2(0.f, 0.f);
+  if (wid < kTfVertexWarps && k_first < nv) {
+    va0 = d.vloc[v0 + k_first];
+    if (lane == 31 || k_first + 1 == nv) vb0 = d.vloc[v0 + (k_first + 1 == nv ? 0 : k_first + 1)];
+  }
   if (threadIdx.x < 4) {
     const int k = threadIdx.x;
     float4 q = d.q[g];
@@ -123,9 +133,6 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   }
   __syncthreads();
   const float4 q = s_q;
-  const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
-  const bool closed = d.elem_closed[g] != 0;
-  const float hw = closed ? 0.0f : d.elem_hw[g];
   if (wid == kTfVertexWarps) {
     // the tile rectangle, the pair slots and the emission's chunks (lane 0 takes the counts)
     const bool finite = isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && q.w > 0.0f;
@@ -167,9 +174,10 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   float xmin = FLT_MAX, ymin = FLT_MAX, xmax = -FLT_MAX, ymax = -FLT_MAX;
   for (int k0 = wid * 32; k0 < nv; k0 += kTfVertexWarps * 32) {  // warp-uniform trip count
     const int k = k0 + lane;
+    const bool first = k0 == wid * 32;
     float2 a = make_float2(0.f, 0.f);
     if (k < nv) {
-      a = vertex_px(d.vloc[v0 + k], rot);
+      a = vertex_px(first ? va0 : d.vloc[v0 + k], rot);
       xmin = fminf(xmin, a.x);
       xmax = fmaxf(xmax, a.x);
       ymin = fminf(ymin, a.y);
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     b.x = __shfl_down_sync(0xffffffffu, a.x, 1);
     b.y = __shfl_down_sync(0xffffffffu, a.y, 1);
     const int kb = k + 1 == nv ? 0 : k + 1;
-    if (k < nv && (lane == 31 || k + 1 == nv)) b = vertex_px(d.vloc[v0 + kb], rot);
+    if (k < nv && (lane == 31 || k + 1 == nv)) b = vertex_px(first ? vb0 : d.vloc[v0 + kb], rot);
     if (k < nv) {
       float4 sa = make_float4(a.x, a.y, 0.f, 0.f);
       float2 sb = make_float2(a.y, 0.f);
