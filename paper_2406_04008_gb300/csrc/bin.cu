@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   __shared__ float s_box[4][kTfVertexWarps];
   const int g = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int p = d.elem_prob[g];
+  // (a single problem's resolution is read without waiting for the element's problem index)
+  const int p = d.n_probs == 1 ? 0 : d.elem_prob[g];
   const int res = d.prob_res[p];
   if (g == 0 && threadIdx.x == 0) {  // this iteration's live pairs and finished gradient blocks
     d.work[1] = 0;
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   const int v0 = d.elem_voff[g], nv = d.elem_voff[g + 1] - v0;
   const bool closed = d.elem_closed[g] != 0;
   const float hw = closed ? 0.0f : d.elem_hw[g];
+  const float rbin = wid == kTfVertexWarps ? d.elem_rbin[g] : 0.0f;
   const int k_first = wid * 32 + lane;
   float2 va0 = make_float2(0.f, 0.f), vb0 = make_float2(0.f, 0.f);
   if (wid < kTfVertexWarps && k_first < nv) {
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
     // the tile rectangle, the pair slots and the emission's chunks (lane 0 takes the counts)
     const bool finite = isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w) && q.w > 0.0f;
     int4 r = make_int4(0, 0, -1, -1);
-    if (finite) r = bin_rect(q, d.elem_rbin[g], hw, res, d.tile, d.L.rho_px, d.L.pad_px);
+    if (finite) r = bin_rect(q, rbin, hw, res, d.tile, d.L.rho_px, d.L.pad_px);
     else if (lane == 0) atomicOr(d.status, kStatusBadParam);
     if (lane == 0) {
       d.rect[g] = r;
@@ -153,16 +155,16 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
       const int tiles = min(r.z - r.x + 1, cw) * min(r.w - r.y + 1, cw);
       const bool heavy = nv * tiles > kHeavyChunk;
       int pbase = 0, cbase = 0;
-      if (lane == 0) {
+      if (lane == 0) {  // both counts taken at once (neither waits for the other's result)
         pbase = atomicAdd(d.pair_need, n);
+        cbase = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);
         if (pbase > d.cap - n) atomicOr(d.status, kStatusOverflow);
         d.elem_pbase[g] = pbase;
-        cbase = atomicAdd(d.chunk_count + (heavy ? 0 : 1), nx * ny);
       }
       cbase = __shfl_sync(0xffffffffu, cbase, 0);
       // (heavy + light chunks beyond the list mean more pairs than the capacity too: the iteration
-      // overflows and the list is not read; every write stays inside it)
-      if (cbase + nx * ny <= d.list_cap && !(*d.status & kStatusOverflow))
+      // overflows and the emission does not read the list; every write stays inside it)
+      if (cbase + nx * ny <= d.list_cap)
         for (int c = lane; c < nx * ny; c += 32) {
           const int at = heavy ? cbase + c : d.list_cap - 1 - (cbase + c);
           d.near_list[at] = make_int4(g, (r.x + (c % nx) * cw) | ((r.y + (c / nx) * cw) << 16), p, 0);
