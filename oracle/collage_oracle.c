@@ -780,7 +780,8 @@ double ora_pair_work(const ora_scene* sc, const double* params, int R, const ora
 /* ---------------------------------------------------------------------------------------------
  * Quality metrics (Sec. 6 and Sec. 6.1)
  * ------------------------------------------------------------------------------------------- */
-void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* out) {
+void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* out,
+                 unsigned char* obj_out, unsigned char* shape_out) {
   double rho = o->rho_px / R, pad = o->pad_px / R;
   long NP = (long)R * R;
   double* covc = (double*)malloc(sizeof(double) * NP);
@@ -813,45 +814,6 @@ void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opt
     n_exceed += !shape && obj[p];
     n_over += over[p];
   }
-  /* squared distance (pixels^2) to the nearest object pixel centre, from its definition: the
-   * nearest object pixel of column k lies gcol(i, k) rows away, so the distance^2 is the minimum
-   * over the columns k of (j - k)^2 + gcol(i, k)^2 */
-  const long INF = 1L << 40;
-  long* gcol = (long*)malloc(sizeof(long) * NP);
-#pragma omp parallel for schedule(static)
-  for (int k = 0; k < R; ++k) {
-    long last = -INF;  /* row of the last object pixel above */
-    for (int i = 0; i < R; ++i) {
-      if (obj[(long)i * R + k]) last = i;
-      gcol[(long)i * R + k] = last > -INF ? i - last : INF;
-    }
-    last = INF;
-    for (int i = R - 1; i >= 0; --i) {
-      if (obj[(long)i * R + k]) last = i;
-      if (last < INF && last - i < gcol[(long)i * R + k]) gcol[(long)i * R + k] = last - i;
-    }
-  }
-  double* rowsum = (double*)calloc(R, sizeof(double));
-  double n_free = 0;
-  for (long p = 0; p < NP; ++p) n_free += covc[p] >= 0.5 && !obj[p];
-#pragma omp parallel for schedule(static)
-  for (int i = 0; i < R; ++i)
-    for (int j = 0; j < R; ++j) {
-      long p = (long)i * R + j;
-      if (!(covc[p] >= 0.5) || obj[p]) continue;
-      long best = INF;
-      for (int k = 0; k < R; ++k) {
-        long gk = gcol[(long)i * R + k];
-        if (gk >= INF) continue;
-        long d2 = (long)(j - k) * (j - k) + gk * gk;
-        if (d2 < best) best = d2;
-      }
-      if (best < INF) rowsum[i] += (double)best;
-    }
-  double tot = 0.0; /* rows summed in order */
-  for (int i = 0; i < R; ++i) tot += rowsum[i];
-  int any_obj = 0;
-  for (long p = 0; p < NP && !any_obj; ++p) any_obj = obj[p];
   out[0] = n_obj_in;
   out[1] = n_shape;
   out[2] = n_over;
@@ -859,9 +821,11 @@ void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opt
   out[4] = n_shape > 0 ? n_obj_in / n_shape : 0.0;
   out[5] = n_shape > 0 ? n_over / n_shape : 0.0;
   out[6] = n_shape > 0 ? n_exceed / n_shape : 0.0;
-  out[7] = (any_obj && n_free > 0) ? tot / n_free / ((double)R * (double)R) : 0.0;
-  free(rowsum);
-  free(gcol);
+  out[7] = 0.0;
+  for (long p = 0; p < NP; ++p) {
+    if (obj_out) obj_out[p] = obj[p];
+    if (shape_out) shape_out[p] = covc[p] >= 0.5;
+  }
   free(covc);
   free(obj);
   free(over);

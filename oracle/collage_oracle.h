@@ -105,11 +105,14 @@ double ora_pair_work(const ora_scene* sc, const double* params, int res, const o
  * where at least two elements have sd >= 0 (c_i >= 1/2).  out[8]:
  *   [0] object pixels inside the shape, [1] shape pixels, [2] overlap pixels,
  *   [3] object pixels outside the shape,
- *   [4] LC = [0]/[1], [5] OO = [2]/[1], [6] EA = [3]/[1],
- *   [7] L-nU: mean over the non-object shape pixels of the squared distance (unit coordinates)
- *       from the pixel centre to the nearest object pixel centre (0 if there is no object pixel
- *       or no such pixel). */
-void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* out);
+ *   [4] LC = [0]/[1], [5] OO = [2]/[1], [6] EA = [3]/[1], [7] 0.
+ * obj_out [R*R] (may be NULL) receives the object mask (1: object) and shape_out [R*R] (may be
+ * NULL) the shape mask; the layout non-uniformity L-nU (the mean over the non-object shape pixels
+ * of the squared distance, unit coordinates, from the pixel centre to the nearest object pixel
+ * centre) is formed from them by oracle.py, as a nearest-neighbour search over every object
+ * pixel. */
+void ora_metrics(const ora_scene* sc, const double* params, int R, const ora_opts* o, double* out,
+                 unsigned char* obj_out, unsigned char* shape_out);
 
 /* Threads the OpenMP loops use from now on (n < 1: all the host's cores); returns the previous
  * setting.  For timing the oracle on one core. */

@@ -21,6 +21,7 @@ _lib = None
 _dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 _fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
@@ -89,7 +90,7 @@ def _load():
     lib.ora_bin_radius.argtypes = [vp, C.c_int]
     lib.ora_pair_work.restype = C.c_double
     lib.ora_pair_work.argtypes = [vp, _dp, C.c_int, opt]
-    lib.ora_metrics.argtypes = [vp, _dp, C.c_int, opt, _dp]
+    lib.ora_metrics.argtypes = [vp, _dp, C.c_int, opt, _dp, _u8p, _u8p]
     lib.ora_uniform_term.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double), dpn]
     lib.ora_set_threads.restype = C.c_int
     lib.ora_set_threads.argtypes = [C.c_int]
@@ -196,9 +197,20 @@ class Scene:
         return self.lib.ora_bin_radius(self.h, e)
 
     def metrics(self, params, res, opts):
-        """[obj in shape, shape, overlap, obj outside shape, LC, OO, EA, L-nU] (see ora_metrics)."""
+        """[obj in shape, shape, overlap, obj outside shape, LC, OO, EA, L-nU] (see ora_metrics).
+        L-nU (Sec. 6.1) from its definition: for every non-object shape pixel the squared distance
+        to the nearest object pixel centre, that pixel found by a nearest-neighbour search over all
+        object pixels; the mean, in unit coordinates."""
         out = np.zeros(8)
-        self.lib.ora_metrics(self.h, _d(params), res, C.byref(opts), out)
+        obj = np.zeros(res * res, np.uint8)
+        shape = np.zeros(res * res, np.uint8)
+        self.lib.ora_metrics(self.h, _d(params), res, C.byref(opts), out, obj, shape)
+        obj = obj.reshape(res, res).astype(bool)
+        free = shape.reshape(res, res).astype(bool) & ~obj
+        out[7] = 0.0
+        if obj.any() and free.any():
+            d2 = nearest_d2(np.argwhere(obj), np.argwhere(free))
+            out[7] = float(d2.sum()) / len(d2) / (float(res) * res)
         return out
 
     def pair_work(self, params, res, opts):
@@ -298,34 +310,37 @@ def adam_points(pts, m, v, g, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
     return pts, m, v
 
 
+def nearest_d2(sites: np.ndarray, queries: np.ndarray) -> np.ndarray:
+    """Exact integer squared distance from each query pixel (row, column) to its nearest site
+    pixel: a k-d tree nearest-neighbour search (a library primitive) names the nearest site, and
+    the squared distance is formed from the integer coordinates (squared distances between
+    integer points are exact in double, so the search's choice is a true nearest one; any of
+    several equally near sites gives the same value)."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(sites.astype(np.float64))
+    _, idx = tree.query(queries.astype(np.float64), k=1)
+    diff = sites[idx].astype(np.int64) - queries.astype(np.int64)
+    return (diff * diff).sum(axis=1)
+
+
 # skeleton-based initialisation (Sec. 4.1) ---------------------------------------------------------
 def medial_axis(covc: np.ndarray):
     """(D2, axis) of a container raster covc [R, R] (Sec. 4.1: the medial axis and the medial width).
 
     inside = covc >= 1/2, the pixels one step beyond the image outside.  D2 is the squared distance
-    in pixels from each inside pixel centre to the nearest outside pixel centre (0 outside): per
-    column the row distance g to the nearest outside pixel, then per row the minimum over columns
-    k of (j - k)^2 + g(k)^2, the two columns beyond the image included with g = 0.  The axis is the
-    ridge of D2: inside pixels that are a maximum of D2 along one of the four lines through them
-    (horizontal, vertical, the two diagonals), D2(p) >= both line neighbours and > at least one
-    (neighbours beyond the image count 0)."""
+    in pixels from each inside pixel centre to the nearest outside pixel centre (0 outside), the
+    nearest one found by a nearest-neighbour search over every outside pixel (nearest_d2).  The axis
+    is the ridge of D2: inside pixels that are a maximum of D2 along one of the four lines through
+    them (horizontal, vertical, the two diagonals), D2(p) >= both line neighbours and > at least
+    one (neighbours beyond the image count 0)."""
     R = covc.shape[0]
     inside = covc >= 0.5
-    g = np.zeros((R, R), np.int64)
-    last = np.full(R, -1, np.int64)
-    for i in range(R):
-        last = np.where(inside[i], last, i)
-        g[i] = i - last
-    last = np.full(R, R, np.int64)
-    for i in range(R - 1, -1, -1):
-        last = np.where(inside[i], last, i)
-        g[i] = np.minimum(g[i], last - i)
-    j = np.arange(R, dtype=np.int64)
+    ring = [(i, j) for i in range(-1, R + 1) for j in (-1, R)] + [(i, j) for i in (-1, R) for j in range(R)]
+    outside = np.concatenate([np.argwhere(~inside), np.array(ring, np.int64)])
     D2 = np.zeros((R, R), np.int64)
-    for i in range(R):
-        best = ((j[:, None] - j[None, :]) ** 2 + g[i][None, :] ** 2).min(axis=1)
-        best = np.minimum(best, np.minimum((j + 1) ** 2, (R - j) ** 2))
-        D2[i] = np.where(inside[i], best, 0)
+    q = np.argwhere(inside)
+    if len(q):
+        D2[q[:, 0], q[:, 1]] = nearest_d2(outside, q)
     pad = np.zeros((R + 2, R + 2), np.int64)
     pad[1:-1, 1:-1] = D2
     axis = np.zeros((R, R), bool)
