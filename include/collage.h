@@ -181,7 +181,11 @@ collage_status collage_run_schedule(collage_t h, void* stream);
  * and synchronises.  Pinned host memory is faster but not required; the outputs are gathered by
  * one kernel into a mapped (page-locked) staging buffer of the handle.  Unless a bin overflow has
  * to be recovered (as collage_step does), the transfers, the iterations and the status check share
- * one host round trip. */
+ * one host round trip.  With params in, one iteration and graphs enabled, the call copies the params
+ * on the host into a second mapped buffer of the handle and launches one captured graph: its
+ * transform reads them from there (a pending Adam step updates the moments, the params are
+ * replaced) and its last kernel writes the outputs, so no separate copy or launch precedes or
+ * follows the iteration. */
 collage_status collage_step_host(collage_t h, void* stream, int n_iters, const float* h_params_in,
                                  float* h_params_out, float* h_loss_out);
 

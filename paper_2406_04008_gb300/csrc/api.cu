@@ -79,6 +79,8 @@ struct collage_s {
   float* h_stage = nullptr;  // pinned: their host copy ([4n | 5 n_probs | 4], see k_adam_flush)
   float* h_stage_dev = nullptr;  // h_stage mapped into the device's address space (or null): the
                                  // gathering kernel then writes the host copy itself
+  float* h_in = nullptr;         // pinned, mapped: params in for the host-buffer step ([4n])
+  float4* h_in_dev = nullptr;    // h_in in the device's address space (or null: no host graph)
   bool ctl_current = false;  // h_ctl[1] (step count) and h_ctl[3] (pending) are the device's:
                              // no step was enqueued since the last read
   cudaStream_t cap_stream = nullptr;
@@ -86,6 +88,8 @@ struct collage_s {
   cudaStream_t body_stream = nullptr;  // captures the loop bodies of the schedule graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;  // one iteration at the current level
+  cudaGraphExec_t host_graph = nullptr;  // one iteration taking its params from h_in, then the
+                                         // gathering kernel writing h_stage (collage_step_host)
   cudaGraphExec_t sched = nullptr;  // the schedule from level sched_start to the last
   int sched_start = -1;
   // quality-metric scratch (allocated by collage_metrics)
@@ -153,6 +157,8 @@ bool is_finite_f(float x) { return std::isfinite(x); }
 void drop_iter_graph(collage_t h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+  if (h->host_graph) cudaGraphExecDestroy(h->host_graph);
+  h->host_graph = nullptr;
 }
 
 void drop_graph(collage_t h) {
@@ -166,6 +172,8 @@ void drop_graph(collage_t h) {
 
 collage_s::~collage_s() {
   if (graph) cudaGraphExecDestroy(graph);
+  if (host_graph) cudaGraphExecDestroy(host_graph);
+  if (h_in) cudaFreeHost(h_in);
   if (sched) cudaGraphExecDestroy(sched);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (body_stream) cudaStreamDestroy(body_stream);
@@ -647,6 +655,29 @@ static collage_status ensure_graph(collage_t h) {
   return COLLAGE_OK;
 }
 
+// The host-buffer step's graph: one iteration whose transform takes the params from the mapped
+// input buffer h_in (so no copy precedes it), then the kernel that applies the Adam step and gathers
+// params, loss terms and control words into the mapped h_stage.  Needs both mapped buffers.
+static collage_status ensure_host_graph(collage_t h) {
+  if (h->host_graph) return COLLAGE_OK;
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  h->d.q_in = h->h_in_dev;
+  cudaError_t e = enqueue_iter(h, h->cap_stream, kStep, nullptr, nullptr);
+  h->d.q_in = nullptr;
+  if (e == cudaSuccess) e = launch_adam_flush(h->d, h->cap_stream, h->h_stage_dev);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, e, "capture");
+  }
+  CK(h, e2);
+  e = cudaGraphInstantiate(&h->host_graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(h, e);
+  return COLLAGE_OK;
+}
+
 // After a batch of work: check the latched status; grow the pair buffers when the last binning
 // used more than 3/4 of them.  Returns OVERFLOW if the batch overflowed (caller re-runs).
 static collage_status check_and_grow(collage_t h, cudaStream_t s, bool* overflowed) {
@@ -914,6 +945,11 @@ extern "C" collage_status collage_create(const collage_problem* probs, int n_pro
     h->h_stage_dev = nullptr;
     cudaGetLastError();
   }
+  CKC(cudaHostAlloc(&h->h_in, sizeof(float4) * std::max<size_t>(h->N, 1), cudaHostAllocMapped));
+  if (cudaHostGetDevicePointer(&h->h_in_dev, h->h_in, 0) != cudaSuccess) {
+    h->h_in_dev = nullptr;
+    cudaGetLastError();
+  }
   CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CKC(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
   CKC(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
@@ -1162,18 +1198,29 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
   collage_status st = h->ctl_current ? COLLAGE_OK : read_ctl(h, s);
   if (st) return st;
   const int step0 = h->h_ctl[1];
-  if (h_params_in) {
-    // a pending step belongs to the old params (none is pending right after this call's own flush)
-    if (h->h_ctl[3] != 0) CK(h, launch_adam_flush(h->d, s));
-    CK(h, cudaMemcpyAsync(h->d.q, h_params_in, sizeof(float4) * h->N, cudaMemcpyHostToDevice, s));
+  // one iteration with params in: one graph launch (its transform reads them from the mapped
+  // input buffer and takes a pending step's moments; its last kernel writes the mapped output)
+  const bool host_graph = h_params_in && n_iters == 1 && h->opt.use_graphs && h->h_in_dev && h->h_stage_dev;
+  if (host_graph) {
+    st = ensure_host_graph(h);
+    if (st) return st;
+    std::memcpy(h->h_in, h_params_in, sizeof(float4) * h->N);
+    CK(h, cudaGraphLaunch(h->host_graph, s));
+  } else {
+    if (h_params_in) {
+      // a pending step belongs to the old params (none is pending right after this call's flush)
+      if (h->h_ctl[3] != 0) CK(h, launch_adam_flush(h->d, s));
+      CK(h, cudaMemcpyAsync(h->d.q, h_params_in, sizeof(float4) * h->N, cudaMemcpyHostToDevice, s));
+    }
+    // one host round trip when nothing overflows: the steps, then one kernel that applies the
+    // last Adam step and gathers the params, the loss terms and the control words, one copy of
+    // those to pinned memory, and one synchronisation
+    st = enqueue_steps(h, s, n_iters);
+    if (st) return st;
   }
-  // one host round trip when nothing overflows: the steps, then one kernel that applies the last
-  // Adam step and gathers the params, the loss terms and the control words, one copy of those to
-  // pinned memory, and one synchronisation
-  st = enqueue_steps(h, s, n_iters);
-  if (st) return st;
-  auto copy_out = [&]() -> collage_status {
-    if (h->h_stage_dev) {
+  auto copy_out = [&](bool launched) -> collage_status {
+    if (launched) {
+    } else if (h->h_stage_dev) {
       CK(h, launch_adam_flush(h->d, s, h->h_stage_dev));
     } else {
       CK(h, launch_adam_flush(h->d, s, h->d_stage));
@@ -1187,7 +1234,7 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
     h->ctl_current = true;
     return COLLAGE_OK;
   };
-  st = copy_out();
+  st = copy_out(host_graph);
   if (st) return st;
   const int status = h->h_ctl[0], done = h->h_ctl[1] - step0;
   if (!(status & (kStatusVoid | kStatusInternal)) && done == n_iters &&
@@ -1200,7 +1247,7 @@ extern "C" collage_status collage_step_host(collage_t h, void* stream, int n_ite
   if (done < n_iters) {
     st = collage_step(h, stream, n_iters - done);
     if (st) return st;
-    st = copy_out();
+    st = copy_out(false);
     if (st) return st;
   }
   return COLLAGE_OK;

@@ -112,26 +112,32 @@ __global__ void __launch_bounds__(kTfThreads) k_transform(Dev d, int zero_grad) 
   }
   if (threadIdx.x < 4) {
     const int k = threadIdx.x;
-    float4 q = d.q[g];
+    float4 q = d.q[g], m, v;
     // the previous iteration's step (when the outlines are fitted the transforms stay fixed)
-    if (*d.pending && !d.fit) {
-      float4 m = d.m[g], v = d.v[g];
+    const bool step = *d.pending && !d.fit;
+    if (step) {
+      m = d.m[g];
+      v = d.v[g];
       const uchar4 tr = d.trainable ? d.trainable[g] : make_uchar4(1, 1, 1, 1);
       adam_apply(d, *d.step, d.dq[g], tr, q, m, v);
-      __syncwarp(0xfu);  // every reader of the old params is done
-      auto pick = [k](float4 x) { return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w; };
-      reinterpret_cast<float*>(d.q + g)[k] = pick(q);
+    }
+    // the host-buffer step: the caller's params replace the stepped ones (the moments keep the step)
+    if (d.q_in) q = d.q_in[g];
+    __syncwarp(0xfu);  // every reader of the old params is done
+    auto pick = [k](float4 x) { return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w; };
+    if (step) {
       reinterpret_cast<float*>(d.m + g)[k] = pick(m);
       reinterpret_cast<float*>(d.v + g)[k] = pick(v);
     }
+    if (step || d.q_in) reinterpret_cast<float*>(d.q + g)[k] = pick(q);
     if (k == 0) s_q = q;
     double sn, c;
     sincos((double)q.z, &sn, &c);
     const double sc = (double)q.w * (double)res;
-    const double m = k == 0 ? sc * c : k == 1 ? -sc * sn : k == 2 ? sc * sn : sc * c;
-    const float hi = (float)m;
+    const double mk = k == 0 ? sc * c : k == 1 ? -sc * sn : k == 2 ? sc * sn : sc * c;
+    const float hi = (float)mk;
     s_rot.m[k][0] = hi;
-    s_rot.m[k][1] = (float)(m - (double)hi);
+    s_rot.m[k][1] = (float)(mk - (double)hi);
   }
   __syncthreads();
   const float4 q = s_q;

@@ -78,6 +78,8 @@ struct Dev {
   float4* q;
   float4* m;
   float4* v;
+  const float4* q_in;           // [n] params the transform takes in place of q (the host-buffer
+                                //   step's mapped input), or null
   const uchar4* trainable;      // may be null
   float lr, b1, b2, eps, s_min, s_max;
   // ---- per iteration ----

@@ -188,6 +188,40 @@ def test_step_host_recovers_an_overflow(Collage):
     ref.close()
 
 
+def test_single_host_step_graph_equals_synchronous_calls(Collage):
+    """collage_step_host with params in and one iteration runs one captured graph whose transform
+    reads the params from the mapped input buffer; call after call (a pending step's moments kept,
+    the params replaced) it equals set_params + step + get_params bit for bit, and an input that
+    outgrows the bins is finished by the synchronous path."""
+    prob, opts, grid = _case()
+    g, _ = U.paired(**opts)
+    kw = dict(level_res=[grid], deterministic=1, **g)
+    col = Collage(prob, **kw)
+    ref = Collage(prob, **kw)
+    q = np.asarray(prob["params0"], np.float32).reshape(-1)
+    rng = np.random.default_rng(5)
+    for k in range(4):
+        if k == 2:  # a caller's params that are not the last output
+            q = (q.reshape(-1, 4) + np.float32(1e-3) * rng.standard_normal((q.size // 4, 4)).astype(np.float32)
+                 * np.array([1, 1, 1, 0], np.float32)).reshape(-1).astype(np.float32)
+        pout, lout = col.step_host(1, params_in=q)
+        ref.set_params(torch.from_numpy(q).cuda())
+        ref.step(1)
+        assert np.array_equal(pout, ref.get_params().reshape(-1).cpu().numpy()), k
+        assert np.array_equal(lout, ref.loss().reshape(-1).cpu().numpy()), k
+        assert col.get_state()[1] == ref.get_state()[1] == k + 1
+        q = pout
+    big = q.reshape(-1, 4).copy()
+    big[:, 3] *= 4.0
+    pout, _ = col.step_host(1, params_in=big.reshape(-1))
+    ref.set_params(torch.from_numpy(big.reshape(-1)).cuda())
+    ref.step(1)
+    assert np.array_equal(pout, ref.get_params().reshape(-1).cpu().numpy())
+    assert col.get_state()[1] == ref.get_state()[1] == 5
+    col.close()
+    ref.close()
+
+
 def test_fp32_peak_is_plausible(Collage):
     """The FMA-chain measurement lands between half and 1.05x of SMs x 128 lanes x 2 x max clock."""
     import ctypes as C
