@@ -274,7 +274,7 @@ typedef struct {
  * kernels (each candidate a
  * captured one-iteration graph of loss and gradient, no Adam step, the fastest of three batches of
  * 20 timed replays), and keeps the fastest; a launch parameter other than the tile changes only
- * when its candidate is more than 1.5% faster.  The choice is cached for the process, keyed on (pixels of the level, element
+ * when its candidate is more than 3% faster.  The choice is cached for the process, keyed on (pixels of the level, element
  * count, pair density in half-octaves, deterministic mode); a handle with the same key reuses it
  * without a search.  One configuration serves the whole handle (every problem of a batch).
  * h_best_ms (may be NULL) receives the chosen configuration's iteration time.  Params and Adam

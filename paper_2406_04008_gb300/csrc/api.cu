@@ -1543,7 +1543,8 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
       if (std::memcmp(&c, &base, sizeof(c)) == 0) continue;
       float ms = 0.0f;
       if ((st = trial(c, &ms))) break;
-      if (ms < best_ms * 0.985f) {  // a change of launch parameter has to win clearly
+      if (ms < best_ms * 0.97f) {  // a change of launch parameter has to win clearly (3%: the
+        // one-iteration graphs it is timed on run warm; smaller gains do not carry to the step)
         best_ms = ms;
         best = c;
       }
