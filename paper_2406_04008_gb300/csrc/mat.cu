@@ -17,14 +17,18 @@
 //    so every decision is reproducible.  The element's translation becomes its pixel centre;
 //    rotation and scale are kept.
 #include <cfloat>
+#include <cooperative_groups.h>
 
 #include "collage.h"
 #include "internal.h"
 
 namespace collage {
 
+namespace cg = cooperative_groups;
+
 constexpr int kMatWarps = 4;
-constexpr int kPlaceThreads = 1024;
+constexpr int kPlaceThreads = 512;
+constexpr int kPlaceCluster = 8;  // blocks (one thread-block cluster) per problem
 
 __device__ __forceinline__ bool inside_px(const Dev& d, long long pix) { return d.covc[pix] >= 0.5f; }
 
@@ -137,7 +141,7 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v, un
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    v = s[threadIdx.x];
+    v = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0ull;
     for (int o = 16; o; o >>= 1) {
       const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
       v = w > v ? w : v;
@@ -148,22 +152,56 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v, un
   return s[0];
 }
 
+// The block's maxima of two keys in one reduction.
+__device__ __forceinline__ void block_max2(unsigned long long& a, unsigned long long& b, unsigned long long (*s)[2]) {
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long wa = __shfl_xor_sync(0xffffffffu, a, o);
+    const unsigned long long wb = __shfl_xor_sync(0xffffffffu, b, o);
+    a = wa > a ? wa : a;
+    b = wb > b ? wb : b;
+  }
+  __syncthreads();  // the previous reduction's readers are done
+  if ((threadIdx.x & 31) == 0) {
+    s[threadIdx.x >> 5][0] = a;
+    s[threadIdx.x >> 5][1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool in = threadIdx.x < (blockDim.x >> 5);
+    a = in ? s[threadIdx.x][0] : 0ull;
+    b = in ? s[threadIdx.x][1] : 0ull;
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long wa = __shfl_xor_sync(0xffffffffu, a, o);
+      const unsigned long long wb = __shfl_xor_sync(0xffffffffu, b, o);
+      a = wa > a ? wa : a;
+      b = wb > b ? wb : b;
+    }
+  }
+}
+
 // A float's bits as an unsigned key with the float's order (negative values included).
 __device__ __forceinline__ unsigned ordered(float f) {
   const unsigned u = __float_as_uint(f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Greedy placement, one block per problem.  First the elements are ranked by radius (ties: lower
-// index) into order[]; then every axis pixel's D2, packed coordinates and clearance are gathered
-// into per-candidate arrays, in dynamic shared memory when they fit there (else in cand, gxy and
-// clear); then each step is one pass over the candidates: the clearances take the previous
-// element's disk into account and the next element's choice is reduced over the block.
+// Greedy placement, one thread-block cluster of kPlaceCluster blocks per problem.  Block 0 first
+// ranks the elements by radius (ties: lower index) into order[]; every block then gathers its
+// share of the axis pixels (D2, packed coordinates, clearance) into dynamic shared memory (else
+// into cand, gxy and clear); each step is one pass of every block over its share: the clearances
+// take the previous element's disk into account and the block reduces its two candidates (the
+// widest pixel with room, the pixel of largest clearance); after one cluster barrier every block
+// reads the cluster's partials from the blocks' shared memory (double-buffered by step parity, so
+// one barrier a step suffices) and takes the same choice; block 0 writes the translation.  Every
+// block runs the same steps and barriers, and a last barrier keeps each block's shared memory
+// alive until the others have read it.
 constexpr int kPlaceRankMax = 4096;                // elements ranked in shared memory (more: a
                                                    // reduction per step)
-constexpr int kPlaceSmem = 224 * 1024;             // dynamic shared memory of the placement
-constexpr int kPlaceSmemCands = kPlaceSmem / 12;   // candidates it holds (D2, coordinates, clearance)
-static_assert(kPlaceSmem >= kPlaceRankMax * 8, "the ranking keys share the candidates' space");
+constexpr int kPlaceSmemCandBytes = 160 * 1024;    // candidates of a placement block (D2,
+constexpr int kPlaceSmemCands = kPlaceSmemCandBytes / 12;  // coordinates, clearance)
+// then, for the ranked elements, each step's element and radius
+constexpr int kPlaceSmem = kPlaceSmemCandBytes + kPlaceRankMax * 8;
+static_assert(kPlaceSmemCandBytes >= kPlaceRankMax * 8, "the ranking keys share the candidates' space");
 
 __device__ __forceinline__ unsigned long long elem_key(const Dev& d, int e, float fres) {
   const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
@@ -175,35 +213,52 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, c
                                                              int* order) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ unsigned long long s_red[kPlaceThreads / 32];
-  const int p = blockIdx.x;
+  __shared__ unsigned long long s_red2[kPlaceThreads / 32][2];
+  __shared__ unsigned long long s_part[2][2];  // per step parity: (widest with room, largest clearance)
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int p = blockIdx.x / kPlaceCluster;
   const int res = d.prob_res[p], nc = n_cand[p];
   const long long pb = d.prob_pix_base[p];
   const int e0 = d.prob_elem_base[p], e1 = d.prob_elem_base[p + 1], ne = e1 - e0;
-  if (nc == 0) return;  // no inside pixel: the params stay
+  if (nc == 0) return;  // no inside pixel: the params stay (every block of the cluster leaves here)
   const float fres = (float)res;
   // the elements in placement order: decreasing key (radius bits, then the lower index)
   const bool ranked = ne <= kPlaceRankMax;
-  if (ranked) {
-    unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_dyn);
-    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) s_key[i] = elem_key(d, e0 + i, fres);
-    __syncthreads();
-    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
-      const unsigned long long k = s_key[i];
-      int rank = 0;
-      for (int j = 0; j < ne; ++j) rank += s_key[j] > k ? 1 : 0;
-      order[e0 + rank] = e0 + i;
+  if (rank == 0) {
+    if (ranked) {
+      unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_dyn);
+      for (int i = threadIdx.x; i < ne; i += kPlaceThreads) s_key[i] = elem_key(d, e0 + i, fres);
+      __syncthreads();
+      for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
+        const unsigned long long k = s_key[i];
+        int rnk = 0;
+        for (int j = 0; j < ne; ++j) rnk += s_key[j] > k ? 1 : 0;
+        order[e0 + rnk] = e0 + i;
+      }
+    } else {
+      for (int i = threadIdx.x; i < ne; i += kPlaceThreads) order[e0 + i] = 0;  // 0: not placed yet
     }
-  } else {
-    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) order[e0 + i] = 0;  // 0: not placed yet
+    __threadfence();
   }
-  __syncthreads();  // the keys' space is free
-  // per candidate: D2, x | y << 16, the clearance
-  const bool in_smem = nc <= kPlaceSmemCands;
-  unsigned* cd2 = in_smem ? reinterpret_cast<unsigned*>(s_dyn) : reinterpret_cast<unsigned*>(cand + pb);
-  int* cxy = in_smem ? reinterpret_cast<int*>(s_dyn + 4 * kPlaceSmemCands) : gxy + pb;
-  float* ccl = in_smem ? reinterpret_cast<float*>(s_dyn + 8 * kPlaceSmemCands) : clear + pb;
-  for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
-    const int idx = cand[pb + c];
+  cluster.sync();  // order[] is complete (and block 0's keys' space is free)
+  int* s_ord = reinterpret_cast<int*>(s_dyn + kPlaceSmemCandBytes);
+  float* s_rad = reinterpret_cast<float*>(s_dyn + kPlaceSmemCandBytes + 4 * kPlaceRankMax);
+  if (ranked)
+    for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
+      const int e = order[e0 + i];
+      s_ord[i] = e;
+      s_rad[i] = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
+    }
+  // this block's share of the candidates: D2, x | y << 16, the clearance
+  const int c_lo = (int)((long long)nc * rank / kPlaceCluster);
+  const int mc = (int)((long long)nc * (rank + 1) / kPlaceCluster) - c_lo;
+  const bool in_smem = mc <= kPlaceSmemCands;
+  unsigned* cd2 = in_smem ? reinterpret_cast<unsigned*>(s_dyn) : reinterpret_cast<unsigned*>(cand + pb + c_lo);
+  int* cxy = in_smem ? reinterpret_cast<int*>(s_dyn + 4 * kPlaceSmemCands) : gxy + pb + c_lo;
+  float* ccl = in_smem ? reinterpret_cast<float*>(s_dyn + 8 * kPlaceSmemCands) : clear + pb + c_lo;
+  for (int c = threadIdx.x; c < mc; c += kPlaceThreads) {
+    const int idx = cand[pb + c_lo + c];
     const unsigned w = d2[pb + idx];
     cd2[c] = w;
     cxy[c] = (idx % res) | ((idx / res) << 16);
@@ -214,9 +269,11 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, c
   float pr = -1.0f;
   for (int step = 0; step < ne; ++step) {
     int e;
+    float r;
     if (ranked) {
-      e = order[e0 + step];
-    } else {  // the largest element not yet placed, by a reduction
+      e = s_ord[step];
+      r = s_rad[step];
+    } else {  // the largest element not yet placed, by a reduction (the same in every block)
       unsigned long long ek = 0;
       for (int i = threadIdx.x; i < ne; i += kPlaceThreads) {
         if (order[e0 + i]) continue;
@@ -225,12 +282,12 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, c
       }
       ek = block_max(ek, s_red);
       e = (int)(0xffffffffu - (unsigned)(ek & 0xffffffffu));
+      r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
     }
-    const float r = __fmul_rn(__fmul_rn(d.elem_rbin[e], d.q[e].w), fres);
     // one pass: the previous element's disk into the clearances, then the widest axis pixel with
     // clearance >= r (key: D2, then the lower pixel index), and the largest clearance as fallback
     unsigned long long ck = 0, fk = 0;
-    for (int c = threadIdx.x; c < nc; c += kPlaceThreads) {
+    for (int c = threadIdx.x; c < mc; c += kPlaceThreads) {
       const int xy = cxy[c], x = xy & 0xffff, y = xy >> 16;
       float cl = ccl[c];
       if (pr >= 0.0f) {
@@ -249,21 +306,45 @@ __global__ void __launch_bounds__(kPlaceThreads) k_mat_place(Dev d, int* cand, c
       const unsigned long long kf = ((unsigned long long)ordered(cl) << 32) | low;
       fk = kf > fk ? kf : fk;
     }
-    ck = block_max(ck, s_red);
-    if (ck == 0) ck = block_max(fk, s_red);  // none has room: the largest clearance
-    const int idx = (int)(0xffffffffu - (unsigned)(ck & 0xffffffffu));
+    block_max2(ck, fk, s_red2);
+    if (threadIdx.x == 0) {
+      s_part[step & 1][0] = ck;
+      s_part[step & 1][1] = fk;
+    }
+    cluster.sync();  // every block's partials of this step are written
+    // every warp reduces the cluster's partials itself (lane k reads block k's)
+    unsigned long long a = 0, b = 0;
+    const int lane = threadIdx.x & 31;
+    if (lane < kPlaceCluster) {
+      const unsigned long long* part = cluster.map_shared_rank(&s_part[step & 1][0], (unsigned)lane);
+      a = part[0];
+      b = part[1];
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long wa = __shfl_xor_sync(0xffffffffu, a, o);
+      const unsigned long long wb = __shfl_xor_sync(0xffffffffu, b, o);
+      a = wa > a ? wa : a;
+      b = wb > b ? wb : b;
+    }
+    const unsigned long long best = a != 0 ? a : b;  // none has room: the largest clearance
+    const int idx = (int)(0xffffffffu - (unsigned)(best & 0xffffffffu));
     px = idx % res;
     py = idx / res;
     pr = r;
     if (threadIdx.x == 0) {
-      if (!ranked) order[e] = 1;
-      float4 q = d.q[e];
-      q.x = __fdiv_rn(__fadd_rn((float)px, 0.5f), fres);
-      q.y = __fdiv_rn(__fadd_rn((float)py, 0.5f), fres);
-      d.q[e] = q;
+      if (!ranked) order[e] = 1;  // (every block marks it: its own next reduction reads it)
+      if (rank == 0) {
+        float4 q = d.q[e];
+        q.x = __fdiv_rn(__fadd_rn((float)px, 0.5f), fres);
+        q.y = __fdiv_rn(__fadd_rn((float)py, 0.5f), fres);
+        d.q[e] = q;
+      }
     }
-    __syncthreads();  // the choice is complete before the next pass (the unranked flags too)
+    // the unranked flags are visible to the next reduction (the partials' buffer of this step is
+    // not written again before the next step's cluster barrier, which every thread passes)
+    if (!ranked) __syncthreads();
   }
+  cluster.sync();  // no block leaves while another may still read its partials
 }
 
 cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol, unsigned* d2,
@@ -280,8 +361,19 @@ cudaError_t launch_mat_init(const Dev& d, cudaStream_t s, int max_res, int* gcol
   // shared memory
   e = cudaFuncSetAttribute(k_mat_place, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaceSmem);
   if (e != cudaSuccess) return e;
-  k_mat_place<<<d.n_probs, kPlaceThreads, kPlaceSmem, s>>>(d, cand, n_cand, d2, clear, gcol, order);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(d.n_probs * kPlaceCluster);
+  cfg.blockDim = dim3(kPlaceThreads);
+  cfg.dynamicSmemBytes = kPlaceSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kPlaceCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mat_place, d, cand, n_cand, d2, clear, gcol, order);
 }
 
 }  // namespace collage
