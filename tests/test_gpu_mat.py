@@ -90,3 +90,18 @@ def test_mat_init_more_elements_than_ranked(env):
         params.append((0.5, 0.5, 0.0, 0.6 + 0.8 * rng.uniform()))
     prob = W.make_problem(els, W.annulus_container(), params, 256)
     _check(env, [prob], [256], level_res=[256], tile=16)
+
+
+def test_mat_init_few_axis_pixels(env):
+    # a container a few pixels wide: fewer axis pixels than the placement's cluster has blocks,
+    # so most blocks hold no candidate and the choice comes from the others' partials; more
+    # elements than axis pixels, so the later ones take the pixel of largest clearance
+    O, Collage = env
+    rng = W.PCG32(7)
+    els = [(1, W.regular_polygon(0.01 + 0.005 * k, 6), 0.0) for k in range(5)] + \
+          [(0, W.blob_controls(rng, 0.012), 0.0) for _ in range(4)]
+    params = [(0.2 + 0.07 * k, 0.3, 0.1 * k, 1.0) for k in range(len(els))]
+    for side in (0.018, 0.035):  # 4 and 16 axis pixels
+        ring = W.regular_polygon(side, 24) + (0.5, 0.5)
+        prob = W.make_problem(els, [ring], params, 64)
+        _check(env, [prob], [64], level_res=[64], tile=8)
