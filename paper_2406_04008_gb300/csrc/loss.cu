@@ -58,6 +58,8 @@ struct DilGeom {
   static constexpr int SP = S | 1;        // staged row stride (odd)
   static constexpr int HR = hbase(K);     // rows of H over all kernels
   static constexpr int Q = qbits(2 * h + 1);
+  static constexpr int CW = S <= 32 ? 32 : S <= 64 ? 64 : 128;  // staging: threads per staged row
+  static_assert(CW <= kDThreads, "a staged row fits the block");
 };
 
 template <int K>
@@ -175,11 +177,18 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
     __syncthreads();
+    {  // thread (column, first row): no division per element, 32-bit offsets from the problem's base
+      constexpr int CW = DilGeom<K>::CW, RP = kDThreads / CW;
+      const int c = threadIdx.x % CW, X = x0 + c - h;
+      const bool col_in = X >= 0 && X < res;
+      const float* src = d.img_I + pb;
+      if (c < S) {
 #pragma unroll 8
-    for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
-      const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
-      sO[(idx / S) * SP + idx % S] =
-          (X >= 0 && Y >= 0 && X < res && Y < res) ? to_fixed<K>(1.0f - d.img_I[pb + (long long)Y * res + X]) : 0u;
+        for (int r = threadIdx.x / CW; r < S; r += RP) {  // unrolled: loads in flight together
+          const int Y = y0 + r - h;
+          sO[r * SP + c] = col_in && Y >= 0 && Y < res ? to_fixed<K>(1.0f - src[Y * res + X]) : 0u;
+        }
+      }
     }
     __syncthreads();
     hsums_all<K>(OccSrc{sO, SP}, H);
@@ -254,13 +263,20 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
     __syncthreads();
+    {  // thread (column, first row): no division per element, 32-bit offsets from the problem's base
+      constexpr int CW = DilGeom<K>::CW, RP = kDThreads / CW;
+      const int c = threadIdx.x % CW, X = x0 + c - h;
+      const bool col_in = X >= 0 && X < res;
+      const float* msrc = d.dil_m + pb;
+      const uint8_t* ksrc = d.dil_mask + pb;
+      if (c < S) {
 #pragma unroll 8
-    for (int idx = threadIdx.x; idx < S * S; idx += kDThreads) {  // unrolled: loads in flight together
-      const int Y = y0 + idx / S - h, X = x0 + idx % S - h;
-      const bool in = X >= 0 && Y >= 0 && X < res && Y < res;
-      const long long pix = pb + (long long)Y * res + X;
-      const int si = (idx / S) * SP + idx % S;
-      sM[si] = in ? to_fixed<K>(d.dil_m[pix]) | ((uint32_t)d.dil_mask[pix] << 24) : 0u;
+        for (int r = threadIdx.x / CW; r < S; r += RP) {  // unrolled: loads in flight together
+          const int Y = y0 + r - h;
+          const int o = Y * res + X;
+          sM[r * SP + c] = col_in && Y >= 0 && Y < res ? to_fixed<K>(msrc[o]) | ((uint32_t)ksrc[o] << 24) : 0u;
+        }
+      }
     }
     __syncthreads();
     hsums_all<K>(GSrc{sM, SP}, H);
