@@ -6,7 +6,8 @@
 // w_k M_C (1 - O) (1 - D_k) over the container.  Its adjoint is
 //   dL_u/dO(q) = sum_k w_k [ -M_C(q)(1 - D_k(q)) - sum_{p in box_k(q)} M_C(p)(1 - O(p)) [B_k(p) < 1] ].
 // Both passes stage a 32 x 32 tile plus a halo of the largest radius in shared memory and form the
-// box sums separably (rows, then columns) with running windows, in fixed point.
+// box sums in fixed point: the forward pass from one integral image of the staged occupancy, the
+// adjoint (whose summand differs per kernel) separably, rows then columns, with running windows.
 #include "internal.h"
 
 namespace collage {
@@ -156,16 +157,25 @@ __device__ __forceinline__ int dil_tile(const Dev& d, int which, int i) {
   return d.dtile_list ? d.dtile_list[which * d.total_dtiles + i] : i;
 }
 
+// The forward pass forms every box sum from one integral image of the staged occupancy:
+// II[i][j] = sum of the staged values at rows < i and columns < j (row 0 and column 0 are zero), so
+// B_k at a pixel is four loads at offsets fixed by r_k.  Unsigned wrap-around is exact here too.
+template <int K>
+struct IIGeom {
+  static constexpr int S = DilGeom<K>::S;
+  static constexpr int P = S + 1;  // row stride and side of II; odd, as S is even
+  static_assert(P % 2 == 1, "odd row stride");
+};
+
 template <int K>
 __global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
   pdl_enter();
-  constexpr int S = DilGeom<K>::S, SP = DilGeom<K>::SP, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
+  constexpr int S = DilGeom<K>::S, P = IIGeom<K>::P, h = DilGeom<K>::h, Q = DilGeom<K>::Q;
   constexpr float inv_q = 1.0f / (float)(1u << Q);
   extern __shared__ uint32_t sm[];
   __shared__ float s_red[kDThreads / 32];
   if (*d.status & kStatusNoBins) return;
-  uint32_t* sO = sm;
-  uint32_t* H = sO + S * SP;
+  uint32_t* II = sm;
   // the tiles with container coverage; on the others M_C (1 - O) = 0, dL_u/dO = 0 and the loss
   // partial is 0, as written once per level
   const int n_own = dil_count(d, 0);
@@ -176,58 +186,84 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
     const int res = d.prob_res[p], nd = (res + kDT - 1) / kDT, ld = dt - d.prob_dtile_base[p];
     const int x0 = (ld % nd) * kDT, y0 = (ld / nd) * kDT;
     const long long pb = d.prob_pix_base[p];
+    const float* Ib = d.img_I + pb;
+    const float* Mb = d.covc + pb;
     __syncthreads();
     {  // thread (column, first row): no division per element, 32-bit offsets from the problem's base
       constexpr int CW = DilGeom<K>::CW, RP = kDThreads / CW;
       const int c = threadIdx.x % CW, X = x0 + c - h;
       const bool col_in = X >= 0 && X < res;
-      const float* src = d.img_I + pb;
       if (c < S) {
 #pragma unroll 8
         for (int r = threadIdx.x / CW; r < S; r += RP) {  // unrolled: loads in flight together
           const int Y = y0 + r - h;
-          sO[r * SP + c] = col_in && Y >= 0 && Y < res ? to_fixed<K>(1.0f - src[Y * res + X]) : 0u;
+          II[(r + 1) * P + c + 1] = col_in && Y >= 0 && Y < res ? to_fixed<K>(1.0f - Ib[Y * res + X]) : 0u;
         }
+      }
+      if (threadIdx.x < P) II[threadIdx.x] = 0u;              // row 0
+      if (threadIdx.x < S) II[(threadIdx.x + 1) * P] = 0u;    // column 0
+    }
+    __syncthreads();
+    if (threadIdx.x < S) {  // rows: lanes take rows (odd stride, distinct banks)
+      uint32_t* row = II + (threadIdx.x + 1) * P + 1;
+      uint32_t acc = 0u;
+#pragma unroll 9
+      for (int c = 0; c < S; ++c) {
+        acc += row[c];
+        row[c] = acc;
       }
     }
     __syncthreads();
-    hsums_all<K>(OccSrc{sO, SP}, H);
+    if (threadIdx.x < S) {  // columns: lanes take columns
+      uint32_t* col = II + P + 1 + threadIdx.x;
+      uint32_t acc = 0u;
+#pragma unroll 9
+      for (int r = 0; r < S; ++r) {
+        acc += col[r * P];
+        col[r * P] = acc;
+      }
+    }
     __syncthreads();
     float lu = 0.0f;
     for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
       const int c = it % kDT, r0 = (it / kDT) * kVRows;
+      const int X = x0 + c, Xc = min(X, res - 1);
       // the item's per-pixel inputs, read (from a clamped address, used only inside the image)
       // before its box sums are formed, so that the loads are in flight meanwhile
       float Iv[kVRows], Mv[kVRows];
 #pragma unroll
       for (int i = 0; i < kVRows; ++i) {
-        const long long pix = pb + (long long)min(y0 + r0 + i, res - 1) * res + min(x0 + c, res - 1);
-        Iv[i] = d.img_I[pix];
-        Mv[i] = d.covc[pix];
+        const int o = min(y0 + r0 + i, res - 1) * res + Xc;
+        Iv[i] = Ib[o];
+        Mv[i] = Mb[o];
       }
-      uint32_t B[K][kVRows];
-      vsums_col<K>(H, c, r0, B);
+      // II index of the pixel's own staged position (row r0 + i + h + 1, column c + h + 1)
+      const uint32_t* q0 = II + (r0 + h) * P + c + h;
 #pragma unroll
       for (int i = 0; i < kVRows; ++i) {
-        const int X = x0 + c, Y = y0 + r0 + i;
+        const int Y = y0 + r0 + i;
         if (X >= res || Y >= res) continue;
-        const long long pix = pb + (long long)Y * res + X;
-        const float O = 1.0f - Iv[i];
-        const float M = Mv[i];
-        const float mval = M * (1.0f - O);
-        float gdir = 0.0f;
+        const uint32_t* q = q0 + i * P;
+        // s = sum_k w_k (1 - D_k), with 1 - D_k = max(0, 2^Q - B_k) 2^-Q exactly
+        float s = 0.0f;
         unsigned mask = 0u;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          const float D = fminf(1.0f, (float)B[k][i] * inv_q);
-          const float w = d.L.dil_w[k];
-          lu += w * mval * (1.0f - D);
-          if (B[k][i] < (1u << Q)) mask |= 1u << k;  // B_k < 1, decided on the exact fixed-point sum
-          gdir -= w * (1.0f - D);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q) below
+          const int r = dil_r(k);
+          const uint32_t B = q[(r + 1) * P + r + 1] - q[-r * P + r + 1] - q[(r + 1) * P - r] + q[-r * P - r];
+          // B_k may reach 2^32 - 1 (not 2^31): the difference is taken unsigned
+          const uint32_t t = (1u << Q) - min(B, 1u << Q);
+          if (t != 0u) mask |= 1u << k;  // B_k < 1, decided on the exact fixed-point sum
+          s = fmaf(d.L.dil_w[k] * inv_q, (float)t, s);
         }
-        d.dil_m[pix] = mval;
-        d.dil_mask[pix] = (uint8_t)mask;
-        d.gOu[pix] = M * gdir;
+        const int o = Y * res + X;
+        const float O = 1.0f - Iv[i];
+        const float M = Mv[i];
+        const float mval = M * (1.0f - O);
+        lu = fmaf(mval, s, lu);
+        d.dil_m[pb + o] = mval;
+        d.dil_mask[pb + o] = (uint8_t)mask;
+        d.gOu[pb + o] = -(M * s);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q)
       }
     }
     // fixed-order block sum
@@ -472,7 +508,9 @@ __global__ void k_adam_flush(Dev d, float* out) {
 
 static size_t dilate_smem(int K, bool backward) {
   const int S = kDT + 2 * dil_r(K - 1), SP = S | 1;
-  (void)backward;  // the backward pass packs its masks into the staged words
+  // the forward pass keeps one integral image with a zero row and column; the backward pass packs
+  // its masks into the staged words and keeps every kernel's horizontal sums
+  if (!backward) return (size_t)(S + 1) * (S + 1) * sizeof(uint32_t);
   const size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP;
   return f * sizeof(uint32_t);
 }

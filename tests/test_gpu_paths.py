@@ -7,7 +7,9 @@ prove that it did:
     the emission stages in shared memory, so its tiles read the outline from global memory;
   - 40 small disks stacked at one spot: tiles that list more than 32 elements, ranked in global
     memory by the composite;
-  - a disk container of 3000 segments: the container raster stages its ring in chunks.
+  - a disk container of 3000 segments: the container raster stages its ring in chunks;
+  - a solid disk wider than the widest dilation kernel: full boxes, whose fixed-point sums pass
+    2^31 (the distribution term's unsigned arithmetic).
 Per-pixel Ihat / A_tau are compared with the FP64 oracle at 1e-5, the loss terms at 1e-5 relative
 and every gradient component at 1e-3 (atomic and deterministic modes): nonzero winding and the
 composites of Sec. 3-4.2.
@@ -119,3 +121,23 @@ def test_ordinary_case_takes_none_of_these_paths(env):
     # the counters count: a plain small case leaves them at zero
     info = _check_case(env, W.config_problem(1), 128, 16, 0, dict(gamma=0.0))
     assert info["path_row_fallback"] == info["path_wide_tile"] == info["path_ring_chunk"] == 0, info
+
+
+def solid_problem(res):
+    """One large disk over the middle of the container: the occupancy is 1 over whole boxes of the
+    widest kernel, whose fixed-point sums then pass 2^31."""
+    els = [(1, W.regular_polygon(0.3, 64), 0.0), (1, W.regular_polygon(0.05, 16), 0.0)]
+    params = [(0.5, 0.5, 0.0, 1.0), (0.5, 0.88, 0.0, 1.0)]
+    return W.make_problem(els, W.disk_container(), params, res)
+
+
+@pytest.mark.parametrize("n_dil", [4, 8])
+def test_solid_occupancy_box_sums_past_2_31(env, n_dil):
+    # the fixed-point precision Q is the largest with (w^2 + w) 2^(Q+1) < 2^32, w the widest
+    # kernel, so a full box holds w^2 2^Q, which is 2^31 or more for both kernel counts here
+    w, q = 5 + 6 * (n_dil - 1), 0
+    while q < 23 and ((w * w + w) << (q + 1)) < (1 << 32):
+        q += 1
+    assert (w * w) << q >= 1 << 31
+    _check_case(env, solid_problem(128), 128, 8, 0,
+                dict(n_dil=n_dil, dil_weight=tuple(float(k + 1) for k in range(n_dil))))
