@@ -37,7 +37,7 @@ __device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
 // region has an odd row stride; the horizontal sums H of kernel k keep only the 32 + 2 r_k rows its
 // vertical pass reads, with a row stride of 33; consecutive lanes take consecutive rows in the
 // horizontal pass and consecutive columns in the vertical one.
-constexpr int kSeg = 16;
+constexpr int kSeg = 32;  // one running window per row of the tile
 constexpr int kNSeg = kDT / kSeg;
 constexpr int kHP = kDT + 1;  // row stride of H
 constexpr int kFlagOwn = 1;   // container coverage is nonzero somewhere on the tile
@@ -93,6 +93,7 @@ __device__ __forceinline__ void hsum_one(const Src& src, uint32_t* H, int it) {
 // B[k][i] = sum_{|dr| <= r_k} H[k][r0 + i + r_k + dr][c].
 constexpr int kVRows = 4;
 constexpr int kVItems = kDT * (kDT / kVRows);
+static_assert(kVItems == kDThreads, "one output item per thread");
 
 template <int K, int k = 0>
 __device__ __forceinline__ void vsums_col(const uint32_t* H, int c, int r0, uint32_t (&B)[K][kVRows]) {
@@ -135,7 +136,8 @@ struct GSrc {  // G_k = M_C (1 - O) where B_k < 1, else 0; the staged word holds
   int SP;
   __device__ uint32_t operator()(int k, int rr, int cc) const {
     const uint32_t x = sM[rr * SP + cc];
-    return ((x >> (24 + k)) & 1u) ? (x & 0xffffffu) : 0u;
+    // bit 24 + k moved to the sign and spread over the word: all ones where B_k < 1
+    return x & 0xffffffu & (uint32_t)((int)(x << (7 - k)) >> 31);
   }
 };
 
@@ -203,6 +205,17 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
       if (threadIdx.x < P) II[threadIdx.x] = 0u;              // row 0
       if (threadIdx.x < S) II[(threadIdx.x + 1) * P] = 0u;    // column 0
     }
+    // the thread's output item (column c, rows r0..r0 + kVRows - 1): its per-pixel inputs are
+    // read now (from a clamped address, used only inside the image), in flight during the scans
+    const int c = threadIdx.x % kDT, r0 = (threadIdx.x / kDT) * kVRows;
+    const int X = x0 + c, Xc = min(X, res - 1);
+    float Iv[kVRows], Mv[kVRows];
+#pragma unroll
+    for (int i = 0; i < kVRows; ++i) {
+      const int o = min(y0 + r0 + i, res - 1) * res + Xc;
+      Iv[i] = Ib[o];
+      Mv[i] = Mb[o];
+    }
     __syncthreads();
     if (threadIdx.x < S) {  // rows: lanes take rows (odd stride, distinct banks)
       uint32_t* row = II + (threadIdx.x + 1) * P + 1;
@@ -225,18 +238,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
     }
     __syncthreads();
     float lu = 0.0f;
-    for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
-      const int c = it % kDT, r0 = (it / kDT) * kVRows;
-      const int X = x0 + c, Xc = min(X, res - 1);
-      // the item's per-pixel inputs, read (from a clamped address, used only inside the image)
-      // before its box sums are formed, so that the loads are in flight meanwhile
-      float Iv[kVRows], Mv[kVRows];
-#pragma unroll
-      for (int i = 0; i < kVRows; ++i) {
-        const int o = min(y0 + r0 + i, res - 1) * res + Xc;
-        Iv[i] = Ib[o];
-        Mv[i] = Mb[o];
-      }
+    {
       // II index of the pixel's own staged position (row r0 + i + h + 1, column c + h + 1)
       const uint32_t* q0 = II + (r0 + h) * P + c + h;
 #pragma unroll
@@ -314,26 +316,31 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
         }
       }
     }
+    // the thread's output item (column c, rows r0..r0 + kVRows - 1): the forward pass's direct
+    // part of dL_u/dO is read now, in flight during the horizontal pass
+    float* g = d.gOu + pb;
+    const int c = threadIdx.x % kDT, r0 = (threadIdx.x / kDT) * kVRows;
+    const int X = x0 + c, Xc = min(X, res - 1);
+    float gv[kVRows];
+#pragma unroll
+    for (int i = 0; i < kVRows; ++i) gv[i] = own ? g[min(y0 + r0 + i, res - 1) * res + Xc] : 0.0f;
     __syncthreads();
     hsums_all<K>(GSrc{sM, SP}, H);
     __syncthreads();
-    for (int it = threadIdx.x; it < kVItems; it += kDThreads) {
-      const int c = it % kDT, r0 = (it / kDT) * kVRows;
-      // the forward pass's direct part of dL_u/dO, read before the box sums are formed
-      float gv[kVRows];
+    float wq[K];
 #pragma unroll
-      for (int i = 0; i < kVRows; ++i)
-        gv[i] = own ? d.gOu[pb + (long long)min(y0 + r0 + i, res - 1) * res + min(x0 + c, res - 1)] : 0.0f;
+    for (int k = 0; k < K; ++k) wq[k] = d.L.dil_w[k] * inv_q;
+    {
       uint32_t B[K][kVRows];
       vsums_col<K>(H, c, r0, B);
 #pragma unroll
       for (int i = 0; i < kVRows; ++i) {
-        const int X = x0 + c, Y = y0 + r0 + i;
+        const int Y = y0 + r0 + i;
         if (X >= res || Y >= res) continue;
         float acc = 0.0f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc -= d.L.dil_w[k] * ((float)B[k][i] * inv_q);
-        d.gOu[pb + (long long)Y * res + X] = gv[i] + acc;
+        for (int k = 0; k < K; ++k) acc = fmaf(-wq[k], (float)B[k][i], acc);
+        g[Y * res + X] = gv[i] + acc;
       }
     }
   }

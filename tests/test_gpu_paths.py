@@ -124,10 +124,12 @@ def test_ordinary_case_takes_none_of_these_paths(env):
 
 
 def solid_problem(res):
-    """One large disk over the middle of the container: the occupancy is 1 over whole boxes of the
-    widest kernel, whose fixed-point sums then pass 2^31."""
-    els = [(1, W.regular_polygon(0.3, 64), 0.0), (1, W.regular_polygon(0.05, 16), 0.0)]
-    params = [(0.5, 0.5, 0.0, 1.0), (0.5, 0.88, 0.0, 1.0)]
+    """One large irregular polygon over the middle of the container: the occupancy is 1 over whole
+    boxes of the widest kernel, whose fixed-point sums then pass 2^31.  Placed off both axes with
+    a blob beside it, so that no gradient component vanishes by symmetry."""
+    rng = W.PCG32(17)
+    els = [(1, W.convex_polygon(rng, 0.28, 24), 0.0), (0, W.blob_controls(rng, 0.05), 0.0)]
+    params = [(0.47, 0.52, 0.3, 1.0), (0.62, 0.86, 0.0, 1.0)]
     return W.make_problem(els, W.disk_container(), params, res)
 
 
