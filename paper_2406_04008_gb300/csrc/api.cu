@@ -413,8 +413,7 @@ static collage_status ensure_level_bufs(collage_t h, size_t np, size_t nt, size_
   CK(h, dmalloc(h->level_bufs, d.img_I, np));
   CK(h, dmalloc(h->level_bufs, d.img_Pt, np));
   CK(h, dmalloc(h->level_bufs, d.gOu, np));
-  CK(h, dmalloc(h->level_bufs, d.dil_m, np));
-  CK(h, dmalloc(h->level_bufs, d.dil_mask, np));
+  CK(h, dmalloc(h->level_bufs, d.dil_g, np));
   CK(h, dmalloc(h->level_bufs, d.tile_n, nt));
   CK(h, cudaMemset(d.tile_n, 0, sizeof(int) * nt));
   CK(h, dmalloc(h->level_bufs, d.tile_m, nt));
@@ -510,8 +509,7 @@ static cudaError_t enqueue_level_switch(const Dev& d, cudaStream_t s) {
   cudaError_t e = launch_container(d, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.dtile_n, 0, 2 * sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.gOu, 0, sizeof(float) * (size_t)d.total_pix, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.dil_m, 0, sizeof(float) * (size_t)d.total_pix, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.dil_mask, 0, (size_t)d.total_pix, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.dil_g, 0, sizeof(uint32_t) * (size_t)d.total_pix, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.lossU, 0, sizeof(float) * (size_t)d.total_dtiles, s);
   if (e == cudaSuccess) e = launch_dtile_flags(d, s);
   return e;

@@ -120,8 +120,8 @@ struct Dev {
   float* img_I;                 // [pix] Ihat = prod(1 - c)
   float* img_Pt;                // [pix] +-prod(1 - tau c^pad), negative where A_tau > tau
   float* gOu;                   // [pix] dL_u/dO
-  float* dil_m;                 // [pix] M_C (1 - O), masked per kernel by dil_mask
-  uint8_t* dil_mask;            // [pix] bit k: B_k < 1
+  uint32_t* dil_g;              // [pix] the adjoint's staged word: round(M_C (1 - O) 2^Q) in bits
+                                // 0..23, bit 24 + k set where B_k < 1 (Q of the kernel count)
   float4* lossA;                // [total_tiles] (sum W(I-Ic)^2, sum relu(A-tau), sum O(1-y), 0)
   float* lossU;                 // [total_dtiles] weighted uniform-loss partial
   uint8_t* dtile_flags;         // [total_dtiles] container coverage on the tile / its halo (or null)

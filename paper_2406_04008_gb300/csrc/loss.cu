@@ -263,8 +263,7 @@ __global__ void __launch_bounds__(kDThreads, 5) k_dilate_fwd(Dev d) {
         const float M = Mv[i];
         const float mval = M * (1.0f - O);
         lu = fmaf(mval, s, lu);
-        d.dil_m[pb + o] = mval;
-        d.dil_mask[pb + o] = (uint8_t)mask;
+        d.dil_g[pb + o] = to_fixed<K>(mval) | (mask << 24);  // mval <= 1: at most 2^Q < 2^24
         d.gOu[pb + o] = -(M * s);  // d/dO(q) of M(q)(1 - O(q))(1 - D_k(q)), times M(q)
       }
     }
@@ -305,14 +304,13 @@ __global__ void __launch_bounds__(kDThreads, 6) k_dilate_bwd(Dev d) {
       constexpr int CW = DilGeom<K>::CW, RP = kDThreads / CW;
       const int c = threadIdx.x % CW, X = x0 + c - h;
       const bool col_in = X >= 0 && X < res;
-      const float* msrc = d.dil_m + pb;
-      const uint8_t* ksrc = d.dil_mask + pb;
+      const uint32_t* gsrc = d.dil_g + pb;
       if (c < S) {
 #pragma unroll 8
         for (int r = threadIdx.x / CW; r < S; r += RP) {  // unrolled: loads in flight together
           const int Y = y0 + r - h;
           const int o = Y * res + X;
-          sM[r * SP + c] = col_in && Y >= 0 && Y < res ? to_fixed<K>(msrc[o]) | ((uint32_t)ksrc[o] << 24) : 0u;
+          sM[r * SP + c] = col_in && Y >= 0 && Y < res ? gsrc[o] : 0u;
         }
       }
     }
@@ -515,8 +513,8 @@ __global__ void k_adam_flush(Dev d, float* out) {
 
 static size_t dilate_smem(int K, bool backward) {
   const int S = kDT + 2 * dil_r(K - 1), SP = S | 1;
-  // the forward pass keeps one integral image with a zero row and column; the backward pass packs
-  // its masks into the staged words and keeps every kernel's horizontal sums
+  // the forward pass keeps one integral image with a zero row and column; the backward pass stages
+  // the packed words the forward pass wrote and keeps every kernel's horizontal sums
   if (!backward) return (size_t)(S + 1) * (S + 1) * sizeof(uint32_t);
   const size_t f = (size_t)S * SP + (size_t)hbase(K) * kHP;
   return f * sizeof(uint32_t);

@@ -15,10 +15,9 @@
 namespace collage {
 
 constexpr int kNoAllocMaxDT = (1024 / 32) * (1024 / 32);  // 32 x 32 dilation tiles
-// layout: [m: float x max pixels][mask: byte x max pixels][tile partials: float x max tiles]
+// layout: [the adjoint's staged words: uint32 x max pixels][tile partials: float x max tiles]
 //         [small ints: status, res, dilation-tile base (2), pixel base as long long (2)]
-constexpr size_t kOffMask = sizeof(float) * COLLAGE_NOALLOC_MAX_PIXELS;
-constexpr size_t kOffLossU = kOffMask + COLLAGE_NOALLOC_MAX_PIXELS;
+constexpr size_t kOffLossU = sizeof(uint32_t) * COLLAGE_NOALLOC_MAX_PIXELS;
 constexpr size_t kOffInts = kOffLossU + sizeof(float) * kNoAllocMaxDT;
 constexpr size_t kNoAllocBytes = kOffInts + 256;
 
@@ -107,8 +106,7 @@ extern "C" collage_status collage_uniform_term_noalloc(void* stream, int res, in
   d.img_I = const_cast<float*>(d_ihat);
   d.covc = const_cast<float*>(d_cov);
   d.gOu = d_grad_occ;
-  d.dil_m = reinterpret_cast<float*>(base);
-  d.dil_mask = base + kOffMask;
+  d.dil_g = reinterpret_cast<uint32_t*>(base);
   d.lossU = reinterpret_cast<float*>(base + kOffLossU);
   d.L.n_dil = n_dilations;
   d.L.gamma = 1.0f;
