@@ -273,7 +273,8 @@ typedef struct {
  * emission's chunk side and the persistent-grid multiples of the emission, adjoint and composite
  * kernels (each candidate a
  * captured one-iteration graph of loss and gradient, no Adam step, the fastest of three batches of
- * 20 timed replays), and keeps the fastest; a launch parameter other than the tile changes only
+ * 20 replays, each timed alone from a cold L2 after a write of twice the L2 size through a
+ * scratch buffer the call allocates and frees), and keeps the fastest; a launch parameter other than the tile changes only
  * when its candidate is more than 3% faster.  The choice is cached for the process, keyed on (pixels of the level, element
  * count, pair density in half-octaves, deterministic mode); a handle with the same key reuses it
  * without a search.  One configuration serves the whole handle (every problem of a batch).

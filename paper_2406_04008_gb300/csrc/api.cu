@@ -1412,6 +1412,16 @@ struct EventPair {
     if (b) cudaEventDestroy(b);
   }
 };
+
+// A buffer of twice the L2 size, written before each timed replay so that every candidate starts
+// from a cold cache, as a step does after the host or other work has used the device.
+struct L2Evict {
+  void* p = nullptr;
+  size_t n = 0;
+  ~L2Evict() {
+    if (p) cudaFree(p);
+  }
+};
 }  // namespace
 
 // Applies a choice (tile change: new level tables and pair buffers).
@@ -1431,9 +1441,12 @@ static collage_status apply_choice(collage_t h, const TuneChoice& c) {
 }
 
 // Milliseconds per loss + gradient iteration (no Adam step) in the current configuration: a
-// captured one-iteration graph, 3 replays to warm up, then three batches of `reps` timed replays;
-// the fastest batch's mean (the least disturbed by anything else on the device).
-static collage_status time_config(collage_t h, cudaStream_t s, int reps, float* ms) {
+// captured one-iteration graph, 3 replays to warm up, then three batches of `reps` replays, each
+// timed alone after the L2 eviction write; the fastest batch's mean (the least disturbed by
+// anything else on the device).  Timed warm and back to back, the replays favoured launch
+// parameters whose gain reversed from a cold cache.
+static collage_status time_config(collage_t h, cudaStream_t s, int reps, const L2Evict& ev2,
+                                  float* ms) {
   collage_status st = run_checked(h, s, kLossBwd, nullptr, nullptr);  // regrows if needed
   if (st) return st;
   cudaGraph_t g = nullptr;
@@ -1451,15 +1464,23 @@ static collage_status time_config(collage_t h, cudaStream_t s, int reps, float* 
   EventPair ev;
   cudaError_t er = cudaEventCreate(&ev.a);
   if (er == cudaSuccess) er = cudaEventCreate(&ev.b);
-  for (int i = 0; i < 3 && er == cudaSuccess; ++i) er = cudaGraphLaunch(ge, s);
+  for (int i = 0; i < 3 && er == cudaSuccess; ++i) {
+    er = cudaMemsetAsync(ev2.p, 0, ev2.n, s);
+    if (er == cudaSuccess) er = cudaGraphLaunch(ge, s);
+  }
   float t = 1e30f;
   for (int batch = 0; batch < 3 && er == cudaSuccess; ++batch) {
-    er = cudaEventRecord(ev.a, s);
-    for (int i = 0; i < reps && er == cudaSuccess; ++i) er = cudaGraphLaunch(ge, s);
-    if (er == cudaSuccess) er = cudaEventRecord(ev.b, s);
-    if (er == cudaSuccess) er = cudaEventSynchronize(ev.b);
     float tb = 0.0f;
-    if (er == cudaSuccess) er = cudaEventElapsedTime(&tb, ev.a, ev.b);
+    for (int i = 0; i < reps && er == cudaSuccess; ++i) {
+      er = cudaMemsetAsync(ev2.p, 0, ev2.n, s);
+      if (er == cudaSuccess) er = cudaEventRecord(ev.a, s);
+      if (er == cudaSuccess) er = cudaGraphLaunch(ge, s);
+      if (er == cudaSuccess) er = cudaEventRecord(ev.b, s);
+      if (er == cudaSuccess) er = cudaEventSynchronize(ev.b);
+      float ti = 0.0f;
+      if (er == cudaSuccess) er = cudaEventElapsedTime(&ti, ev.a, ev.b);
+      tb += ti;
+    }
     t = std::min(t, tb);
   }
   cudaGraphExecDestroy(ge);
@@ -1467,7 +1488,7 @@ static collage_status time_config(collage_t h, cudaStream_t s, int reps, float* 
   bool over = false;
   st = check_and_grow(h, s, &over);
   if (st) return st;
-  if (over) return time_config(h, s, reps, ms);  // grown: time again
+  if (over) return time_config(h, s, reps, ev2, ms);  // grown: time again
   *ms = t / reps;
   return COLLAGE_OK;
 }
@@ -1484,6 +1505,14 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   const double pairs = (double)std::max(h->h_ctl[2], 1) * (h->d.tile == 8 ? 1.0 : 4.0);
   const int density = (int)std::floor(2.0 * std::log2(1.0 + pairs / tiles8));
   const auto key = std::make_tuple(pix, h->N, density, h->opt.deterministic);
+  L2Evict ev2;
+  {
+    int dev = 0, l2 = 0;
+    CK(h, cudaGetDevice(&dev));
+    CK(h, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    ev2.n = std::max<size_t>(2 * (size_t)l2, (size_t)64 << 20);
+    CK(h, cudaMalloc(&ev2.p, ev2.n));
+  }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1491,7 +1520,7 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
       collage_status st = apply_choice(h, it->second);
       if (st) return st;
       float ms = 0.0f;
-      st = time_config(h, s, 10, &ms);
+      st = time_config(h, s, 10, ev2, &ms);
       if (st) return st;
       h->tuning.tile = it->second.tile;
       h->tuning.emit_threads = it->second.emit_threads;
@@ -1512,7 +1541,7 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
   float best_ms = 1e30f, default_ms = 0.0f;
   auto trial = [&](const TuneChoice& c, float* out) -> collage_status {
     collage_status st = apply_choice(h, c);
-    if (!st) st = time_config(h, s, reps, out);
+    if (!st) st = time_config(h, s, reps, ev2, out);
     ++trials;
     return st;
   };
@@ -1541,8 +1570,8 @@ extern "C" collage_status collage_autotune(collage_t h, void* stream, float* h_b
       if (std::memcmp(&c, &base, sizeof(c)) == 0) continue;
       float ms = 0.0f;
       if ((st = trial(c, &ms))) break;
-      if (ms < best_ms * 0.97f) {  // a change of launch parameter has to win clearly (3%: the
-        // one-iteration graphs it is timed on run warm; smaller gains do not carry to the step)
+      if (ms < best_ms * 0.97f) {  // a change of launch parameter has to win clearly (3%:
+        // smaller gains on the one-iteration graph do not carry to the whole step)
         best_ms = ms;
         best = c;
       }
