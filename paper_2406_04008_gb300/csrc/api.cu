@@ -1038,7 +1038,10 @@ extern "C" collage_status collage_step_async(collage_t h, void* stream, int n_it
 
 // --------------------------------------------------------------------------------------------
 // The level schedule (Sec. 4.3) as one CUDA graph: per level the level switch, then a WHILE node
-// whose body is one iteration; the loop conditions are set on the device (csrc/sched.cu).
+// whose body is U iterations, U the largest divisor of the level's count up to kSchedUnroll (so
+// the loop ends on the level's target); the loop conditions are set on the device (csrc/sched.cu).
+constexpr int kSchedUnroll = 10;
+
 // --------------------------------------------------------------------------------------------
 static cudaError_t capture_schedule(collage_t h, int start, cudaStream_t s) {
   const collage_options& o = h->opt;
@@ -1069,12 +1072,22 @@ static cudaError_t capture_schedule(collage_t h, int start, cudaStream_t s) {
     if (e == cudaSuccess)
       e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
     if (e != cudaSuccess) break;
-    // the loop body: one iteration, then the condition for the next pass
+    // the loop body: U iterations, then the condition for the next pass (one body relaunch and
+    // one condition kernel per U iterations; a status latched inside the body makes its later
+    // kernels return without stepping, so the loop still stops on the iteration that failed)
+    const int n_l = o.level_iters[l];
+    int U = 1;
+    for (int u = std::min(n_l, kSchedUnroll); u > 1; --u)
+      if (n_l % u == 0) {
+        U = u;
+        break;
+      }
     cudaStream_t b = h->body_stream;
     e = cudaStreamBeginCaptureToGraph(b, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
-    cudaError_t eb = enqueue_iter(h, b, kStep, nullptr, nullptr);
+    cudaError_t eb = cudaSuccess;
+    for (int u = 0; u < U && eb == cudaSuccess; ++u) eb = enqueue_iter(h, b, kStep, nullptr, nullptr);
     if (eb == cudaSuccess) eb = launch_sched_cond(d, b, cond, target);
     cudaGraph_t body = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(b, &body);

@@ -1,7 +1,8 @@
 // Device side of the captured level schedule (Sec. 4.3: the coarse-to-fine loop over the resolution
 // pyramid).  collage_run_schedule captures the whole run as one CUDA graph: per level, the level
 // switch (container raster and the distribution term's tile lists), then a conditional WHILE node
-// whose body is one iteration.  The loop condition is decided on the device: these kernels compare
+// whose body is a few iterations (a divisor of the level's count).  The loop condition is decided
+// on the device: these kernels compare
 // the iterations completed in this run (Adam step count now against the count when the run began)
 // with the run's cumulative target through the level, and stop the loop once the status word has
 // latched a bin overflow or non-finite params, so that the host can resume from exactly the

@@ -112,3 +112,20 @@ def test_schedule_with_a_level_of_zero_iterations(Collage):
     assert torch.equal(a.get_state()[0], b.get_state()[0])
     a.close()
     b.close()
+
+
+def test_schedule_bodies_of_several_iterations(Collage):
+    # 12 iterations: two passes of a 6-iteration body; 11 (prime): eleven passes of one; 4: one pass
+    prob = _prob()
+    kw = _kw()
+    kw["level_iters"] = [12, 11, 4]
+    a = Collage(prob, use_graphs=1, **kw)
+    b = Collage(prob, use_graphs=0, **kw)
+    a.run_schedule()
+    b.run_schedule()
+    _, step, level = a.get_state()
+    assert step == 27 and level == 2
+    assert torch.equal(a.get_state()[0], b.get_state()[0])
+    assert torch.equal(a.loss(), b.loss())
+    a.close()
+    b.close()
