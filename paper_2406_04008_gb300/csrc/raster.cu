@@ -444,13 +444,15 @@ __global__ void __launch_bounds__(NT, (T == 8 ? 1024 : 512) / NT) k_raster_chunk
 // tile by a fixed shuffle tree.  No block-wide barrier: each warp owns its tile.
 // ------------------------------------------------------------------------------------------------
 constexpr int kCompWarps = 4;
-constexpr int kCompGroup = 4;  // pairs whose records are read together
+constexpr int kCompGroup = 4;   // pairs whose records are read together
+constexpr int kCompWide = 256;  // lists up to this long are ranked from shared memory
 template <int T>
 __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out_bw, float* out_tau) {
   pdl_enter();
   constexpr int NP = T * T, PPL = NP / 32;
   __shared__ int s_slot[kCompWarps][32];
   __shared__ uint8_t s_cls[kCompWarps][32];
+  __shared__ int s_wide[kCompWarps][kCompWide];  // a long list's element ids, in list order
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // the emission has completed: its work list is spent
     d.chunk_count[0] = d.chunk_count[1] = 0;
     d.work[0] = 0;
@@ -504,6 +506,19 @@ __global__ void __launch_bounds__(kCompWarps * 32) k_composite(Dev d, float* out
         w_cls[r] = c0;
         sorted[r] = v;
         sorted_slot[r] = sl;
+      }
+    } else if (m <= kCompWide) {
+      // the element ids read once (independent loads), then each entry ranked against them all
+      if (lane == 0 && d.paths) atomicAdd(&d.paths[2], 1ull);
+      int* wv = s_wide[wid];
+      for (int i = lane; i < m; i += 32) wv[i] = d.pair_elem[d.tile_list[lb + i]];
+      __syncwarp();
+      for (int i = lane; i < m; i += 32) {
+        const int vi = wv[i];
+        int r = 0;
+        for (int j = 0; j < m; ++j) r += wv[j] < vi ? 1 : 0;  // one address for every lane
+        sorted[r] = vi;
+        sorted_slot[r] = d.tile_list[lb + i];
       }
     } else {
       if (lane == 0 && d.paths) atomicAdd(&d.paths[2], 1ull);
