@@ -26,17 +26,19 @@ __device__ __forceinline__ int find_prob_d(const int* base, int P, int t) {
 }
 
 // Box sums in fixed point: a value v in [0, 1] is held as round(v 2^Q) in a 32-bit unsigned
-// integer, with Q the largest precision for which (w^2 + w) 2^Q < 2^32, w the widest kernel.
-// Integer sums are exact in any order (unsigned wrap-around cancels between the add and the
-// subtract of a running window, and every box sum is below 2^32), so a thread slides one window
-// along kSeg outputs of a row (or column) of one kernel with one add and one subtract per output
-// and no rounding drift.  The kernels are instantiated per number of dilations K so that every
-// window loop unrolls.
+// integer, with Q the largest precision for which (w^2 + w) 2^Q < 2^32, w the widest kernel (so a
+// full box, w^2 2^Q, may pass 2^31).  Integer sums are exact in any order: unsigned wrap-around
+// cancels between the add and the subtract of a running window, and in the four-corner difference
+// of an integral image, since every box sum is below 2^32.  The adjoint slides one window along
+// kSeg outputs of a row (or column) of one kernel, with one add and one subtract per output and no
+// rounding drift; the forward pass reads every kernel's box sums from one integral image.  The
+// kernels are instantiated per number of dilations K so that every window loop unrolls.
 //
 // Shared-memory layout, chosen so that the 32 lanes of a warp touch 32 distinct banks: the staged
-// region has an odd row stride; the horizontal sums H of kernel k keep only the 32 + 2 r_k rows its
-// vertical pass reads, with a row stride of 33; consecutive lanes take consecutive rows in the
-// horizontal pass and consecutive columns in the vertical one.
+// region and the integral image have odd row strides; the horizontal sums H of kernel k keep only
+// the 32 + 2 r_k rows its vertical pass reads, with a row stride of 33; consecutive lanes take
+// consecutive rows in the horizontal pass and the row scan, and consecutive columns in the
+// vertical pass, the column scan and the staging.
 constexpr int kSeg = 32;  // one running window per row of the tile
 constexpr int kNSeg = kDT / kSeg;
 constexpr int kHP = kDT + 1;  // row stride of H
