@@ -692,12 +692,23 @@ static collage_status check_and_grow(collage_t h, cudaStream_t s, bool* overflow
   if (status & (kStatusOverflow | kStatusTileCap)) {
     // void bins: the tiles' lists are cleared, then the pair buffers or the lists regrown
     *overflowed = true;
+    int fullest = 0;
+    if (status & kStatusTileCap) {
+      // the emission counts on past the capacity: the fullest list's length, read before the
+      // counts are cleared, sizes the lists in one regrow
+      std::vector<int> cnt((size_t)h->d.total_tiles);
+      CK(h, cudaMemcpyAsync(cnt.data(), h->d.tile_n, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaStreamSynchronize(s));
+      for (int c : cnt) fullest = std::max(fullest, c);
+    }
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(int), s));
     CK(h, cudaMemsetAsync(h->d.tile_n, 0, sizeof(int) * h->tile_cap, s));
     CK(h, cudaStreamSynchronize(s));
     if (status & kStatusTileCap) {
-      if (h->d.tile_cap >= (1 << 20)) return fail(h, COLLAGE_ERR_OVERFLOW, "a tile lists more than 2^20 pairs");
-      collage_status st2 = ensure_tile_lists(h, 2 * h->d.tile_cap);
+      if (fullest >= (1 << 20)) return fail(h, COLLAGE_ERR_OVERFLOW, "a tile lists more than 2^20 pairs");
+      int per_tile = 2 * h->d.tile_cap;  // at least doubled; past 3/4 full at the fullest list
+      while (per_tile * 3 < fullest * 4) per_tile *= 2;
+      collage_status st2 = ensure_tile_lists(h, per_tile);
       if (st2) return st2;
     }
     if (status & kStatusOverflow) {

@@ -5,8 +5,9 @@ prove that it did:
   - a comb whose pixel rows cross the outline more than 16 times inside one tile: the winding
     number of those rows is taken over every segment; its 523 segments are more than the 512
     the emission stages in shared memory, so its tiles read the outline from global memory;
-  - 40 small disks stacked at one spot: tiles that list more than 32 elements, ranked in global
-    memory by the composite;
+  - 40 small disks stacked at one spot: tiles that list more than 32 elements, ranked by the
+    composite from their element ids staged in shared memory; 300 of them: lists longer than that
+    staging (256), ranked from global memory;
   - a disk container of 3000 segments: the container raster stages its ring in chunks;
   - a solid disk wider than the widest dilation kernel: full boxes, whose fixed-point sums pass
     2^31 (the distribution term's unsigned arithmetic).
@@ -143,3 +144,23 @@ def test_solid_occupancy_box_sums_past_2_31(env, n_dil):
     assert (w * w) << q >= 1 << 31
     _check_case(env, solid_problem(128), 128, 8, 0,
                 dict(n_dil=n_dil, dil_weight=tuple(float(k + 1) for k in range(n_dil))))
+
+
+def deep_stack_problem(res, n=300):
+    rng = np.random.default_rng(7)
+    els, params = [], []
+    for _ in range(n):
+        els.append((1, W.regular_polygon(rng.uniform(1.5, 2.5) / res, 8), 0.0))
+        params.append((0.5 + rng.uniform(-0.8, 0.8) / res, 0.5 + rng.uniform(-0.8, 0.8) / res,
+                       rng.uniform(0, 1), 1.0))
+    return W.make_problem(els, W.disk_container(), params, res)
+
+
+def test_tiles_with_more_than_256_elements(env):
+    # lists longer than the composite ranks in shared memory: ranked from global memory
+    O, _ = env
+    prob = deep_stack_problem(128)
+    t, _ = O.Scene(prob).bins(prob["params0"], 128, 8, 1.0, 1.0)
+    assert np.bincount(t).max() > 256  # the case reaches that path
+    info = _check_case(env, prob, 128, 8, 1, dict(pad_px=1.0))
+    assert info["path_wide_tile"] > 0, info
